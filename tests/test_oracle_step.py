@@ -1,0 +1,248 @@
+"""Pins of the oracle's full step (Sec. 4, 5) against the paper: the 1D growth
+matrix and its eigenvalues (Sec. 5.4), the exact shift at xi = 1, exact transport
+of linear data, cross-derivative reconstruction (Sec. 2.3 approach A), and the
+convergence orders of Sec. 6.1.1 and 6.1.2."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3409_gb300 import inputs
+
+
+def _growth_matrix_paper(xi, theta, h):
+    """G~_{xi,h}(theta) as printed in Sec. 5.4 (f0=f(xi), f1=f(1-xi), g0=g(xi),
+    g1=-g(1-xi), primes are d/dxi)."""
+    f = lambda x: 1 - 3 * x * x + 2 * x ** 3
+    fp = lambda x: -6 * x + 6 * x * x
+    g = lambda x: x * (1 - x) ** 2
+    gp = lambda x: (1 - x) ** 2 - 2 * x * (1 - x)
+    f0, f1 = f(xi), f(1 - xi)
+    g0, g1 = g(xi), -g(1 - xi)
+    f0p, f1p = fp(xi), -fp(1 - xi)
+    g0p, g1p = gp(xi), gp(1 - xi)
+    E = np.exp(1j * theta)
+    return np.array([[f0 + E * f1, h * (g0 + E * g1)],
+                     [(f0p + E * f1p) / h, g0p + E * g1p]])
+
+
+def _growth_matrix_oracle(xi, theta, n=40):
+    """Apply one oracle step (constant v < 0, 1D) to the Fourier modes
+    (phi, psi) = (e^{i theta j}, 0) and (0, e^{i theta j}) and read the matrix off
+    an interior node."""
+    h = 1.0 / (n - 1)
+    dt = 0.01
+    v = -xi * h / dt  # foot = x_j + xi h, i.e. in cell [x_j, x_{j+1}]
+    g = oracle.grid((n,))
+    vel = oracle.velocity("const", c=(v,))
+    j = np.arange(n)
+    G = np.zeros((2, 2), dtype=complex)
+    for col in range(2):
+        out = []
+        for part in (np.cos, np.sin):
+            st = np.zeros((2, n))
+            st[col] = part(theta * j)
+            out.append(oracle.step(g, vel, st, 0.0, dt))
+        res = out[0] + 1j * out[1]
+        jj = n // 2
+        G[:, col] = res[:, jj] / np.exp(1j * theta * jj)
+    return G
+
+
+@pytest.mark.parametrize("xi", [0.2, 0.4, 0.6, 0.8, 0.37])
+@pytest.mark.parametrize("theta", [0.0, 0.3, 1.0, 2.5, math.pi])
+def test_growth_matrix_matches_paper(xi, theta):
+    n = 40
+    h = 1.0 / (n - 1)
+    G = _growth_matrix_oracle(xi, theta, n)
+    assert np.allclose(G, _growth_matrix_paper(xi, theta, h), atol=1e-11)
+
+
+@pytest.mark.parametrize("xi", [0.2, 0.4, 0.6, 0.8])
+def test_theta0_eigenvalues(xi, golden):
+    # Sec. 5.4: at theta = 0, lambda1 = 1, lambda2 = 1 - 6 xi (1 - xi)
+    G = _growth_matrix_oracle(xi, 0.0)
+    lam = np.sort(np.linalg.eigvals(G).real)
+    assert lam == pytest.approx(sorted([golden["stability_theta0"]["lambda1"], 1 - 6 * xi * (1 - xi)]), abs=1e-11)
+
+
+@pytest.mark.parametrize("xi", [0.2, 0.4, 0.6, 0.8])
+def test_eigenvalues_inside_unit_circle(xi, golden):
+    # figure of Sec. 5.4: for theta != 0 both eigenvalues are strictly inside
+    assert xi in golden["stability_unit_circle"]["xi_values"]
+    for theta in np.linspace(-math.pi, math.pi, 41):
+        if abs(theta) < 1e-12:
+            continue
+        lam = np.linalg.eigvals(_growth_matrix_oracle(xi, theta))
+        assert np.max(np.abs(lam)) < 1.0 - 1e-6
+
+
+def test_exact_shift_xi1():
+    # Sec. 5.4, xi = 1: phi_j^{n+1} = phi_{j+1}^n, psi likewise -- bit-exact
+    n = 65
+    g = oracle.grid((n,))
+    vel = oracle.velocity("const", c=(-1.0,))
+    rng = np.random.default_rng(2)
+    st = rng.normal(size=(2, n))
+    out = oracle.step(g, vel, st, 0.0, 1.0 / 64)
+    assert np.array_equal(out[:, :-1], st[:, 1:])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_integer_cell_shift_bit_exact(dim):
+    """A translation by exactly one cell per axis moves every plane by one node
+    (h = 2^-6); the rebuilt cross derivatives shift too, away from the boundary."""
+    n = 33 if dim == 2 else 17
+    h = 1.0 / (n - 1)
+    g = oracle.grid((n,) * dim)
+    vel = oracle.velocity("const", c=(-1.0,) * dim)
+    st = inputs.random_state((oracle.nplanes(dim),) + (n,) * dim, seed=3)
+    st = oracle.recon_cross(g, st)
+    out = oracle.step(g, vel, st, 0.0, h)
+    ncore = 1 + dim
+    if dim == 2:
+        assert np.array_equal(out[:ncore, :-1, :-1], st[:ncore, 1:, 1:])
+        assert np.array_equal(out[ncore:, 1:-2, 1:-2], st[ncore:, 2:-1, 2:-1])
+    else:
+        assert np.array_equal(out[:ncore, :-1, :-1, :-1], st[:ncore, 1:, 1:, 1:])
+        assert np.array_equal(out[ncore:, 1:-2, 1:-2, 1:-2], st[ncore:, 2:-1, 2:-1, 2:-1])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("trace", ["rk3", "euler"])
+def test_linear_transport_exact(dim, trace):
+    """Linear phi under constant v is transported exactly; cross derivatives stay 0."""
+    n = 21 if dim == 2 else 11
+    g = oracle.grid((n,) * dim)
+    c = np.array([0.31, -0.17, 0.23])[:dim]
+    vel = oracle.velocity("const", c=tuple(c))
+    a = np.array([0.3, -0.7, 0.2])[:dim]
+    st = inputs.linear2d((n,) * 2, a=a) if dim == 2 else inputs.linear3d((n,) * 3, a=a)
+    dt = 0.02
+    out = oracle.step(g, vel, st, 0.0, dt, trace_scheme=trace)
+    X = inputs.node_coords((n,) * dim)
+    grids = np.meshgrid(*X[::-1], indexing="ij")[::-1]  # x fastest
+    phi_exact = sum(a[i] * (grids[i] - c[i] * dt) for i in range(dim)) + 0.1
+    # nodes whose foot lies inside the box
+    inside = np.ones(phi_exact.shape, bool)
+    for i in range(dim):
+        fi = grids[i] - c[i] * dt
+        inside &= (fi >= 0) & (fi <= 1)
+    assert np.max(np.abs(out[0] - phi_exact)[inside]) < 1e-13
+    for i in range(dim):
+        assert np.max(np.abs(out[1 + i] - a[i])) < 1e-12
+    assert np.max(np.abs(out[1 + dim:])) < 1e-10
+
+
+def test_cross_recon_exact_on_quadratic_gradients():
+    """Approach A (Sec. 2.3): central differences -- and the one-sided boundary
+    stencils -- are exact when the differenced gradient is quadratic along the axis:
+    phi = x^2 y^3 + x y^2 gives phi_xy exactly."""
+    n = (9, 13)
+    coef = np.zeros((3, 4))
+    coef[2, 3] = 1.0
+    coef[1, 2] = 1.0
+    st = inputs.polynomial2d(n, coef)
+    g = oracle.grid(n)
+    pxy_exact = st[3].copy()
+    st[3] = 0.0
+    rec = oracle.recon_cross(g, st)
+    assert np.max(np.abs(rec[3] - pxy_exact)) < 1e-12
+
+
+def test_cross_recon_3d_quadratic():
+    n = (7, 8, 9)
+    g = oracle.grid(n)
+    X, Y, Z = np.meshgrid(*inputs.node_coords(n)[::-1], indexing="ij")[::-1]
+    # phi = x^2 y^2 z^3 : psi_y = 2 x^2 y z^3 (quadratic in x), psi_z = 3 x^2 y^2 z^2
+    st = np.zeros((8,) + X.shape)
+    st[0] = X ** 2 * Y ** 2 * Z ** 3
+    st[1] = 2 * X * Y ** 2 * Z ** 3
+    st[2] = 2 * X ** 2 * Y * Z ** 3
+    st[3] = 3 * X ** 2 * Y ** 2 * Z ** 2
+    rec = oracle.recon_cross(g, st)
+    assert np.max(np.abs(rec[4] - 4 * X * Y * Z ** 3)) < 1e-12        # phi_xy
+    assert np.max(np.abs(rec[5] - 6 * X * Y ** 2 * Z ** 2)) < 1e-12   # phi_xz
+    assert np.max(np.abs(rec[6] - 6 * X ** 2 * Y * Z ** 2)) < 1e-12   # phi_yz
+    assert np.max(np.abs(rec[7] - 12 * X * Y * Z ** 2)) < 1e-12       # phi_xyz
+
+
+def test_step_nodes_equals_full_step():
+    n = (23, 19)
+    g = oracle.grid(n)
+    vel = oracle.velocity("vortex2d", T=8.0)
+    st = oracle.recon_cross(g, inputs.circle_sdf(n))
+    full = oracle.step(g, vel, st, 0.3, 0.04)
+    rng = np.random.default_rng(0)
+    sel = np.concatenate([[0, n[0] - 1, n[0] * n[1] - 1], rng.integers(0, n[0] * n[1], 30)])
+    part = oracle.step_nodes(g, vel, st, 0.3, 0.04, sel)
+    flat = full.reshape(4, -1)
+    assert np.array_equal(part, flat[:, sel].T)
+    g3 = oracle.grid((9, 8, 7))
+    vel3 = oracle.velocity("deform3d", T=3.0)
+    st3 = oracle.recon_cross(g3, inputs.sphere_sdf((9, 8, 7), center=(0.4, 0.5, 0.45), r=0.3))
+    full3 = oracle.step(g3, vel3, st3, 0.1, 0.05)
+    sel3 = np.array([0, 5, 77, 200, 503])
+    part3 = oracle.step_nodes(g3, vel3, st3, 0.1, 0.05, sel3)
+    assert np.array_equal(part3, full3.reshape(8, -1)[:, sel3].T)
+
+
+def _pseudo1d_solution(X, Y, t, x0=(0.5, 0.5)):
+    d = np.array([math.sqrt(2), math.sqrt(math.pi)]) / math.sqrt(2 + math.pi)
+    s = d[0] * X + d[1] * Y
+    sf = -np.log(np.exp(-s) + t)
+    dsf = np.exp(-s) / (np.exp(-s) + t)
+    FX, FY = X + (sf - s) * d[0], Y + (sf - s) * d[1]
+    e, gx, gy = inputs.gaussian_bump2d_exact(FX, FY, x0)
+    # grad phi(x,t) = (dX/dx)^T grad phi0(X), dX/dx = I + d d^T (dsf - 1)
+    m = dsf - 1
+    px = gx + d[0] * m * (d[0] * gx + d[1] * gy)
+    py = gy + d[1] * m * (d[0] * gx + d[1] * gy)
+    return e - math.exp(-0.15 ** 2), px, py
+
+
+def test_local_truncation_order_pseudo1d(golden):
+    """Sec. 6.1.1: 16 steps with dt = h/2 on the pseudo-1D flow; the error away
+    from the boundary converges with order 4 in phi and 3 in grad phi.  The
+    region [0.4, 0.7]^2 is outside the numerical domain of dependence of the
+    inflow edges and away from the one-sided cross stencils at the outflow edges
+    (the paper only says 'a part of the domain not influenced by the boundary')."""
+    vel = oracle.velocity("pseudo1d")
+    ephi, epsi = [], []
+    for n in (129, 257, 513):
+        h = 1.0 / (n - 1)
+        dt = h / 2
+        g = oracle.grid((n, n))
+        st = oracle.recon_cross(g, inputs.gaussian_bump2d((n, n)))
+        st = oracle.run(g, vel, st, 0.0, dt, 16)
+        X, Y = np.meshgrid(*inputs.node_coords((n, n)), indexing="xy")
+        ph, px, py = _pseudo1d_solution(X, Y, 16 * dt)
+        region = (X >= 0.4) & (Y >= 0.4) & (X <= 0.7) & (Y <= 0.7)
+        ephi.append(np.max(np.abs(st[0] - ph)[region]))
+        epsi.append(max(np.max(np.abs(st[1] - px)[region]), np.max(np.abs(st[2] - py)[region])))
+    o_phi = math.log2(ephi[-2] / ephi[-1])
+    o_psi = math.log2(epsi[-2] / epsi[-1])
+    assert golden["local_truncation_order"]["phi"] == 4
+    assert o_phi >= 3.7, (ephi, o_phi)
+    assert o_psi >= 2.7, (epsi, o_psi)
+
+
+@pytest.mark.slow
+def test_global_error_order_vortex(golden):
+    """Sec. 6.1.2: vortex in a box, dt = h, T = 2: the flow returns the data; the
+    error at t = T converges with order 3 in phi and 2 in grad phi."""
+    vel = oracle.velocity("vortex2d", T=2.0)
+    ephi, epsi = [], []
+    for n in (65, 129, 257):
+        h = 1.0 / (n - 1)
+        g = oracle.grid((n, n))
+        st0 = oracle.recon_cross(g, inputs.gaussian_bump2d((n, n), x0=(0.5, 0.75)))
+        st = oracle.run(g, vel, st0, 0.0, h, int(round(2.0 / h)))
+        ephi.append(oracle.emax(st[0], st0[0]))
+        epsi.append(max(oracle.emax(st[1], st0[1]), oracle.emax(st[2], st0[2])))
+    o_phi = math.log2(ephi[-2] / ephi[-1])
+    o_psi = math.log2(epsi[-2] / epsi[-1])
+    assert golden["global_error_order"] == {"cite": golden["global_error_order"]["cite"], "phi": 3, "psi": 2}
+    assert o_phi >= 2.7, (ephi, o_phi)
+    assert o_psi >= 1.7, (epsi, o_psi)
