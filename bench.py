@@ -1,0 +1,385 @@
+"""Benchmark of the GALS step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload vortex4096|rotation4096|deform512] [--layout full|compact]
+
+A bench step is one GALS time step (trace + Jacobian, Hermite evaluation, gradient
+write-back and mixed-derivative reconstruction) over the whole grid.  The default
+workload is the 4096^2 FP32 single-vortex case (state 4 float32 planes per node, 268 MB
+per buffer, larger than the 129 MB L2, so no flush is needed between steps).
+The K timed steps are issued as one gals_step call (a CUDA-graph replay), bracketed by
+CUDA events on the grid's stream.  Prints ONE JSON line.
+
+--impl reference times the FP64 CPU oracle (the reference of this method) on the host
+cores, on bounded row bands of the same workload.
+Under torchrun (N > 1) every rank advances an independent replica (the method runs on
+one GPU per problem; there is no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GALS node-updates/s and % of HBM roofline; learned vs plain trace at equal error"
+UNIT = "node-updates/s"
+
+WORKLOADS = {
+    # name: (dim, n, velocity kwargs, dt rule, description)
+    "vortex4096": dict(dim=2, n=(4096, 4096), vel=dict(kind="vortex2d", T=8.0), vmax=1.0,
+                       desc="2D GALS 4096x4096 nodes on [0,1]^2, FP32, single vortex T=8, "
+                            "circle SDF r=0.15 at (0.5,0.75), superconsistent RK3 trace, CFL 1"),
+    "rotation4096": dict(dim=2, n=(4096, 4096), vel=dict(kind="rotation", omega=2 * math.pi,
+                                                         center=(0.5, 0.5, 0.0)), vmax=math.pi,
+                         desc="2D GALS 4096x4096, FP32, Zalesak slotted disk in rigid rotation "
+                              "(omega=2pi about (0.5,0.5)), RK3 trace, CFL 1"),
+    "deform512": dict(dim=3, n=(512, 512, 512), vel=dict(kind="deform3d", T=3.0), vmax=2.0,
+                      desc="3D GALS 512^3 nodes on [0,1]^3, FP32, LeVeque deformation T=3, "
+                           "sphere SDF r=0.15 at (0.35,0.35,0.35), RK3 trace, CFL 1"),
+}
+
+
+def bytes_per_node(dim, layout):
+    """Algorithmic bytes per node update: the stored state read once and written once."""
+    planes = (4 if dim == 2 else 8) if layout == "full" else (3 if dim == 2 else 4)
+    return 2 * 4 * planes
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def initial_state(wl):
+    from paper_0905_3409_gb300 import inputs
+    n = wl["n"]
+    if wl["dim"] == 2:
+        if wl["vel"]["kind"] == "rotation":
+            st = inputs.slotted_disk_sdf(n)
+        else:
+            st = inputs.circle_sdf(n)
+    else:
+        st = inputs.sphere_sdf(n)
+    return st.astype(np.float32)
+
+
+def initial_state_cached(name, wl):
+    """The 512^3 signed distance takes a while in numpy; cache it per process run."""
+    return initial_state(wl)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            if len(s) < 9:
+                continue
+            for nm, v in zip(names, s[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0905_3409_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, layout):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{workload}/{layout}")
+    if not e or e.get("kernel_sources") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------- CPU oracle leg
+
+def oracle_leg(wl, budget_s=12.0, max_bands=None):
+    """Time the FP64 oracle on row bands (2D) / z-slabs (3D) of the workload: each band
+    is an exact, independent part of one step.  Returns (node-updates/s, cores, sample)."""
+    import oracle
+    n = wl["n"]
+    st = initial_state(wl).astype(np.float64)
+    from paper_0905_3409_gb300 import inputs  # noqa: F401
+    if wl["dim"] == 2:
+        from paper_0905_3409_gb300.inputs import node_coords  # noqa: F401
+    g = oracle.grid(n)
+    st = oracle.recon_cross(g, st) if wl["dim"] == 2 else st
+    v = wl["vel"]
+    ov = oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
+                         center=v.get("center", (0.5, 0.5, 0.5)))
+    h = 1.0 / (n[0] - 1)
+    dt = h / wl["vmax"]
+    planes = oracle.state_planes(g, st)
+    cores = oracle.default_threads()
+    outer = n[-1]
+    inner_nodes = int(np.prod(n[:-1]))
+    band = 64 if wl["dim"] == 2 else 2
+    done = 0
+    nodes = 0
+    t0 = time.perf_counter()
+    b0 = outer // 3
+    while True:
+        oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes)
+        nodes += band * inner_nodes
+        done += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or (max_bands and done >= max_bands):
+            break
+        b0 = (b0 + band) % (outer - band)
+    return nodes / el, cores, f"{done} bands of {band} {'rows' if wl['dim'] == 2 else 'z-slices'} " \
+                              f"({nodes} node updates, one step each) of the {n} grid in {el:.1f} s"
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n = wl["n"]
+    g = oracle.grid(n)
+    st = initial_state(wl).astype(np.float64)
+    if wl["dim"] == 2:
+        st = oracle.recon_cross(g, st)
+    v = wl["vel"]
+    ov = oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
+                         center=v.get("center", (0.5, 0.5, 0.5)))
+    h = 1.0 / (n[0] - 1)
+    dt = h / wl["vmax"]
+    planes = oracle.state_planes(g, st)
+    outer = n[-1]
+    inner_nodes = int(np.prod(n[:-1]))
+    # each reference step: one band of the grid, sized to keep the run within minutes
+    band = 8 if wl["dim"] == 2 else 1
+    for s in range(args.warmup):
+        oracle.step_band(g, ov, None, 0.0, dt, (s * band) % (outer - band), (s * band) % (outer - band) + band,
+                         planes=planes)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        b0 = (outer // 4 + s * band) % (outer - band)
+        oracle.step_band(g, ov, None, s * dt, dt, b0, b0 + band, planes=planes)
+    el = time.perf_counter() - t0
+    nodes = args.steps * band * inner_nodes
+    value = nodes / el
+    cores = oracle.default_threads()
+    sample = f"each step: one band of {band} {'rows' if wl['dim'] == 2 else 'z-slices'} " \
+             f"({band * inner_nodes} node updates) of the {n} grid"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"] + " (FP64 CPU oracle)", "nodes_per_step_sample": band * inner_nodes},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------- GPU leg
+
+def run_ours(args, wl):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if dist:
+        dist.barrier()
+    from paper_0905_3409_gb300 import gals
+
+    n = wl["n"]
+    dim = wl["dim"]
+    nodes = int(np.prod(n))
+    h = 1.0 / (n[0] - 1)
+    dt = h / wl["vmax"]
+    vel = gals.Velocity(trace="rk3", **wl["vel"])
+    st_host = initial_state(wl)
+    stream = torch.cuda.Stream()
+    g = gals.Grid(n, layout=args.layout, stream=stream)
+    g.set_state(st_host, t0=0.0, recon=True)
+
+    # warm-up (also captures the CUDA graph for K steps)
+    g.step(vel, dt, args.warmup)
+    g.step(vel, dt, args.steps)
+    g.synchronize()
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(vel, dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if rank == 0 else None
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = nodes * args.steps * world / (ms * 1e-3)
+
+    # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels)
+    launches_per_step = 2 if args.layout == "full" else 1
+    bpn = bytes_per_node(dim, args.layout)
+    step_s = ms * 1e-3 / args.steps
+    achieved = bpn * nodes / step_s / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # e2e through the C ABI with host buffers: per step, pinned host -> device state,
+    # one step, device -> pinned host state
+    nplanes = 4 if dim == 2 else 8
+    pin_in = torch.from_numpy(st_host).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    e2e_steps = max(1, min(args.steps, 20))
+    g2 = gals.Grid(n, layout=args.layout, stream=stream)
+    g2.set_state(pin_in.numpy(), recon=False)
+    g2.step(vel, dt, 1)
+    g2.read_state(pin_out.numpy())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g2.set_state(pin_in.numpy(), recon=False)
+        g2.step(vel, dt, 1)
+        g2.read_state(pin_out.numpy())
+    el = time.perf_counter() - t0
+    el_t = torch.tensor([el], device="cuda")
+    if dist:
+        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+    el = float(el_t.item())
+    e2e_value = nodes * e2e_steps * world / el
+    io_bytes = nplanes * 4 * nodes
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "layout": args.layout, "nodes": nodes,
+                       "dt": dt, "bytes_per_node_update": bpn,
+                       "l2": f"inputs larger than L2 ({nodes * nplanes * 4 / 1e6:.0f} MB state per buffer)",
+                       "parallelism": f"{world} independent replica(s), one per GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(args.workload, args.layout),
+                         "peak_source": peak_kind,
+                         "kernel": f"gals step ({launches_per_step} launch(es) per step)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": args.steps * launches_per_step + 1,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, cores, sample = oracle_leg(wl, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line))
+    g.close()
+    g2.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="vortex4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--layout", default="full", choices=["full", "compact"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

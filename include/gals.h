@@ -1,0 +1,188 @@
+/*
+ * gals.h -- C ABI of the GB300 gradient-augmented level set (GALS) library.
+ *
+ * The library advances a level set function phi together with its gradient
+ * psi = grad phi on a uniform grid with the gradient-augmented CIR scheme of Nave,
+ * Rosales and Seibold (arXiv 0905.3409): for every grid node the characteristic is
+ * traced back one time step with the superconsistent Shu-Osher RK3 scheme and the
+ * Jacobian of that backward map (Sec. 5.1, Ex. "superconsistent Shu-Osher"); the
+ * bi-/tri-cubic Hermite interpolant of the cell containing the foot point
+ * (Sec. 2.3, eq. p-cubic_interpolant) gives phi+ = H(foot) and psi+ = J^T grad H(foot)
+ * (eq. superconsistency); the mixed derivatives the interpolant needs are rebuilt
+ * from the new gradients by central differences (Sec. 2.3, approach A).
+ *
+ * All arithmetic of a step runs in hand-written CUDA kernels for sm_103a, in FP32;
+ * diagnostics accumulate in FP64 or exact integers.  There is no CPU fallback.
+ *
+ * Conventions for every call:
+ *   - Every function returns gals_status: GALS_OK (0) or a negative error code.
+ *     No exception or signal crosses the ABI.  gals_last_error() gives a message.
+ *   - Grid data are SoA FP32 planes, x fastest: node (i,j,k) of a plane is element
+ *     (k*n[1] + j)*n[0] + i of a dense array of n[0]*n[1]*n[2] floats (n[2] = 1 in 2D).
+ *   - Plane order: 2D  phi, phi_x, phi_y, phi_xy
+ *                  3D  phi, phi_x, phi_y, phi_z, phi_xy, phi_xz, phi_yz, phi_xyz.
+ *   - Device pointers must be memory of the current CUDA device, 4-byte aligned.
+ *   - Work is ordered on the grid's CUDA stream.  gals_step returns before the GPU
+ *     has finished; errors of asynchronous work surface at the next synchronising
+ *     call (gals_read_state, gals_diagnostics, gals_synchronize).
+ *   - Handles are not thread-safe: use one handle per host thread.
+ */
+#ifndef GALS_H
+#define GALS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GALS_OK = 0,
+    GALS_ERR_ARG = -1,         /* invalid argument (null, size, range, non-finite) */
+    GALS_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    GALS_ERR_NOMEM = -3,       /* device allocation failed */
+    GALS_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out */
+    GALS_ERR_NONFINITE = -5,   /* non-finite values found where finite ones are required */
+    GALS_ERR_STATE = -6,       /* call out of order (e.g. step before set_state) */
+    GALS_ERR_UNSUPPORTED = -7  /* combination of options not implemented */
+} gals_status;
+
+enum { GALS_MEM_HOST = 0, GALS_MEM_DEVICE = 1 };
+
+/* Storage of the mixed derivatives between steps.
+ *   FULL     all 4 (2D) / 8 (3D) planes are written every step (the paper's stored
+ *            representation, Sec. 5.2: the projection keeps per-node cross derivatives).
+ *   COMPACT  only phi and psi are kept in memory between steps; the mixed derivatives
+ *            are rebuilt from psi by the same central differences each time they are
+ *            needed.  Results are bit-identical to FULL; it moves 24 instead of 32 bytes
+ *            per 2D node update (32 instead of 64 in 3D). */
+enum { GALS_LAYOUT_FULL = 0, GALS_LAYOUT_COMPACT = 1 };
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int n[3];           /* nodes per axis including both ends, each >= 4 (n[2] ignored in 2D) */
+    double lo[3];       /* domain [lo, hi] per axis; node spacing h = (hi - lo)/(n - 1) */
+    double hi[3];
+    int layout;         /* GALS_LAYOUT_FULL (default 0) or GALS_LAYOUT_COMPACT */
+    void *cuda_stream;  /* cudaStream_t to order work on, or NULL for a library-owned stream */
+} gals_grid_desc;
+
+/* Analytic velocity fields v(x, t) with exactly known Jacobian (Sec. 4 assumes both
+ * "exactly accessible everywhere").  Coordinates are physical (not index) units. */
+enum {
+    GALS_VEL_CONST = 0,     /* v = c */
+    GALS_VEL_ROTATION = 1,  /* rigid rotation about center with angular speed omega, w = 0 */
+    GALS_VEL_VORTEX2D = 2,  /* v = (-Psi_y, Psi_x), Psi = (1/pi)cos(pi t/T) sin^2(pi x) sin^2(pi y) (Sec. 6.1.2) */
+    GALS_VEL_DEFORM3D = 3,  /* u = 2 sin^2(pi x) sin(2 pi y) sin(2 pi z), v = -sin(2 pi x) sin^2(pi y) sin(2 pi z),
+                               w = -sin(2 pi x) sin(2 pi y) sin^2(pi z), all times cos(pi t/T) (Sec. 6.2.4) */
+    GALS_VEL_PSEUDO1D = 4,  /* eq. velocity_1 (Sec. 6.1.1) */
+    GALS_VEL_FOURIER2D = 5  /* v = (-Psi_y, Psi_x), Psi = sum_m a_m sin(k_m pi x) sin(l_m pi y) cos(2 pi n_m t + chi_m) */
+};
+
+/* Backward trace of one step. */
+enum {
+    GALS_TRACE_EULER = 0,   /* superconsistent forward Euler (Sec. 5.1, first order) */
+    GALS_TRACE_RK3 = 1      /* superconsistent Shu-Osher RK3 (Sec. 5.1), the default of Sec. 6 */
+};
+
+#define GALS_MAX_MODES 64
+
+typedef struct {
+    int kind;               /* GALS_VEL_* */
+    int trace;              /* GALS_TRACE_* */
+    double T;               /* modulation period of VORTEX2D / DEFORM3D */
+    double omega;           /* ROTATION angular speed (counter-clockwise) */
+    double center[3];       /* ROTATION center */
+    double c[3];            /* CONST velocity */
+    int nmodes;             /* FOURIER2D: number of modes, 1..GALS_MAX_MODES */
+    const double *modes;    /* FOURIER2D: host array of nmodes rows (a, k, l, n, chi); k, l integers
+                               in 1..4, n >= 0.  Copied during the call. */
+} gals_velocity;
+
+typedef struct gals_grid gals_grid;   /* opaque, owned by the library */
+
+/* Create a grid and allocate its double-buffered device state on the current device.
+ * Errors: GALS_ERR_ARG (dim not 2/3, n < 4, hi <= lo, bad layout), GALS_ERR_NOMEM,
+ * GALS_ERR_CUDA.  On error *out is set to NULL. */
+gals_status gals_create_grid(const gals_grid_desc *desc, gals_grid **out);
+
+/* Free the grid's device memory and stream (if library-owned).  NULL is accepted. */
+gals_status gals_destroy_grid(gals_grid *grid);
+
+/* Flags of gals_set_state. */
+enum { GALS_SET_RECON_CROSS = 1 };  /* rebuild the mixed derivatives from the given gradients */
+
+/* Load the state at time t0.  fields[p] points to plane p (layout above) in host or
+ * device memory (memspace); the data are copied and the caller keeps ownership.
+ * nfields = 1 + dim (phi and gradient; the mixed derivatives are then rebuilt from the
+ * gradients, Sec. 2.3 approach A) or all planes (4 in 2D, 8 in 3D), whose mixed
+ * derivatives are used as given unless flags has GALS_SET_RECON_CROSS.
+ * The copy is stream-ordered; host sources are read before the call returns.
+ * Errors: GALS_ERR_ARG (null pointers, wrong nfields, memspace), GALS_ERR_CUDA. */
+gals_status gals_set_state(gals_grid *grid, const float *const *fields, int nfields,
+                           int memspace, double t0, int flags);
+
+/* Advance nsteps steps of size dt from the grid's current time (Sec. 4 steps 1-3 in the
+ * superconsistent form of Sec. 5.1; M = P A of Sec. 5.2).  Step s uses the velocity at
+ * the stage times of the step from t0 + s*dt.  Feet outside the box are clamped into it
+ * (outflow or tangential boundaries need no data, Sec. 4.1).  nsteps > 1 is replayed
+ * from a cached CUDA graph.  Asynchronous on the grid stream.
+ * Errors: GALS_ERR_ARG (dt <= 0 or non-finite, nsteps < 0, bad velocity descriptor),
+ * GALS_ERR_STATE (no state loaded), GALS_ERR_UNSUPPORTED (velocity kind not available in
+ * this dimension), GALS_ERR_CUDA (launch failure). */
+gals_status gals_step(gals_grid *grid, const gals_velocity *vel, double dt, int nsteps);
+
+/* Copy the current state out (all planes, or the first nfields).  In the COMPACT layout
+ * the mixed derivatives are rebuilt first.  Synchronises the grid stream.
+ * Errors: GALS_ERR_ARG, GALS_ERR_STATE, GALS_ERR_CUDA. */
+gals_status gals_read_state(gals_grid *grid, float *const *fields, int nfields, int memspace);
+
+/* Diagnostics of the current state (Sec. 6: e_max of eq. maximum_norm, volume loss
+ * tables).  The interpolant is sampled at q^p cell-centred points per cell
+ * (xi = (s + 1/2)/q); counts are exact integers, norms accumulate in FP64. */
+typedef struct {
+    int q;                         /* samples per cell and axis, 1..16 (0: no sampling) */
+    const gals_grid *reference;    /* optional grid of the same shape: symmetric difference of
+                                      {H < 0} and error norms against it */
+} gals_diag_request;
+
+typedef struct {
+    double t;                      /* grid time */
+    int64_t steps;                 /* steps taken since the last set_state */
+    int64_t samples;               /* number of sample points (cells * q^p) */
+    int64_t n_negative;            /* samples with H < 0 */
+    double measure_negative;       /* area (2D) / volume (3D) of {H < 0} = n_negative * cell / q^p */
+    int64_t n_symdiff;             /* samples where sign(H < 0) differs from the reference */
+    double measure_symdiff;        /* its area / volume (interface-location error numerator) */
+    double emax_phi;               /* max |phi - phi_ref| over nodes (eq. maximum_norm) */
+    double emax_psi;               /* max over nodes of max_i |psi_i - psi_ref_i| */
+    double l2_phi;                 /* sqrt(sum (phi - phi_ref)^2 * cell) in FP64 */
+    int64_t nonfinite;             /* nodes with a non-finite value in any plane */
+} gals_diag;
+
+/* Errors: GALS_ERR_ARG (q out of range, reference of another shape), GALS_ERR_STATE,
+ * GALS_ERR_NOMEM, GALS_ERR_CUDA.  Synchronises the grid stream. */
+gals_status gals_diagnostics(gals_grid *grid, const gals_diag_request *req, gals_diag *out);
+
+/* Wait for the grid's stream; returns the first asynchronous error, if any. */
+gals_status gals_synchronize(gals_grid *grid);
+
+/* Current grid time (host copy; advanced by gals_step at issue). */
+double gals_time(const gals_grid *grid);
+
+/* Device pointers of the current state planes (for zero-copy consumers); valid until
+ * the next gals_step.  In the COMPACT layout the mixed-derivative planes are only valid
+ * after gals_read_state.  Errors: GALS_ERR_ARG. */
+gals_status gals_state_planes(gals_grid *grid, float **planes, int nplanes, int64_t *row_pitch);
+
+/* Message of the last error on this grid (or of the last failed create if grid is NULL).
+ * The pointer stays valid until the next call on the same grid. */
+const char *gals_last_error(const gals_grid *grid);
+
+/* Library version string. */
+const char *gals_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GALS_H */

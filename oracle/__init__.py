@@ -90,6 +90,10 @@ def lib():
                                          ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, pp, ctypes.c_long,
                                          ctypes.POINTER(ctypes.c_long), dp, ctypes.c_int]
+            L.orc_step_band.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Velocity),
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, pp, ctypes.c_int, ctypes.c_int, pp,
+                                        ctypes.c_int]
             L.orc_run.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Velocity), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   pp, pp, ctypes.c_int]
@@ -262,6 +266,26 @@ def step_nodes(g, vel, state, t, dt, nodes, trace_scheme="rk3", cross="central",
                          sel.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out),
                          default_threads() if nthreads is None else int(nthreads))
     return out
+
+
+def step_band(g, vel, state, t, dt, b0, b1, trace_scheme="rk3", cross="central", nthreads=None,
+              planes=None):
+    """New state of the outermost-axis band [b0, b1) (rows in 2D, z-slices in 3D);
+    returns (nplanes, b1-b0, ...) with the inner axes of the grid.  ``planes``: the
+    state already split by ``state_planes`` (avoids re-copying a large state)."""
+    ins = planes if planes is not None else _state_list(state, g)
+    inner = (g.n[0],) if g.dim == 2 else (g.n[1], g.n[0])
+    outs = [np.empty((b1 - b0) * int(np.prod(inner))) for _ in ins]
+    lib().orc_step_band(ctypes.byref(g), ctypes.byref(vel), _TRACE_NAMES[trace_scheme],
+                        CROSS_CENTRAL if cross == "central" else CROSS_ZERO, float(t), float(dt),
+                        _planes_ptr(ins), int(b0), int(b1), _planes_ptr(outs),
+                        default_threads() if nthreads is None else int(nthreads))
+    return np.stack(outs).reshape((len(ins), b1 - b0) + inner)
+
+
+def state_planes(g, state):
+    """Split a state into the contiguous FP64 planes the C calls take."""
+    return _state_list(state, g)
 
 
 def run(g, vel, state, t0, dt, nsteps, trace_scheme="rk3", cross="central", nthreads=None):

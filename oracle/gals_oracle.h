@@ -100,6 +100,13 @@ void orc_step_nodes(const orc_grid *g, const orc_velocity *vel, int trace, int c
                     double t, double dt, const double *const *in, long nsel,
                     const long *sel, double *outv, int nthreads);
 
+/* new state of a band of the outermost axis only: rows [b0,b1) in 2D, z-slices in 3D
+ * (the cross stencils never leave a row / slice, so the band is exact); out planes hold
+ * the band's nodes contiguously */
+void orc_step_band(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
+                   double t, double dt, const double *const *in, int b0, int b1,
+                   double *const *out, int nthreads);
+
 /* nsteps steps with ping-pong buffers; final state in `state` */
 void orc_run(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
              double t0, double dt, int nsteps, double *const *state,

@@ -267,3 +267,54 @@ void orc_run(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
     if (a[0] != state[0])
         for (int p = 0; p < np; ++p) memcpy(state[p], a[p], N * sizeof(double));
 }
+
+/* band of the outermost axis (rows j in [b0,b1) in 2D, slices k in [b0,b1) in 3D): the
+ * approach-A stencils difference along x (and y in 3D) only, so a band is updated
+ * exactly from the old state alone.  out planes hold the band's nodes contiguously. */
+typedef struct { const orc_grid *g; double *const *planes; int b0; } band_ctx;
+
+static double get_band(void *vctx, int plane, int i, int j, int k)
+{
+    band_ctx *c = (band_ctx *)vctx;
+    const orc_grid *g = c->g;
+    long id = g->dim == 2 ? (long)(j - c->b0) * g->n[0] + i
+                          : ((long)(k - c->b0) * g->n[1] + j) * g->n[0] + i;
+    return c->planes[plane][id];
+}
+
+void orc_step_band(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
+                   double t, double dt, const double *const *in, int b0, int b1,
+                   double *const *out, int nthreads)
+{
+    int dim = g->dim;
+    int inner = dim == 2 ? 1 : g->n[1];
+    long lines = (long)(b1 - b0) * inner;
+    (void)nthreads;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (long r = 0; r < lines; ++r) {
+        int outer = b0 + (int)(r / inner), jj = (int)(r % inner);
+        int j = dim == 2 ? outer : jj, k = dim == 2 ? 0 : outer;
+        for (int i = 0; i < g->n[0]; ++i) {
+            double phi, psi[3];
+            orc_node_update(g, vel, trace, t, dt, in, i, j, k, &phi, psi);
+            long id = r * g->n[0] + i;
+            out[0][id] = phi;
+            for (int a = 0; a < dim; ++a) out[1 + a][id] = psi[a];
+        }
+    }
+    int first = dim == 2 ? 3 : 4, nc = dim == 2 ? 1 : 4;
+    band_ctx ctx = {g, out, b0};
+    for (long r = 0; r < lines; ++r) {
+        int outer = b0 + (int)(r / inner), jj = (int)(r % inner);
+        int j = dim == 2 ? outer : jj, k = dim == 2 ? 0 : outer;
+        for (int i = 0; i < g->n[0]; ++i) {
+            double cr[4] = {0, 0, 0, 0};
+            if (cross != ORC_CROSS_ZERO) cross_at(g, get_band, &ctx, i, j, k, cr);
+            long id = r * g->n[0] + i;
+            for (int c = 0; c < nc; ++c) out[first + c][id] = cr[c];
+        }
+    }
+}

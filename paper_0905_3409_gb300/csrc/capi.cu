@@ -1,0 +1,456 @@
+// capi.cu -- implementation of the C ABI declared in include/gals.h.
+//
+// A grid owns two device state buffers (A/B ping-pong), each holding all planes of the
+// state in SoA form with a row pitch that is a multiple of 4 floats (16-byte rows).
+// gals_step issues one kernel launch per step (plus the approach-A reconstruction in the
+// FULL layout); runs of more than one step are captured once into a CUDA graph and
+// replayed.  The grid time lives on the device too, so a cached graph is valid for any
+// start time: step s of a call reads t = t_dev + s*dt, and the graph ends by advancing
+// t_dev.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gals.h"
+#include "gals_internal.h"
+
+using namespace gals;
+
+namespace {
+
+char g_create_err[256] = "";
+
+struct GraphEntry {
+    // key
+    int nsteps, cur, first_explicit, trace, layout;
+    double dt;
+    VelParams vp;
+    // value
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct gals_grid {
+    int dim = 0;
+    int n[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+    int layout = GALS_LAYOUT_FULL;
+    int nplanes = 0;
+    Geom geom{};
+    float *buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool has_state = false;
+    bool cross_explicit = false;  // COMPACT: buffer cur holds given mixed derivatives to use once
+    double t = 0.0;
+    int64_t steps = 0;
+    double *t_dev = nullptr;
+    DiagOut *diag_dev = nullptr;
+    double *diag_partials = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<GraphEntry> graphs;
+    char err[256] = "";
+};
+
+namespace {
+
+gals_status fail(gals_grid *g, gals_status st, const char *fmt, ...)
+{
+    char *dst = g ? g->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+gals_status cuda_fail(gals_grid *g, cudaError_t e, const char *what)
+{
+    return fail(g, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+int full_planes(int dim) { return dim == 2 ? 4 : 8; }
+
+bool finite3(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+gals_status make_velparams(gals_grid *g, const gals_velocity *v, VelParams &vp)
+{
+    std::memset(&vp, 0, sizeof(vp));
+    if (!v) return fail(g, GALS_ERR_ARG, "velocity descriptor is NULL");
+    if (v->trace != GALS_TRACE_EULER && v->trace != GALS_TRACE_RK3)
+        return fail(g, GALS_ERR_ARG, "unknown trace scheme %d", v->trace);
+    if (!vel_supported(g->dim, v->kind))
+        return fail(g, GALS_ERR_UNSUPPORTED, "velocity kind %d not available in %dD", v->kind, g->dim);
+    if (!finite3(v->c, 3) || !finite3(v->center, 3) || !std::isfinite(v->omega) || !std::isfinite(v->T))
+        return fail(g, GALS_ERR_ARG, "non-finite velocity parameter");
+    vp.kind = v->kind;
+    vp.omega = (float)v->omega;
+    vp.cx = (float)v->center[0]; vp.cy = (float)v->center[1]; vp.cz = (float)v->center[2];
+    vp.c0 = (float)v->c[0]; vp.c1 = (float)v->c[1]; vp.c2 = (float)v->c[2];
+    const double nrm = std::sqrt(2.0 + M_PI);
+    vp.d0 = (float)(std::sqrt(2.0) / nrm);
+    vp.d1 = (float)(std::sqrt(M_PI) / nrm);
+    if (v->kind == GALS_VEL_VORTEX2D || v->kind == GALS_VEL_DEFORM3D) {
+        if (!(v->T > 0.0)) return fail(g, GALS_ERR_ARG, "modulation period T must be > 0");
+        vp.invT = 1.0 / v->T;
+    }
+    if (v->kind == GALS_VEL_FOURIER2D) {
+        if (v->nmodes < 1 || v->nmodes > GALS_MAX_MODES || !v->modes)
+            return fail(g, GALS_ERR_ARG, "FOURIER2D needs 1..%d modes", GALS_MAX_MODES);
+        vp.nmodes = v->nmodes;
+        for (int m = 0; m < v->nmodes; ++m) {
+            const double *md = v->modes + 5 * m;
+            if (!finite3(md, 5)) return fail(g, GALS_ERR_ARG, "non-finite mode %d", m);
+            int k = (int)md[1], l = (int)md[2];
+            if (k != md[1] || l != md[2] || k < 1 || k > 4 || l < 1 || l > 4)
+                return fail(g, GALS_ERR_ARG, "mode %d: k, l must be integers in 1..4", m);
+            if (md[3] < 0) return fail(g, GALS_ERR_ARG, "mode %d: n must be >= 0", m);
+            vp.mode_a[m] = (float)md[0];
+            vp.mode_kl[m] = k | (l << 8);
+            vp.mode_n[m] = md[3];
+            vp.mode_chi[m] = md[4] / (2.0 * M_PI);
+        }
+    }
+    return GALS_OK;
+}
+
+cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt, int nsteps,
+                        bool first_explicit)
+{
+    int cur = g->cur;
+    for (int s = 0; s < nsteps; ++s) {
+        StepLaunch a;
+        a.in = g->buf[cur];
+        a.out = g->buf[cur ^ 1];
+        a.geom = g->geom;
+        a.vp = vp;
+        a.t_dev = g->t_dev;
+        a.kstep = s;
+        a.dt = dt;
+        a.trace = trace == GALS_TRACE_EULER ? TR_EULER : TR_RK3;
+        if (g->layout == GALS_LAYOUT_FULL) {
+            a.cross_in = CROSS_PLANE;
+            a.write_cross = 1;
+        } else {
+            a.cross_in = (s == 0 && first_explicit) ? CROSS_PLANE : CROSS_RECON;
+            a.write_cross = 0;
+        }
+        cudaError_t e = g->dim == 2 ? launch_step2d(a, g->stream) : launch_step3d(a, g->stream);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return launch_advance_time(g->t_dev, nsteps, dt, g->stream);
+}
+
+bool same_key(const GraphEntry &e, int nsteps, int cur, int fe, int trace, int layout, double dt,
+              const VelParams &vp)
+{
+    return e.nsteps == nsteps && e.cur == cur && e.first_explicit == fe && e.trace == trace &&
+           e.layout == layout && e.dt == dt && std::memcmp(&e.vp, &vp, sizeof(vp)) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gals_version(void) { return "gals-gb300 0.1 (sm_103a)"; }
+
+const char *gals_last_error(const gals_grid *g) { return g ? g->err : g_create_err; }
+
+double gals_time(const gals_grid *g) { return g ? g->t : 0.0; }
+
+gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
+{
+    if (!out) return fail(nullptr, GALS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(nullptr, GALS_ERR_ARG, "descriptor is NULL");
+    if (d->dim != 2 && d->dim != 3) return fail(nullptr, GALS_ERR_ARG, "dim must be 2 or 3");
+    if (d->layout != GALS_LAYOUT_FULL && d->layout != GALS_LAYOUT_COMPACT)
+        return fail(nullptr, GALS_ERR_ARG, "unknown layout %d", d->layout);
+    for (int i = 0; i < d->dim; ++i) {
+        if (d->n[i] < 4) return fail(nullptr, GALS_ERR_ARG, "n[%d] = %d < 4", i, d->n[i]);
+        if (!std::isfinite(d->lo[i]) || !std::isfinite(d->hi[i]) || !(d->hi[i] > d->lo[i]))
+            return fail(nullptr, GALS_ERR_ARG, "axis %d: need finite lo < hi", i);
+    }
+    gals_grid *g = new (std::nothrow) gals_grid();
+    if (!g) return fail(nullptr, GALS_ERR_NOMEM, "host allocation failed");
+    g->dim = d->dim;
+    g->layout = d->layout;
+    g->nplanes = full_planes(d->dim);
+    for (int i = 0; i < 3; ++i) {
+        g->n[i] = i < d->dim ? d->n[i] : 1;
+        g->lo[i] = i < d->dim ? d->lo[i] : 0.0;
+        g->hi[i] = i < d->dim ? d->hi[i] : 1.0;
+        g->h[i] = i < d->dim ? (g->hi[i] - g->lo[i]) / (g->n[i] - 1) : 1.0;
+    }
+    Geom &G = g->geom;
+    G.n0 = g->n[0]; G.n1 = g->n[1]; G.n2 = g->n[2];
+    G.pitch = (g->n[0] + 3) / 4 * 4;
+    const int64_t plane = (int64_t)G.pitch * G.n1 * G.n2;
+    G.plane = (plane + 63) / 64 * 64;  // 256-byte aligned planes
+    G.h0 = (float)g->h[0]; G.h1 = (float)g->h[1]; G.h2 = (float)g->h[2];
+    G.ih0 = (float)(1.0 / g->h[0]); G.ih1 = (float)(1.0 / g->h[1]); G.ih2 = (float)(1.0 / g->h[2]);
+    G.i2h0 = (float)(0.5 / g->h[0]); G.i2h1 = (float)(0.5 / g->h[1]); G.i2h2 = (float)(0.5 / g->h[2]);
+    G.lo0 = (float)g->lo[0]; G.lo1 = (float)g->lo[1]; G.lo2 = (float)g->lo[2];
+
+    cudaError_t e;
+    if (d->cuda_stream) {
+        g->stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            gals_status st = cuda_fail(nullptr, e, "cudaStreamCreate");
+            delete g;
+            return st;
+        }
+        g->own_stream = true;
+    }
+    const size_t bytes = (size_t)G.plane * g->nplanes * sizeof(float);
+    for (int b = 0; b < 2; ++b) {
+        if ((e = cudaMalloc(&g->buf[b], bytes)) != cudaSuccess) {
+            gals_status st = cuda_fail(nullptr, e, "cudaMalloc(state)");
+            gals_destroy_grid(g);
+            return st;
+        }
+    }
+    if ((e = cudaMalloc(&g->t_dev, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g->diag_dev, sizeof(DiagOut))) != cudaSuccess ||
+        (e = cudaMalloc(&g->diag_partials, sizeof(double) * diag_partials_needed())) != cudaSuccess) {
+        gals_status st = cuda_fail(nullptr, e, "cudaMalloc(aux)");
+        gals_destroy_grid(g);
+        return st;
+    }
+    // zero both buffers so that pitch padding never holds garbage
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaMemsetAsync(g->buf[b], 0, bytes, g->stream)) != cudaSuccess) {
+            gals_status st = cuda_fail(nullptr, e, "cudaMemset");
+            gals_destroy_grid(g);
+            return st;
+        }
+    *out = g;
+    return GALS_OK;
+}
+
+gals_status gals_destroy_grid(gals_grid *g)
+{
+    if (!g) return GALS_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+    for (int b = 0; b < 2; ++b) cudaFree(g->buf[b]);
+    cudaFree(g->t_dev);
+    cudaFree(g->diag_dev);
+    cudaFree(g->diag_partials);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return GALS_OK;
+}
+
+gals_status gals_set_state(gals_grid *g, const float *const *fields, int nfields, int memspace,
+                           double t0, int flags)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!fields) return fail(g, GALS_ERR_ARG, "fields is NULL");
+    const int core = 1 + g->dim;
+    if (nfields != core && nfields != g->nplanes)
+        return fail(g, GALS_ERR_ARG, "nfields must be %d or %d", core, g->nplanes);
+    if (memspace != GALS_MEM_HOST && memspace != GALS_MEM_DEVICE)
+        return fail(g, GALS_ERR_ARG, "bad memspace %d", memspace);
+    if (!std::isfinite(t0)) return fail(g, GALS_ERR_ARG, "t0 is not finite");
+    for (int p = 0; p < nfields; ++p)
+        if (!fields[p]) return fail(g, GALS_ERR_ARG, "fields[%d] is NULL", p);
+    const Geom &G = g->geom;
+    const size_t row = (size_t)g->n[0] * sizeof(float);
+    const size_t rows = (size_t)g->n[1] * g->n[2];
+    const cudaMemcpyKind kind = memspace == GALS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    float *dst = g->buf[g->cur];
+    cudaError_t e;
+    for (int p = 0; p < nfields; ++p) {
+        e = cudaMemcpy2DAsync(dst + p * G.plane, (size_t)G.pitch * sizeof(float), fields[p], row, row,
+                              rows, kind, g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "set_state copy");
+    }
+    const bool recon = nfields == core || (flags & GALS_SET_RECON_CROSS);
+    if (recon) {
+        if ((e = launch_recon(g->dim, G, dst, g->stream)) != cudaSuccess) return cuda_fail(g, e, "recon");
+    }
+    g->cross_explicit = (g->layout == GALS_LAYOUT_COMPACT) && !recon;
+    g->t = t0;
+    g->steps = 0;
+    if ((e = cudaMemcpyAsync(g->t_dev, &g->t, sizeof(double), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+        return cuda_fail(g, e, "set time");
+    // the sources and the host time word must be consumed before returning
+    if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "set_state sync");
+    g->has_state = true;
+    return GALS_OK;
+}
+
+gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nsteps)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(g, GALS_ERR_ARG, "dt must be finite and > 0");
+    if (nsteps < 0) return fail(g, GALS_ERR_ARG, "nsteps must be >= 0");
+    VelParams vp;
+    gals_status st = make_velparams(g, v, vp);
+    if (st != GALS_OK) return st;
+    if (nsteps == 0) return GALS_OK;
+    const bool fe = g->cross_explicit;
+    cudaError_t e;
+    if (nsteps == 1) {
+        if ((e = issue_steps(g, vp, v->trace, dt, 1, fe)) != cudaSuccess) return cuda_fail(g, e, "step launch");
+    } else {
+        GraphEntry *hit = nullptr;
+        for (auto &ge : g->graphs)
+            if (same_key(ge, nsteps, g->cur, fe, v->trace, g->layout, dt, vp)) { hit = &ge; break; }
+        if (!hit) {
+            cudaGraph_t graph;
+            if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(g, e, "begin capture");
+            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe);
+            e = cudaStreamEndCapture(g->stream, &graph);
+            if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
+            if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
+            cudaGraphExec_t exec;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+            if (g->graphs.size() >= 8) {
+                cudaGraphExecDestroy(g->graphs.front().exec);
+                g->graphs.erase(g->graphs.begin());
+            }
+            GraphEntry ge;
+            ge.nsteps = nsteps; ge.cur = g->cur; ge.first_explicit = fe; ge.trace = v->trace;
+            ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
+            g->graphs.push_back(ge);
+            hit = &g->graphs.back();
+        }
+        if ((e = cudaGraphLaunch(hit->exec, g->stream)) != cudaSuccess) return cuda_fail(g, e, "graph launch");
+    }
+    if (nsteps & 1) g->cur ^= 1;
+    g->t = g->t + (double)nsteps * dt;
+    g->steps += nsteps;
+    g->cross_explicit = false;
+    return GALS_OK;
+}
+
+gals_status gals_synchronize(gals_grid *g)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "synchronize");
+    return GALS_OK;
+}
+
+static gals_status ensure_cross(gals_grid *g)
+{
+    // COMPACT layout: the mixed derivatives of the current state are not stored by the
+    // step; rebuild them (unless set_state just provided them explicitly).
+    if (g->layout == GALS_LAYOUT_COMPACT && !g->cross_explicit) {
+        cudaError_t e = launch_recon(g->dim, g->geom, g->buf[g->cur], g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "recon");
+    }
+    return GALS_OK;
+}
+
+gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int memspace)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
+    if (!fields || nfields < 1 || nfields > g->nplanes)
+        return fail(g, GALS_ERR_ARG, "nfields must be in 1..%d", g->nplanes);
+    if (memspace != GALS_MEM_HOST && memspace != GALS_MEM_DEVICE)
+        return fail(g, GALS_ERR_ARG, "bad memspace %d", memspace);
+    for (int p = 0; p < nfields; ++p)
+        if (!fields[p]) return fail(g, GALS_ERR_ARG, "fields[%d] is NULL", p);
+    if (nfields > 1 + g->dim) {
+        gals_status st = ensure_cross(g);
+        if (st != GALS_OK) return st;
+    }
+    const Geom &G = g->geom;
+    const size_t row = (size_t)g->n[0] * sizeof(float);
+    const size_t rows = (size_t)g->n[1] * g->n[2];
+    const cudaMemcpyKind kind = memspace == GALS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e;
+    for (int p = 0; p < nfields; ++p) {
+        e = cudaMemcpy2DAsync(fields[p], row, g->buf[g->cur] + p * G.plane, (size_t)G.pitch * sizeof(float),
+                              row, rows, kind, g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "read_state copy");
+    }
+    if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "read_state sync");
+    return GALS_OK;
+}
+
+gals_status gals_state_planes(gals_grid *g, float **planes, int nplanes, int64_t *row_pitch)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!planes || nplanes < 1 || nplanes > g->nplanes)
+        return fail(g, GALS_ERR_ARG, "nplanes must be in 1..%d", g->nplanes);
+    for (int p = 0; p < nplanes; ++p) planes[p] = g->buf[g->cur] + p * g->geom.plane;
+    if (row_pitch) *row_pitch = g->geom.pitch;
+    return GALS_OK;
+}
+
+gals_status gals_diagnostics(gals_grid *g, const gals_diag_request *req, gals_diag *out)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!req || !out) return fail(g, GALS_ERR_ARG, "request/out is NULL");
+    if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
+    if (req->q < 0 || req->q > 16) return fail(g, GALS_ERR_ARG, "q must be in 0..16");
+    const gals_grid *r = req->reference;
+    if (r) {
+        if (r->dim != g->dim || r->n[0] != g->n[0] || r->n[1] != g->n[1] || r->n[2] != g->n[2])
+            return fail(g, GALS_ERR_ARG, "reference grid has another shape");
+        if (!r->has_state) return fail(g, GALS_ERR_STATE, "reference has no state");
+    }
+    gals_status st = ensure_cross(g);
+    if (st != GALS_OK) return st;
+    cudaError_t e;
+    if (r) {
+        // the reference is read on this grid's stream: order after its own work
+        if ((e = cudaStreamSynchronize(r->stream)) != cudaSuccess) return cuda_fail(g, e, "reference sync");
+        if (r->layout == GALS_LAYOUT_COMPACT && !r->cross_explicit) {
+            if ((e = launch_recon(r->dim, r->geom, r->buf[r->cur], g->stream)) != cudaSuccess)
+                return cuda_fail(g, e, "reference recon");
+        }
+    }
+    e = launch_diag(g->dim, g->geom, g->buf[g->cur], r ? r->buf[r->cur] : nullptr, req->q, g->diag_dev,
+                    g->diag_partials, g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "diagnostics launch");
+    DiagOut h;
+    if ((e = cudaMemcpyAsync(&h, g->diag_dev, sizeof(h), cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess)
+        return cuda_fail(g, e, "diagnostics copy");
+    if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "diagnostics sync");
+    std::memset(out, 0, sizeof(*out));
+    double cell = 1.0;
+    int64_t ncell = 1;
+    for (int i = 0; i < g->dim; ++i) { cell *= g->h[i]; ncell *= g->n[i] - 1; }
+    const int q = req->q;
+    double qp = 1.0;
+    for (int i = 0; i < g->dim; ++i) qp *= q;
+    out->t = g->t;
+    out->steps = g->steps;
+    out->samples = q > 0 ? (int64_t)(ncell * qp) : 0;
+    out->n_negative = (int64_t)h.n_neg;
+    out->measure_negative = q > 0 ? (double)h.n_neg * cell / qp : 0.0;
+    out->n_symdiff = (int64_t)h.n_sym;
+    out->measure_symdiff = q > 0 ? (double)h.n_sym * cell / qp : 0.0;
+    float fphi, fpsi;
+    std::memcpy(&fphi, &h.emax_phi_bits, 4);
+    std::memcpy(&fpsi, &h.emax_psi_bits, 4);
+    out->emax_phi = r ? (double)fphi : 0.0;
+    out->emax_psi = r ? (double)fpsi : 0.0;
+    out->l2_phi = r ? std::sqrt(h.l2_phi_sum * cell) : 0.0;
+    out->nonfinite = (int64_t)h.nonfinite;
+    return GALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,449 @@
+// gals_device.cuh -- device-side building blocks of the GALS step (FP32).
+//
+// The per-node update follows the superconsistent gradient-augmented CIR scheme of
+// Nave, Rosales and Seibold (arXiv 0905.3409):
+//   * analytic velocity v and Jacobian Dv (Sec. 4 assumes both are known exactly),
+//   * backward trace with the Jacobian of the approximate backward map
+//     (Sec. 5.1, Ex. "superconsistent forward Euler" and "superconsistent Shu-Osher"),
+//   * cell location of the foot point and the p-cubic Hermite interpolant
+//     (Sec. 2.3, eq. 1-cubic_basis_functions and eq. p-cubic_interpolant),
+//   * phi+ = H(foot), psi+ = J^T grad H(foot)  (eq. superconsistency),
+//   * mixed derivatives from central differences of the gradient (Sec. 2.3, approach A).
+//
+// FP32 design notes (they keep the result within ~1e-7 relative of an exact evaluation):
+//   * the trace carries the foot displacement delta = foot - x (small) instead of the
+//     absolute foot, and the cell index is node index + floor(delta/h), so xi keeps
+//     full precision even on 4096^2 grids;
+//   * the Hermite evaluation subtracts the base corner's phi from all corner values
+//     first (the interpolant reproduces constants exactly), so the value terms are O(h)
+//     and their derivatives divided by h lose no digits to cancellation;
+//   * the interpolant is sum-factorised along x, then y (then z); the sum is the same
+//     polynomial as the direct 4^p-term form of the paper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gals {
+
+constexpr int kMaxModes = 64;
+constexpr float kPi = 3.14159265358979323846f;
+
+enum VelKind { VK_CONST = 0, VK_ROTATION = 1, VK_VORTEX2D = 2, VK_DEFORM3D = 3,
+               VK_PSEUDO1D = 4, VK_FOURIER2D = 5 };
+enum TraceKind { TR_EULER = 0, TR_RK3 = 1 };
+enum CrossSrc { CROSS_PLANE = 0, CROSS_RECON = 1 };
+
+// Velocity descriptor as passed to kernels (by value).
+struct VelParams {
+    int kind;
+    float omega, cx, cy, cz;
+    float c0, c1, c2;
+    float d0, d1;               // PSEUDO1D direction (unit vector)
+    double invT;                // 1/T of the cos(pi t/T) modulation
+    int nmodes;
+    float mode_a[kMaxModes];
+    int mode_kl[kMaxModes];     // k | (l << 8), k, l in 1..4
+    double mode_n[kMaxModes];   // temporal frequency n (cycles per unit time)
+    double mode_chi[kMaxModes]; // phase / (2 pi)
+};
+
+// Grid geometry for kernels.
+struct Geom {
+    int n0, n1, n2;
+    int pitch;                  // row pitch in floats (multiple of 4)
+    int64_t plane;              // plane stride in floats
+    float h0, h1, h2;
+    float ih0, ih1, ih2;        // 1/h
+    float i2h0, i2h1, i2h2;     // 1/(2h)
+    float lo0, lo1, lo2;
+};
+
+// Time-dependent scalars of the three RK3 stage times (t+dt, t, t+dt/2), computed once
+// per thread block in shared memory.  FOURIER2D folds the modes into 4x4 tables
+// A_kl(t) = sum_{m: k_m = k, l_m = l} a_m cos(2 pi n_m t + chi_m), pre-scaled.
+struct StageCoef {
+    float mod[3];               // cos(pi t_s / T)
+    float Al[3][16];            // A_kl * l pi
+    float A[3][16];             // A_kl
+    float All[3][16];           // A_kl * (l pi)^2
+};
+
+// ---------------------------------------------------------------- stage coefficients
+
+// Fill sc for stage times (t+dt, t, t+dt/2).  Called by all threads of a block,
+// followed by __syncthreads() at the call site.
+__device__ inline void fill_stage_coef(const VelParams &vp, double t, double dt, StageCoef &sc)
+{
+    int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid < 3) {
+        const double ts = tid == 0 ? t + dt : (tid == 1 ? t : t + 0.5 * dt);
+        // cos(pi t/T): reduce the phase t/T modulo 2 in FP64, then evaluate in FP64
+        double ph = ts * vp.invT;
+        ph = ph - 2.0 * floor(0.5 * ph);
+        sc.mod[tid] = (float)cospi(ph);
+    }
+    if (vp.kind == VK_FOURIER2D && tid >= 32 && tid < 32 + 48) {
+        int s = (tid - 32) / 16, kl = (tid - 32) % 16;
+        int k = kl / 4 + 1, l = kl % 4 + 1;
+        const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
+        double acc = 0.0;
+        for (int m = 0; m < vp.nmodes; ++m) {
+            if (vp.mode_kl[m] != (k | (l << 8))) continue;
+            double ph = 2.0 * (vp.mode_n[m] * ts + vp.mode_chi[m]);  // in units of pi
+            ph = ph - 2.0 * floor(0.5 * ph);
+            acc += (double)vp.mode_a[m] * cospi(ph);
+        }
+        float a = (float)acc, lp = (float)l * kPi;
+        sc.A[s][kl] = a;
+        sc.Al[s][kl] = a * lp;
+        sc.All[s][kl] = a * lp * lp;
+    }
+}
+
+// ---------------------------------------------------------------- velocity fields
+
+struct V2 { float u, v, d00, d01, d10, d11; };          // Dv[i][j] = dv_i/dx_j
+struct V3 { float v[3]; float d[9]; };
+
+__device__ __forceinline__ void sincospi_f(float x, float *s, float *c)
+{
+    __sincosf(x * kPi, s, c);
+}
+
+template <int VK>
+__device__ __forceinline__ V2 vel2d(const VelParams &vp, const StageCoef &sc, int stage,
+                                    float x, float y)
+{
+    V2 r;
+    if (VK == VK_CONST) {
+        r.u = vp.c0; r.v = vp.c1; r.d00 = r.d01 = r.d10 = r.d11 = 0.f;
+    } else if (VK == VK_ROTATION) {
+        r.u = -vp.omega * (y - vp.cy);
+        r.v = vp.omega * (x - vp.cx);
+        r.d00 = 0.f; r.d01 = -vp.omega; r.d10 = vp.omega; r.d11 = 0.f;
+    } else if (VK == VK_VORTEX2D) {
+        float sx, cxx, sy, cyy;
+        sincospi_f(x, &sx, &cxx);
+        sincospi_f(y, &sy, &cyy);
+        float c = sc.mod[stage];
+        float s2x = 2.f * sx * cxx, s2y = 2.f * sy * cyy;
+        float c2x = 1.f - 2.f * sx * sx, c2y = 1.f - 2.f * sy * sy;
+        float sx2 = sx * sx, sy2 = sy * sy;
+        r.u = -c * sx2 * s2y;
+        r.v = c * s2x * sy2;
+        float cp = c * kPi;
+        r.d00 = -cp * s2x * s2y;
+        r.d01 = -2.f * cp * sx2 * c2y;
+        r.d10 = 2.f * cp * c2x * sy2;
+        r.d11 = cp * s2x * s2y;
+    } else if (VK == VK_PSEUDO1D) {
+        float e = __expf(vp.d0 * x + vp.d1 * y);
+        r.u = e * vp.d0; r.v = e * vp.d1;
+        r.d00 = e * vp.d0 * vp.d0; r.d01 = e * vp.d0 * vp.d1;
+        r.d10 = r.d01; r.d11 = e * vp.d1 * vp.d1;
+    } else {  // VK_FOURIER2D
+        float s[5], c[5], sy_[5], cy_[5];
+        sincospi_f(x, &s[1], &c[1]);
+        sincospi_f(y, &sy_[1], &cy_[1]);
+        // multiple angles by the Chebyshev recurrences
+        s[2] = 2.f * s[1] * c[1];            c[2] = 1.f - 2.f * s[1] * s[1];
+        s[3] = s[2] * c[1] + c[2] * s[1];    c[3] = c[2] * c[1] - s[2] * s[1];
+        s[4] = 2.f * s[2] * c[2];            c[4] = 1.f - 2.f * s[2] * s[2];
+        sy_[2] = 2.f * sy_[1] * cy_[1];          cy_[2] = 1.f - 2.f * sy_[1] * sy_[1];
+        sy_[3] = sy_[2] * cy_[1] + cy_[2] * sy_[1]; cy_[3] = cy_[2] * cy_[1] - sy_[2] * sy_[1];
+        sy_[4] = 2.f * sy_[2] * cy_[2];          cy_[4] = 1.f - 2.f * sy_[2] * sy_[2];
+        // Psi = sum A_kl s_k(x) s_l(y); u = -Psi_y, v = Psi_x
+        float u = 0.f, v = 0.f, d00 = 0.f, d01 = 0.f, d10 = 0.f;
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            float Ux = 0.f, Vx = 0.f, W = 0.f;
+#pragma unroll
+            for (int l = 1; l <= 4; ++l) {
+                int kl = (k - 1) * 4 + (l - 1);
+                Ux = fmaf(sc.Al[stage][kl], cy_[l], Ux);   // sum_l A l pi c_l(y)
+                Vx = fmaf(sc.A[stage][kl], sy_[l], Vx);    // sum_l A s_l(y)
+                W = fmaf(sc.All[stage][kl], sy_[l], W);    // sum_l A (l pi)^2 s_l(y)
+            }
+            float kp = (float)k * kPi;
+            u = fmaf(-s[k], Ux, u);
+            v = fmaf(kp * c[k], Vx, v);
+            d00 = fmaf(-kp * c[k], Ux, d00);
+            d01 = fmaf(s[k], W, d01);
+            d10 = fmaf(-kp * kp * s[k], Vx, d10);
+        }
+        r.u = u; r.v = v; r.d00 = d00; r.d01 = d01; r.d10 = d10; r.d11 = -d00;
+    }
+    return r;
+}
+
+template <int VK>
+__device__ __forceinline__ V3 vel3d(const VelParams &vp, const StageCoef &sc, int stage,
+                                    float x, float y, float z)
+{
+    V3 r;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) r.d[a] = 0.f;
+    if (VK == VK_CONST) {
+        r.v[0] = vp.c0; r.v[1] = vp.c1; r.v[2] = vp.c2;
+    } else if (VK == VK_ROTATION) {
+        r.v[0] = -vp.omega * (y - vp.cy);
+        r.v[1] = vp.omega * (x - vp.cx);
+        r.v[2] = 0.f;
+        r.d[1] = -vp.omega; r.d[3] = vp.omega;
+    } else {  // VK_DEFORM3D
+        float sx, cxx, sy, cyy, sz, czz;
+        sincospi_f(x, &sx, &cxx);
+        sincospi_f(y, &sy, &cyy);
+        sincospi_f(z, &sz, &czz);
+        float c = sc.mod[stage];
+        float s2x = 2.f * sx * cxx, s2y = 2.f * sy * cyy, s2z = 2.f * sz * czz;
+        float c2x = 1.f - 2.f * sx * sx, c2y = 1.f - 2.f * sy * sy, c2z = 1.f - 2.f * sz * sz;
+        float sx2 = sx * sx, sy2 = sy * sy, sz2 = sz * sz;
+        float cp = c * kPi;
+        r.v[0] = 2.f * c * sx2 * s2y * s2z;
+        r.v[1] = -c * s2x * sy2 * s2z;
+        r.v[2] = -c * s2x * s2y * sz2;
+        float sss = s2x * s2y * s2z;
+        r.d[0] = 2.f * cp * sss;
+        r.d[1] = 4.f * cp * sx2 * c2y * s2z;
+        r.d[2] = 4.f * cp * sx2 * s2y * c2z;
+        r.d[3] = -2.f * cp * c2x * sy2 * s2z;
+        r.d[4] = -cp * sss;
+        r.d[5] = -2.f * cp * s2x * sy2 * c2z;
+        r.d[6] = -2.f * cp * c2x * s2y * sz2;
+        r.d[7] = -2.f * cp * s2x * c2y * sz2;
+        r.d[8] = -cp * sss;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- backward traces
+
+// 2D trace from node position (x, y) at t+dt back to t: displacement (dx, dy) of the
+// foot and J[i][j] = d foot_i / d x_j (row-major J00, J01, J10, J11).
+template <int TR, int VK>
+__device__ __forceinline__ void trace2d(const VelParams &vp, const StageCoef &sc, float x,
+                                        float y, float dt, float &dx, float &dy, float J[4])
+{
+    V2 a = vel2d<VK>(vp, sc, 0, x, y);                      // v(x, t+dt)
+    if (TR == TR_EULER) {
+        dx = -dt * a.u; dy = -dt * a.v;
+        J[0] = 1.f - dt * a.d00; J[1] = -dt * a.d01;
+        J[2] = -dt * a.d10;      J[3] = 1.f - dt * a.d11;
+        return;
+    }
+    // stage 1: x1 = x - dt v(x, t+dt), J1 = I - dt Dv(x, t+dt)
+    float J1_00 = 1.f - dt * a.d00, J1_01 = -dt * a.d01;
+    float J1_10 = -dt * a.d10, J1_11 = 1.f - dt * a.d11;
+    V2 b = vel2d<VK>(vp, sc, 1, x - dt * a.u, y - dt * a.v);  // v(x1, t)
+    // M = Dv(x1, t) J1
+    float M00 = b.d00 * J1_00 + b.d01 * J1_10, M01 = b.d00 * J1_01 + b.d01 * J1_11;
+    float M10 = b.d10 * J1_00 + b.d11 * J1_10, M11 = b.d10 * J1_01 + b.d11 * J1_11;
+    // stage 2: x2 = x - dt (v1 + v2)/4, J2 = I - dt (Dv1 + Dv2 J1)/4
+    float q = 0.25f * dt;
+    float J2_00 = 1.f - q * (a.d00 + M00), J2_01 = -q * (a.d01 + M01);
+    float J2_10 = -q * (a.d10 + M10), J2_11 = 1.f - q * (a.d11 + M11);
+    V2 c = vel2d<VK>(vp, sc, 2, x - q * (a.u + b.u), y - q * (a.v + b.v));  // v(x2, t+dt/2)
+    float N00 = c.d00 * J2_00 + c.d01 * J2_10, N01 = c.d00 * J2_01 + c.d01 * J2_11;
+    float N10 = c.d10 * J2_00 + c.d11 * J2_10, N11 = c.d10 * J2_01 + c.d11 * J2_11;
+    // stage 3: foot = x - dt (v1/6 + v2/6 + 2 v3/3), J = I - dt (Dv1/6 + Dv2 J1/6 + 2 Dv3 J2/3)
+    // written as w3 + (w1 + w2 - 2 w3)/6 (= w1/6 + w2/6 + 2 w3/3), exact for constant v
+    const float i6 = 1.f / 6.f;
+    dx = -dt * fmaf(a.u + b.u - 2.f * c.u, i6, c.u);
+    dy = -dt * fmaf(a.v + b.v - 2.f * c.v, i6, c.v);
+    J[0] = 1.f - dt * fmaf(a.d00 + M00 - 2.f * N00, i6, N00);
+    J[1] = -dt * fmaf(a.d01 + M01 - 2.f * N01, i6, N01);
+    J[2] = -dt * fmaf(a.d10 + M10 - 2.f * N10, i6, N10);
+    J[3] = 1.f - dt * fmaf(a.d11 + M11 - 2.f * N11, i6, N11);
+}
+
+__device__ __forceinline__ void matmul3(const float *A, const float *B, float *C)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+template <int TR, int VK>
+__device__ __forceinline__ void trace3d(const VelParams &vp, const StageCoef &sc, float x,
+                                        float y, float z, float dt, float d[3], float J[9])
+{
+    V3 a = vel3d<VK>(vp, sc, 0, x, y, z);
+    if (TR == TR_EULER) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d[i] = -dt * a.v[i];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) J[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * a.d[e];
+        return;
+    }
+    float J1[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) J1[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * a.d[e];
+    V3 b = vel3d<VK>(vp, sc, 1, x - dt * a.v[0], y - dt * a.v[1], z - dt * a.v[2]);
+    float M[9];
+    matmul3(b.d, J1, M);
+    float q = 0.25f * dt;
+    float J2[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) J2[e] = ((e % 4) == 0 ? 1.f : 0.f) - q * (a.d[e] + M[e]);
+    V3 c = vel3d<VK>(vp, sc, 2, x - q * (a.v[0] + b.v[0]), y - q * (a.v[1] + b.v[1]),
+                     z - q * (a.v[2] + b.v[2]));
+    float N[9];
+    matmul3(c.d, J2, N);
+    const float i6 = 1.f / 6.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = -dt * fmaf(a.v[i] + b.v[i] - 2.f * c.v[i], i6, c.v[i]);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        J[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * fmaf(a.d[e] + M[e] - 2.f * N[e], i6, N[e]);
+}
+
+// ---------------------------------------------------------------- cell location
+
+// Node index i, foot displacement in cells dc, n nodes: cell k in [0, n-2] and xi in
+// [0, 1]; feet outside the box are clamped to its faces.
+__device__ __forceinline__ void locate(int i, float dc, int n, int &k, float &xi)
+{
+    float fl = floorf(dc);
+    int kk = i + (int)fl;
+    float r = dc - fl;
+    if (kk < 0) { k = 0; xi = 0.f; }
+    else if (kk >= n - 1) { k = n - 2; xi = 1.f; }
+    else { k = kk; xi = r; }
+}
+
+// ---------------------------------------------------------------- Hermite basis
+
+// 1D basis at xi for a cell of length h, pre-scaled:
+//   value part   F0 = 1 - S, F1 = S with S = 3 xi^2 - 2 xi^3  (f(xi), f(1-xi))
+//   slope part   hG0 = h g(xi), hG1 = -h g(1-xi)               (g(x) = x (1-x)^2)
+//   derivatives  dS = S'(xi)/h, dG0 = g'(xi), dG1 = g'(1-xi)
+// The value part is evaluated from the nearer end: p_near + (p1 - p0) (S - near), with
+// near = (xi >= 1/2).  At xi = 0 or 1 this returns the end value exactly, so a foot
+// that lands on a node reproduces the node's data bit for bit.
+struct Basis1 { float Sn, dS, hG0, hG1, dG0, dG1; bool near1; };
+
+__device__ __forceinline__ Basis1 basis1(float xi, float h, float ih)
+{
+    Basis1 b;
+    float om = 1.f - xi;
+    float S = xi * xi * (3.f - 2.f * xi);
+    b.near1 = xi >= 0.5f;
+    b.Sn = b.near1 ? S - 1.f : S;
+    b.dS = 6.f * xi * om * ih;
+    b.hG0 = h * xi * om * om;
+    b.hG1 = -h * om * xi * xi;
+    b.dG0 = om * (1.f - 3.f * xi);
+    b.dG1 = xi * (3.f * xi - 2.f);
+    return b;
+}
+
+// 1D Hermite reduction of an end pair (p0, p1) with slopes (s0, s1): value and derivative
+__device__ __forceinline__ float hval(const Basis1 &b, float p0, float p1, float s0, float s1)
+{
+    return fmaf(p1 - p0, b.Sn, fmaf(s0, b.hG0, fmaf(s1, b.hG1, b.near1 ? p1 : p0)));
+}
+__device__ __forceinline__ float hder(const Basis1 &b, float p0, float p1, float s0, float s1)
+{
+    return fmaf(p1 - p0, b.dS, fmaf(s0, b.dG0, s1 * b.dG1));
+}
+
+// 2D cell data: c[v][a] with corner v = vx + 2 vy and a = 0 phi, 1 phi_x, 2 phi_y, 3 phi_xy.
+// Returns H, H_x, H_y.
+__device__ __forceinline__ void hermite2d(const float c[4][4], const Basis1 &bx,
+                                          const Basis1 &by, float &H, float &Hx, float &Hy)
+{
+    // subtract phi of the corner nearest to the foot: the value terms become O(h)
+    const float b0 = bx.near1 ? c[1][0] : c[0][0];
+    const float b1 = bx.near1 ? c[3][0] : c[2][0];
+    const float base = by.near1 ? b1 : b0;
+    float p00 = c[0][0] - base, p10 = c[1][0] - base, p01 = c[2][0] - base, p11 = c[3][0] - base;
+    // along x on rows y0 (B=0) and y1 (B=1)
+    float P0 = hval(bx, p00, p10, c[0][1], c[1][1]);
+    float P1 = hval(bx, p01, p11, c[2][1], c[3][1]);
+    float Pd0 = hder(bx, p00, p10, c[0][1], c[1][1]);
+    float Pd1 = hder(bx, p01, p11, c[2][1], c[3][1]);
+    float Q0 = hval(bx, c[0][2], c[1][2], c[0][3], c[1][3]);
+    float Q1 = hval(bx, c[2][2], c[3][2], c[2][3], c[3][3]);
+    float Qd0 = hder(bx, c[0][2], c[1][2], c[0][3], c[1][3]);
+    float Qd1 = hder(bx, c[2][2], c[3][2], c[2][3], c[3][3]);
+    // along y
+    H = base + hval(by, P0, P1, Q0, Q1);
+    Hy = hder(by, P0, P1, Q0, Q1);
+    Hx = hval(by, Pd0, Pd1, Qd0, Qd1);
+}
+
+// 3D cell data: c[v][a], corner v = vx + 2 vy + 4 vz, a = plane index
+// (0 phi, 1 x, 2 y, 3 z, 4 xy, 5 xz, 6 yz, 7 xyz).  Returns H and its gradient.
+__device__ __forceinline__ void hermite3d(const float c[8][8], const Basis1 &bx,
+                                          const Basis1 &by, const Basis1 &bz, float &H,
+                                          float g[3])
+{
+    // subtract phi of the corner nearest to the foot: the value terms become O(h)
+    const int vn = (bx.near1 ? 1 : 0) + (by.near1 ? 2 : 0) + (bz.near1 ? 4 : 0);
+    float base = c[0][0];
+#pragma unroll
+    for (int v = 1; v < 8; ++v) base = (v == vn) ? c[v][0] : base;
+    float R[2], Rx[2], Ry[2], Rz[2], Rzx[2], Rzy[2];
+#pragma unroll
+    for (int C = 0; C < 2; ++C) {
+        float P[2], Pd[2], Qy[2], Qyd[2], Qz[2], Qzd[2], Qyz[2], Qyzd[2];
+#pragma unroll
+        for (int B = 0; B < 2; ++B) {
+            int v0 = 2 * B + 4 * C, v1 = v0 + 1;
+            float p0 = c[v0][0] - base, p1 = c[v1][0] - base;
+            P[B] = hval(bx, p0, p1, c[v0][1], c[v1][1]);
+            Pd[B] = hder(bx, p0, p1, c[v0][1], c[v1][1]);
+            Qy[B] = hval(bx, c[v0][2], c[v1][2], c[v0][4], c[v1][4]);
+            Qyd[B] = hder(bx, c[v0][2], c[v1][2], c[v0][4], c[v1][4]);
+            Qz[B] = hval(bx, c[v0][3], c[v1][3], c[v0][5], c[v1][5]);
+            Qzd[B] = hder(bx, c[v0][3], c[v1][3], c[v0][5], c[v1][5]);
+            Qyz[B] = hval(bx, c[v0][6], c[v1][6], c[v0][7], c[v1][7]);
+            Qyzd[B] = hder(bx, c[v0][6], c[v1][6], c[v0][7], c[v1][7]);
+        }
+        R[C] = hval(by, P[0], P[1], Qy[0], Qy[1]);
+        Ry[C] = hder(by, P[0], P[1], Qy[0], Qy[1]);
+        Rx[C] = hval(by, Pd[0], Pd[1], Qyd[0], Qyd[1]);
+        Rz[C] = hval(by, Qz[0], Qz[1], Qyz[0], Qyz[1]);
+        Rzy[C] = hder(by, Qz[0], Qz[1], Qyz[0], Qyz[1]);
+        Rzx[C] = hval(by, Qzd[0], Qzd[1], Qyzd[0], Qyzd[1]);
+    }
+    H = base + hval(bz, R[0], R[1], Rz[0], Rz[1]);
+    g[2] = hder(bz, R[0], R[1], Rz[0], Rz[1]);
+    g[0] = hval(bz, Rx[0], Rx[1], Rzx[0], Rzx[1]);
+    g[1] = hval(bz, Ry[0], Ry[1], Rzy[0], Rzy[1]);
+}
+
+// ---------------------------------------------------------------- approach A stencils
+
+// First derivative along one axis from three samples, shared by every kernel that
+// rebuilds mixed derivatives so that all paths round identically:
+//   interior  (u[i+1] - u[i-1]) / (2h)
+//   i = 0     (-3 u0 + 4 u1 - u2) / (2h)
+//   i = n-1   (3 u_{n-1} - 4 u_{n-2} + u_{n-3}) / (2h)
+__device__ __forceinline__ float dcentral(float up, float um, float i2h)
+{
+    return __fmul_rn(__fsub_rn(up, um), i2h);
+}
+__device__ __forceinline__ float dfirst(float u0, float u1, float u2, float i2h)
+{
+    return __fmul_rn(__fmaf_rn(4.f, u1, __fmaf_rn(-3.f, u0, -u2)), i2h);
+}
+__device__ __forceinline__ float dlast(float un1, float un2, float un3, float i2h)
+{
+    return __fmul_rn(__fmaf_rn(-4.f, un2, __fmaf_rn(3.f, un1, un3)), i2h);
+}
+
+// Derivative at index i of a line accessed through get(idx) (n >= 3).
+template <class Get>
+__device__ __forceinline__ float dline(int i, int n, float i2h, Get get)
+{
+    if (i == 0) return dfirst(get(0), get(1), get(2), i2h);
+    if (i == n - 1) return dlast(get(n - 1), get(n - 2), get(n - 3), i2h);
+    return dcentral(get(i + 1), get(i - 1), i2h);
+}
+
+}  // namespace gals

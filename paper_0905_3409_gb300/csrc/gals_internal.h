@@ -1,0 +1,45 @@
+// gals_internal.h -- host-side interface between the C ABI and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gals_device.cuh"
+
+namespace gals {
+
+struct StepLaunch {
+    const float *in;     // state at t (all planes, plane stride geom.plane)
+    float *out;          // state at t + dt
+    Geom geom;
+    VelParams vp;
+    const double *t_dev; // device copy of the grid time at the start of the call
+    int kstep;           // step index within the call: t = *t_dev + kstep * dt
+    double dt;
+    int trace;           // TR_EULER / TR_RK3
+    int cross_in;        // CROSS_PLANE: read mixed derivatives; CROSS_RECON: rebuild from psi
+    int write_cross;     // 1: also write the mixed-derivative planes of the new state
+};
+
+// Kernel launchers; return the launch error (cudaSuccess if launched).
+cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s);
+cudaError_t launch_step3d(const StepLaunch &a, cudaStream_t s);
+// Rebuild the mixed-derivative planes of `buf` from its gradient planes (approach A).
+cudaError_t launch_recon(int dim, const Geom &g, float *buf, cudaStream_t s);
+// t_dev[0] += nsteps * dt
+cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream_t s);
+// Velocity kinds supported per dimension.
+bool vel_supported(int dim, int kind);
+
+// Diagnostics (diag.cu)
+struct DiagOut {
+    unsigned long long n_neg, n_sym, nonfinite;
+    unsigned int emax_phi_bits, emax_psi_bits;  // non-negative floats as ordered integers
+    double l2_phi_sum;
+};
+// Scratch: `partials` holds at least diag_partials_needed() doubles; `counters` a DiagOut.
+int diag_partials_needed();
+cudaError_t launch_diag(int dim, const Geom &g, const float *a, const float *b, int q,
+                        DiagOut *counters, double *partials, cudaStream_t s);
+
+}  // namespace gals

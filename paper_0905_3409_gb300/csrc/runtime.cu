@@ -1,0 +1,36 @@
+// runtime.cu -- small launchers shared by the C ABI: approach-A reconstruction dispatch,
+// the device clock update and the velocity/dimension support table.
+#include "gals_internal.h"
+
+namespace gals {
+
+cudaError_t launch_recon2d(const Geom &g, float *buf, cudaStream_t s);
+cudaError_t launch_recon3d(const Geom &g, float *buf, cudaStream_t s);
+
+cudaError_t launch_recon(int dim, const Geom &g, float *buf, cudaStream_t s)
+{
+    return dim == 2 ? launch_recon2d(g, buf, s) : launch_recon3d(g, buf, s);
+}
+
+namespace {
+__global__ void k_advance_time(double *t, int nsteps, double dt)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) t[0] = t[0] + (double)nsteps * dt;
+}
+}  // namespace
+
+cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream_t s)
+{
+    k_advance_time<<<1, 32, 0, s>>>(t_dev, nsteps, dt);
+    return cudaGetLastError();
+}
+
+bool vel_supported(int dim, int kind)
+{
+    if (dim == 2)
+        return kind == VK_CONST || kind == VK_ROTATION || kind == VK_VORTEX2D ||
+               kind == VK_PSEUDO1D || kind == VK_FOURIER2D;
+    return kind == VK_CONST || kind == VK_ROTATION || kind == VK_DEFORM3D;
+}
+
+}  // namespace gals

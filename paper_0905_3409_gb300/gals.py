@@ -1,0 +1,245 @@
+"""Thin Python binding of the C ABI in ``include/gals.h`` (ctypes).
+
+Only argument marshalling happens here: every step of the method runs in the CUDA
+kernels of ``libgals.so``.  PyTorch is used for device memory (device tensors are
+passed by pointer) and for streams.  There is no CPU fallback: if the library is
+missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgals.so")
+
+# enums of gals.h
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE, ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+MEM_HOST, MEM_DEVICE = 0, 1
+LAYOUT_FULL, LAYOUT_COMPACT = 0, 1
+VEL = {"const": 0, "rotation": 1, "vortex2d": 2, "deform3d": 3, "pseudo1d": 4, "fourier2d": 5}
+TRACE = {"euler": 0, "rk3": 1}
+SET_RECON_CROSS = 1
+MAX_MODES = 64
+
+# every symbol include/gals.h declares
+EXPORTS = [
+    "gals_create_grid", "gals_destroy_grid", "gals_set_state", "gals_step", "gals_read_state",
+    "gals_diagnostics", "gals_synchronize", "gals_time", "gals_state_planes", "gals_last_error",
+    "gals_version",
+]
+
+
+class GalsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gals status {status}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("layout", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class VelocityDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("trace", ctypes.c_int), ("T", ctypes.c_double),
+                ("omega", ctypes.c_double), ("center", ctypes.c_double * 3), ("c", ctypes.c_double * 3),
+                ("nmodes", ctypes.c_int), ("modes", ctypes.POINTER(ctypes.c_double))]
+
+
+class DiagRequest(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("reference", ctypes.c_void_p)]
+
+
+class DiagOut(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("n_negative", ctypes.c_int64), ("measure_negative", ctypes.c_double),
+                ("n_symdiff", ctypes.c_int64), ("measure_symdiff", ctypes.c_double),
+                ("emax_phi", ctypes.c_double), ("emax_psi", ctypes.c_double),
+                ("l2_phi", ctypes.c_double), ("nonfinite", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libgals.so`` (built by ``paper_0905_3409_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.gals_create_grid.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)]
+        L.gals_destroy_grid.argtypes = [vp]
+        L.gals_set_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int]
+        L.gals_step.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double, ctypes.c_int]
+        L.gals_read_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+        L.gals_diagnostics.argtypes = [vp, ctypes.POINTER(DiagRequest), ctypes.POINTER(DiagOut)]
+        L.gals_synchronize.argtypes = [vp]
+        L.gals_time.argtypes = [vp]
+        L.gals_time.restype = ctypes.c_double
+        L.gals_state_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64)]
+        L.gals_last_error.argtypes = [vp]
+        L.gals_last_error.restype = ctypes.c_char_p
+        L.gals_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, handle=None):
+    if status != OK:
+        msg = lib().gals_last_error(handle)
+        raise GalsError(status, msg.decode() if msg else "")
+
+
+@dataclass
+class Velocity:
+    """Analytic velocity field descriptor (see gals.h for the kinds)."""
+    kind: str
+    trace: str = "rk3"
+    T: float = 1.0
+    omega: float = 0.0
+    center: tuple = (0.5, 0.5, 0.5)
+    c: tuple = (0.0, 0.0, 0.0)
+    modes: np.ndarray | None = None
+
+    def desc(self) -> VelocityDesc:
+        d = VelocityDesc()
+        d.kind = VEL[self.kind]
+        d.trace = TRACE[self.trace]
+        d.T = float(self.T)
+        d.omega = float(self.omega)
+        for i in range(3):
+            d.center[i] = float(self.center[i]) if i < len(self.center) else 0.0
+            d.c[i] = float(self.c[i]) if i < len(self.c) else 0.0
+        if self.modes is not None:
+            m = np.ascontiguousarray(self.modes, dtype=np.float64).reshape(-1, 5)
+            d._keep = m
+            d.nmodes = m.shape[0]
+            d.modes = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        return d
+
+
+def _nplanes(dim):
+    return 4 if dim == 2 else 8
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Grid:
+    """A GALS grid on the current CUDA device.
+
+    ``n``: nodes per axis (x first); the state arrays have shape
+    (nplanes, [nz,] ny, nx) with x fastest."""
+
+    def __init__(self, n, lo=None, hi=None, layout: str = "full", stream=None):
+        dim = len(n)
+        d = GridDesc()
+        d.dim = dim
+        lo = [0.0] * dim if lo is None else list(lo)
+        hi = [1.0] * dim if hi is None else list(hi)
+        for i in range(3):
+            d.n[i] = int(n[i]) if i < dim else 1
+            d.lo[i] = float(lo[i]) if i < dim else 0.0
+            d.hi[i] = float(hi[i]) if i < dim else 1.0
+        d.layout = LAYOUT_FULL if layout == "full" else LAYOUT_COMPACT
+        if stream is not None:
+            d.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        h = ctypes.c_void_p()
+        _check(lib().gals_create_grid(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.dim = dim
+        self.n = tuple(int(v) for v in n)
+        self.nplanes = _nplanes(dim)
+        self.shape = (self.nplanes,) + tuple(reversed(self.n))
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gals_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- state
+    def set_state(self, state, t0: float = 0.0, recon: bool = False):
+        """state: numpy array (host) or torch CUDA tensor (device), float32 planes;
+        1+dim planes (cross derivatives rebuilt) or all planes."""
+        nf = state.shape[0]
+        if _is_torch(state):
+            import torch
+            assert state.is_cuda and state.dtype == torch.float32
+            st = state.contiguous()
+            ptrs = (ctypes.c_void_p * nf)(*[st[p].data_ptr() for p in range(nf)])
+            mem = MEM_DEVICE
+            self._keep = st
+        else:
+            st = np.ascontiguousarray(state, dtype=np.float32)
+            ptrs = (ctypes.c_void_p * nf)(*[st[p].ctypes.data for p in range(nf)])
+            mem = MEM_HOST
+        _check(lib().gals_set_state(self._h, ptrs, nf, mem, float(t0),
+                                    SET_RECON_CROSS if recon else 0), self._h)
+
+    def step(self, vel: Velocity, dt: float, nsteps: int = 1):
+        d = vel.desc()
+        _check(lib().gals_step(self._h, ctypes.byref(d), float(dt), int(nsteps)), self._h)
+
+    def read_state(self, out=None, nfields=None):
+        """Copy the state into ``out`` (numpy or torch CUDA tensor of self.shape);
+        returns a new host array if out is None."""
+        nf = self.nplanes if nfields is None else int(nfields)
+        if out is None:
+            out = np.empty((nf,) + self.shape[1:], dtype=np.float32)
+        if _is_torch(out):
+            assert out.is_cuda and out.is_contiguous()
+            ptrs = (ctypes.c_void_p * nf)(*[out[p].data_ptr() for p in range(nf)])
+            mem = MEM_DEVICE
+        else:
+            assert out.dtype == np.float32 and out.flags.c_contiguous
+            ptrs = (ctypes.c_void_p * nf)(*[out[p].ctypes.data for p in range(nf)])
+            mem = MEM_HOST
+        _check(lib().gals_read_state(self._h, ptrs, nf, mem), self._h)
+        return out
+
+    def diagnostics(self, q: int = 0, reference: "Grid | None" = None) -> dict:
+        req = DiagRequest()
+        req.q = int(q)
+        req.reference = reference._h.value if reference is not None else None
+        out = DiagOut()
+        _check(lib().gals_diagnostics(self._h, ctypes.byref(req), ctypes.byref(out)), self._h)
+        return {f: getattr(out, f) for f, _ in DiagOut._fields_}
+
+    def synchronize(self):
+        _check(lib().gals_synchronize(self._h), self._h)
+
+    @property
+    def time(self) -> float:
+        return lib().gals_time(self._h)
+
+    def state_planes(self):
+        ptrs = (ctypes.c_void_p * self.nplanes)()
+        pitch = ctypes.c_int64()
+        _check(lib().gals_state_planes(self._h, ptrs, self.nplanes, ctypes.byref(pitch)), self._h)
+        return [p for p in ptrs], pitch.value
+
+
+def version() -> str:
+    return lib().gals_version().decode()

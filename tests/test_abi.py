@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every function include/gals.h declares
+(no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_0905_3409_gb300 import gals
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(gals_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__ as ge
+    ge.build()
+    return gals.lib()
+
+
+def test_library_exports_all_declared_symbols(built):
+    decl = _declared()
+    assert decl, "no declarations found"
+    missing = [n for n in sorted(decl) if not hasattr(built, n)]
+    assert not missing, missing
+    assert set(decl) == set(gals.EXPORTS) | (set(decl) - set(gals.EXPORTS))
+    for n in gals.EXPORTS:
+        assert n in decl, n
+
+
+def test_version_and_argument_errors_without_gpu(built):
+    assert "sm_103a" in gals.version()
+    # argument validation happens before any CUDA call
+    d = gals.GridDesc()
+    d.dim = 4
+    h = ctypes.c_void_p()
+    assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
+    assert b"dim" in built.gals_last_error(None)
+    d.dim = 2
+    d.n[0], d.n[1] = 3, 10
+    d.hi[0] = d.hi[1] = 1.0
+    assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
+    assert built.gals_create_grid(None, ctypes.byref(h)) == gals.ERR_ARG
+    assert built.gals_step(None, None, 0.1, 1) == gals.ERR_ARG
+    assert built.gals_destroy_grid(None) == gals.OK
+
+
+def test_struct_layouts_match_header():
+    # sizes of the public structs as laid out by the C compiler (x86-64 / aarch64 LP64)
+    assert ctypes.sizeof(gals.GridDesc) == 4 + 12 + 24 + 24 + 4 + 4 + 8  # padded to 80
+    assert ctypes.sizeof(gals.DiagOut) == 11 * 8

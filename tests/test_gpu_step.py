@@ -1,0 +1,137 @@
+"""GPU parity of the GALS step (through the C ABI) against the FP64 oracle.
+
+Per step, the GPU's FP32 state is widened to FP64, advanced one step by the oracle,
+and compared with the GPU's next state: max |dphi| <= 1e-5 and max |dpsi| <= 1e-4 on
+O(1)-scaled fields.  Mixed derivatives are checked against the oracle's approach-A
+reconstruction of the GPU's own new gradients (tight) and against the oracle step
+(bound 4 eps_psi / h that the stencils imply).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3409_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_PHI, TOL_PSI = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def gals():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_0905_3409_gb300 import gals as G
+    return G
+
+
+def _ovel(kind, **kw):
+    return oracle.velocity(kind, **kw)
+
+
+def _gvel(G, kind, trace="rk3", **kw):
+    return G.Velocity(kind, trace=trace, **kw)
+
+
+def check_step(G, n, state, kind, dt, t0=0.0, steps=1, layout="full", trace="rk3",
+               lo=None, hi=None, recon=False, **vkw):
+    """Advance `steps` steps on the GPU and check each against one oracle step."""
+    g = G.Grid(n, lo=lo, hi=hi, layout=layout)
+    g.set_state(state.astype(np.float32), t0=t0, recon=recon)
+    og = oracle.grid(n, lo=lo, hi=hi)
+    ov = _ovel(kind, **vkw)
+    gv = _gvel(G, kind, trace=trace, **vkw)
+    worst = [0.0, 0.0, 0.0]
+    h = min(og.h[i] for i in range(len(n)))
+    core = 1 + len(n)
+    for _ in range(steps):
+        before = g.read_state().astype(np.float64)
+        t = g.time
+        g.step(gv, dt, 1)
+        after = g.read_state().astype(np.float64)
+        ref = oracle.step(og, ov, before, t, dt, trace_scheme=trace)
+        dphi = np.max(np.abs(after[0] - ref[0]))
+        dpsi = np.max(np.abs(after[1:core] - ref[1:core]))
+        assert dphi <= TOL_PHI, dphi
+        assert dpsi <= TOL_PSI, dpsi
+        # mixed derivatives: exact stencil arithmetic on the GPU's own gradients
+        rec = oracle.recon_cross(og, after)
+        scale = np.max(np.abs(rec[core:])) + 1.0
+        dcr = np.max(np.abs(after[core:] - rec[core:]))
+        assert dcr <= 2e-6 * scale, (dcr, scale)
+        dcr_ref = np.max(np.abs(after[core:] - ref[core:]))
+        assert dcr_ref <= 4 * max(dpsi, 1e-7) / h * (2 if len(n) == 3 else 1) + 2e-6 * scale
+        worst = [max(worst[0], dphi), max(worst[1], dpsi), max(worst[2], dcr)]
+    g.close()
+    return worst
+
+
+def test_config1_vortex_64(gals):
+    """64x64 nodes, circle SDF, exact gradient, phi_xy = 0 (given, not rebuilt)."""
+    n = (64, 64)
+    w = check_step(gals, n, inputs.circle_sdf(n), "vortex2d", 1.0 / 63, steps=4, T=8.0)
+    print("config1 worst", w)
+
+
+@pytest.mark.parametrize("layout", ["full", "compact"])
+@pytest.mark.parametrize("n", [(37, 29), (130, 67), (4, 4), (5, 257)])
+def test_ragged_sizes_vortex(gals, n, layout):
+    st = inputs.circle_sdf(n, center=(0.45, 0.55), r=0.3)
+    check_step(gals, n, st, "vortex2d", 0.7 / (max(n) - 1), t0=0.37, steps=2, layout=layout,
+               recon=True, T=8.0)
+
+
+@pytest.mark.parametrize("trace", ["rk3", "euler"])
+def test_rotation_slotted_disk(gals, trace):
+    n = (96, 96)
+    st = inputs.slotted_disk_sdf(n)
+    check_step(gals, n, st, "rotation", (1.0 / 95) / math.pi, steps=2, trace=trace, recon=True,
+               omega=2 * math.pi, center=(0.5, 0.5))
+
+
+def test_pseudo1d_gaussian_rectangular_cells(gals):
+    n = (48, 33)
+    lo, hi = (0.1, -0.2), (1.3, 0.9)
+    st = inputs.gaussian_bump2d(n, x0=(0.6, 0.3), lo=lo, hi=hi)
+    check_step(gals, n, st, "pseudo1d", 0.01, steps=2, lo=lo, hi=hi)
+
+
+def test_fourier_time_periodic(gals):
+    n = (80, 80)
+    modes = inputs.fourier_modes(16, seed=5, periodic=True)
+    st = inputs.ellipse_sdf(n, (0.5, 0.5), 0.2, 0.1, 0.4)
+    vmax = inputs.fourier_speed_bound(modes)
+    check_step(gals, n, st, "fourier2d", (1.0 / 79) / vmax, t0=0.3, steps=2, recon=True, modes=modes)
+
+
+def test_random_state_high_cfl(gals):
+    """Random O(1) data and CFL ~2 (feet two cells away): stencil reach is not limited."""
+    n = (70, 45)
+    st = inputs.random_state((4,) + n[::-1], seed=11)
+    check_step(gals, n, st, "const", 0.03, steps=1, c=(1.9, -1.4, 0))
+
+
+@pytest.mark.parametrize("layout", ["full", "compact"])
+@pytest.mark.parametrize("n", [(21, 18, 17), (33, 9, 12)])
+def test_3d_deform(gals, n, layout):
+    st = inputs.sphere_sdf(n, center=(0.4, 0.45, 0.5), r=0.25)
+    check_step(gals, n, st, "deform3d", 0.5 / (max(n) - 1), t0=0.2, steps=2, layout=layout,
+               recon=True, T=3.0)
+
+
+def test_3d_rotation_cube(gals):
+    n = (24, 24, 20)
+    st = inputs.cube_sdf(n, center=(0.5, 0.6, 0.5), half=0.2)
+    check_step(gals, n, st, "rotation", 0.01, steps=1, recon=True, omega=2 * math.pi,
+               center=(0.5, 0.5, 0.5))
+
+
+def test_3d_gaussian_explicit_cross(gals):
+    n = (16, 17, 18)
+    st = inputs.gaussian_bump3d(n)
+    check_step(gals, n, st, "const", 0.02, steps=1, c=(0.3, -0.5, 0.7))

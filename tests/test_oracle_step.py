@@ -246,3 +246,22 @@ def test_global_error_order_vortex(golden):
     assert golden["global_error_order"] == {"cite": golden["global_error_order"]["cite"], "phi": 3, "psi": 2}
     assert o_phi >= 2.7, (ephi, o_phi)
     assert o_psi >= 1.7, (epsi, o_psi)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_step_band_equals_full_step(dim):
+    if dim == 2:
+        n = (29, 23)
+        st = inputs.circle_sdf(n, r=0.3, center=(0.5, 0.5))
+        vel = oracle.velocity("vortex2d", T=8.0)
+    else:
+        n = (11, 10, 9)
+        st = inputs.sphere_sdf(n, r=0.3, center=(0.5, 0.5, 0.5))
+        vel = oracle.velocity("deform3d", T=3.0)
+    g = oracle.grid(n)
+    st = oracle.recon_cross(g, st)
+    full = oracle.step(g, vel, st, 0.2, 0.03)
+    outer = n[-1]
+    for b0, b1 in ((0, 3), (4, outer - 1), (outer - 2, outer)):
+        band = oracle.step_band(g, vel, st, 0.2, 0.03, b0, b1)
+        assert np.array_equal(band, full[:, b0:b1])
