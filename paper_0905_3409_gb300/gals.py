@@ -188,6 +188,7 @@ class Grid:
             import torch
             assert state.is_cuda and state.dtype == torch.float32
             st = state.contiguous()
+            torch.cuda.current_stream().synchronize()  # producer work on torch's stream
             ptrs = (ctypes.c_void_p * nf)(*[st[p].data_ptr() for p in range(nf)])
             mem = MEM_DEVICE
             self._keep = st
@@ -209,7 +210,9 @@ class Grid:
         if out is None:
             out = np.empty((nf,) + self.shape[1:], dtype=np.float32)
         if _is_torch(out):
+            import torch
             assert out.is_cuda and out.is_contiguous()
+            torch.cuda.current_stream().synchronize()
             ptrs = (ctypes.c_void_p * nf)(*[out[p].data_ptr() for p in range(nf)])
             mem = MEM_DEVICE
         else:

@@ -63,9 +63,16 @@ def check_step(G, n, state, kind, dt, t0=0.0, steps=1, layout="full", trace="rk3
         rec = oracle.recon_cross(og, after)
         scale = np.max(np.abs(rec[core:])) + 1.0
         dcr = np.max(np.abs(after[core:] - rec[core:]))
-        assert dcr <= 2e-6 * scale, (dcr, scale)
+        # FP32 rounding of differences of psi (and, for phi_xyz, of differences of the
+        # rounded y-differences) amplified by the 1/(2h) factors
+        maxpsi = np.max(np.abs(after[1:core]))
+        cr_tol = 2e-6 * scale + 1e-6 * maxpsi * (1.0 / h if len(n) == 2 else 1.0 / h ** 2)
+        assert dcr <= cr_tol, (dcr, cr_tol)
         dcr_ref = np.max(np.abs(after[core:] - ref[core:]))
-        assert dcr_ref <= 4 * max(dpsi, 1e-7) / h * (2 if len(n) == 3 else 1) + 2e-6 * scale
+        # stencil amplification of a gradient difference: 4/h (one-sided first
+        # derivative), 16/h^2 for the 3D double difference phi_xyz
+        amp = 4.0 / h if len(n) == 2 else max(4.0 / h, 16.0 / h ** 2)
+        assert dcr_ref <= amp * max(dpsi, 1e-7) + 2e-6 * scale
         worst = [max(worst[0], dphi), max(worst[1], dpsi), max(worst[2], dcr)]
     g.close()
     return worst
@@ -110,9 +117,14 @@ def test_fourier_time_periodic(gals):
 
 
 def test_random_state_high_cfl(gals):
-    """Random O(1) data and CFL ~2 (feet two cells away): stencil reach is not limited."""
+    """Random data and CFL ~2 (feet two cells away): stencil reach is not limited.
+    The random values are scaled like a smooth O(1) field sampled on the grid:
+    phi ~ h, psi ~ 1, phi_xy ~ 1/h."""
     n = (70, 45)
+    h = 1.0 / 69
     st = inputs.random_state((4,) + n[::-1], seed=11)
+    st[0] *= h
+    st[3] /= h
     check_step(gals, n, st, "const", 0.03, steps=1, c=(1.9, -1.4, 0))
 
 
