@@ -48,6 +48,8 @@ struct gals_grid {
     double t = 0.0;
     int64_t steps = 0;
     double *t_dev = nullptr;
+    StageCoef *coef = nullptr;    // per-step stage coefficients of the current call
+    int coef_cap = 0;
     DiagOut *diag_dev = nullptr;
     double *diag_partials = nullptr;
     cudaStream_t stream = nullptr;
@@ -128,14 +130,15 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
                         bool first_explicit)
 {
     int cur = g->cur;
+    cudaError_t ce = launch_coef_table(g->coef, vp, g->t_dev, dt, nsteps, g->stream);
+    if (ce != cudaSuccess) return ce;
     for (int s = 0; s < nsteps; ++s) {
         StepLaunch a;
         a.in = g->buf[cur];
         a.out = g->buf[cur ^ 1];
         a.geom = g->geom;
         a.vp = vp;
-        a.t_dev = g->t_dev;
-        a.kstep = s;
+        a.coef = g->coef + s;
         a.dt = dt;
         a.trace = trace == GALS_TRACE_EULER ? TR_EULER : TR_RK3;
         if (g->layout == GALS_LAYOUT_FULL) {
@@ -247,6 +250,7 @@ gals_status gals_destroy_grid(gals_grid *g)
     for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
     for (int b = 0; b < 2; ++b) cudaFree(g->buf[b]);
     cudaFree(g->t_dev);
+    cudaFree(g->coef);
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
@@ -305,6 +309,19 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     if (nsteps == 0) return GALS_OK;
     const bool fe = g->cross_explicit;
     cudaError_t e;
+    if (nsteps > g->coef_cap) {
+        // grow the coefficient table; cached graphs refer to the old one
+        if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
+        for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+        g->graphs.clear();
+        cudaFree(g->coef);
+        g->coef = nullptr;
+        g->coef_cap = 0;
+        const int cap = nsteps < 64 ? 64 : nsteps;
+        if ((e = cudaMalloc(&g->coef, sizeof(StageCoef) * (size_t)cap)) != cudaSuccess)
+            return cuda_fail(g, e, "cudaMalloc(coefficient table)");
+        g->coef_cap = cap;
+    }
     if (nsteps == 1) {
         if ((e = issue_steps(g, vp, v->trace, dt, 1, fe)) != cudaSuccess) return cuda_fail(g, e, "step launch");
     } else {

@@ -59,45 +59,48 @@ struct Geom {
     float lo0, lo1, lo2;
 };
 
-// Time-dependent scalars of the three RK3 stage times (t+dt, t, t+dt/2), computed once
-// per thread block in shared memory.  FOURIER2D folds the modes into 4x4 tables
-// A_kl(t) = sum_{m: k_m = k, l_m = l} a_m cos(2 pi n_m t + chi_m), pre-scaled.
+// Time-dependent scalars of the three RK3 stage times (t+dt, t, t+dt/2) of one step.
+// A table of these (one entry per step of a gals_step call) is filled once per call by
+// k_coef_table from the device clock, so the step kernels do no FP64 work.  FOURIER2D
+// folds the modes into 4x4 tables A_kl(t) = sum_{m: k_m = k, l_m = l} a_m
+// cos(2 pi n_m t + chi_m), pre-scaled.
 struct StageCoef {
     float mod[3];               // cos(pi t_s / T)
-    float Al[3][16];            // A_kl * l pi
+    float pad;
     float A[3][16];             // A_kl
+    float Al[3][16];            // A_kl * l pi
     float All[3][16];           // A_kl * (l pi)^2
 };
 
 // ---------------------------------------------------------------- stage coefficients
 
-// Fill sc for stage times (t+dt, t, t+dt/2).  Called by all threads of a block,
-// followed by __syncthreads() at the call site.
-__device__ inline void fill_stage_coef(const VelParams &vp, double t, double dt, StageCoef &sc)
+__device__ inline void stage_coef_one(const VelParams &vp, double t, double dt, StageCoef &sc)
 {
-    int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    if (tid < 3) {
-        const double ts = tid == 0 ? t + dt : (tid == 1 ? t : t + 0.5 * dt);
+    for (int s = 0; s < 3; ++s) {
+        const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
         // cos(pi t/T): reduce the phase t/T modulo 2 in FP64, then evaluate in FP64
         double ph = ts * vp.invT;
         ph = ph - 2.0 * floor(0.5 * ph);
-        sc.mod[tid] = (float)cospi(ph);
+        sc.mod[s] = (float)cospi(ph);
     }
-    if (vp.kind == VK_FOURIER2D && tid >= 32 && tid < 32 + 48) {
-        int s = (tid - 32) / 16, kl = (tid - 32) % 16;
-        int k = kl / 4 + 1, l = kl % 4 + 1;
+    sc.pad = 0.f;
+    if (vp.kind != VK_FOURIER2D) return;
+    for (int s = 0; s < 3; ++s) {
         const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
-        double acc = 0.0;
-        for (int m = 0; m < vp.nmodes; ++m) {
-            if (vp.mode_kl[m] != (k | (l << 8))) continue;
-            double ph = 2.0 * (vp.mode_n[m] * ts + vp.mode_chi[m]);  // in units of pi
-            ph = ph - 2.0 * floor(0.5 * ph);
-            acc += (double)vp.mode_a[m] * cospi(ph);
+        for (int kl = 0; kl < 16; ++kl) {
+            const int k = kl / 4 + 1, l = kl % 4 + 1;
+            double acc = 0.0;
+            for (int m = 0; m < vp.nmodes; ++m) {
+                if (vp.mode_kl[m] != (k | (l << 8))) continue;
+                double ph = 2.0 * (vp.mode_n[m] * ts + vp.mode_chi[m]);  // in units of pi
+                ph = ph - 2.0 * floor(0.5 * ph);
+                acc += (double)vp.mode_a[m] * cospi(ph);
+            }
+            const float a = (float)acc, lp = (float)l * kPi;
+            sc.A[s][kl] = a;
+            sc.Al[s][kl] = a * lp;
+            sc.All[s][kl] = a * lp * lp;
         }
-        float a = (float)acc, lp = (float)l * kPi;
-        sc.A[s][kl] = a;
-        sc.Al[s][kl] = a * lp;
-        sc.All[s][kl] = a * lp * lp;
     }
 }
 
@@ -223,10 +226,11 @@ __device__ __forceinline__ V3 vel3d(const VelParams &vp, const StageCoef &sc, in
 // 2D trace from node position (x, y) at t+dt back to t: displacement (dx, dy) of the
 // foot and J[i][j] = d foot_i / d x_j (row-major J00, J01, J10, J11).
 template <int TR, int VK>
-__device__ __forceinline__ void trace2d(const VelParams &vp, const StageCoef &sc, float x,
-                                        float y, float dt, float &dx, float &dy, float J[4])
+__device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, const StageCoef &sc,
+                                             float x, float y, float dt, float &dx, float &dy,
+                                             float J[4])
 {
-    V2 a = vel2d<VK>(vp, sc, 0, x, y);                      // v(x, t+dt)
+    // a = v(x, t+dt) and its Jacobian, supplied by the caller
     if (TR == TR_EULER) {
         dx = -dt * a.u; dy = -dt * a.v;
         J[0] = 1.f - dt * a.d00; J[1] = -dt * a.d01;
@@ -256,6 +260,13 @@ __device__ __forceinline__ void trace2d(const VelParams &vp, const StageCoef &sc
     J[1] = -dt * fmaf(a.d01 + M01 - 2.f * N01, i6, N01);
     J[2] = -dt * fmaf(a.d10 + M10 - 2.f * N10, i6, N10);
     J[3] = 1.f - dt * fmaf(a.d11 + M11 - 2.f * N11, i6, N11);
+}
+
+template <int TR, int VK>
+__device__ __forceinline__ void trace2d(const VelParams &vp, const StageCoef &sc, float x,
+                                        float y, float dt, float &dx, float &dy, float J[4])
+{
+    trace2d_from<TR, VK>(vel2d<VK>(vp, sc, 0, x, y), vp, sc, x, y, dt, dx, dy, J);
 }
 
 __device__ __forceinline__ void matmul3(const float *A, const float *B, float *C)

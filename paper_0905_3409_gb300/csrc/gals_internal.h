@@ -13,8 +13,7 @@ struct StepLaunch {
     float *out;          // state at t + dt
     Geom geom;
     VelParams vp;
-    const double *t_dev; // device copy of the grid time at the start of the call
-    int kstep;           // step index within the call: t = *t_dev + kstep * dt
+    const StageCoef *coef; // this step's stage coefficients (filled by launch_coef_table)
     double dt;
     int trace;           // TR_EULER / TR_RK3
     int cross_in;        // CROSS_PLANE: read mixed derivatives; CROSS_RECON: rebuild from psi
@@ -26,6 +25,9 @@ cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s);
 cudaError_t launch_step3d(const StepLaunch &a, cudaStream_t s);
 // Rebuild the mixed-derivative planes of `buf` from its gradient planes (approach A).
 cudaError_t launch_recon(int dim, const Geom &g, float *buf, cudaStream_t s);
+// table[s] = stage coefficients of step s (t = t_dev[0] + s*dt), s < nsteps
+cudaError_t launch_coef_table(StageCoef *table, const VelParams &vp, const double *t_dev,
+                              double dt, int nsteps, cudaStream_t s);
 // t_dev[0] += nsteps * dt
 cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream_t s);
 // Velocity kinds supported per dimension.

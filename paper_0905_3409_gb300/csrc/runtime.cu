@@ -19,6 +19,24 @@ __global__ void k_advance_time(double *t, int nsteps, double dt)
 }
 }  // namespace
 
+namespace {
+__global__ void k_coef_table(StageCoef *table, VelParams vp, const double *t_dev, double dt,
+                             int nsteps)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsteps) return;
+    const double t = t_dev[0] + (double)k * dt;
+    stage_coef_one(vp, t, dt, table[k]);
+}
+}  // namespace
+
+cudaError_t launch_coef_table(StageCoef *table, const VelParams &vp, const double *t_dev,
+                              double dt, int nsteps, cudaStream_t s)
+{
+    k_coef_table<<<(nsteps + 63) / 64, 64, 0, s>>>(table, vp, t_dev, dt, nsteps);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream_t s)
 {
     k_advance_time<<<1, 32, 0, s>>>(t_dev, nsteps, dt);

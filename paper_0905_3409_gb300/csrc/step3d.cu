@@ -29,12 +29,9 @@ __device__ __forceinline__ float dwin(const float w[4], int q, int n, float i2h)
 template <int TR, int VK, int CR>
 __global__ void __launch_bounds__(BX *BY *BZ)
 k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParams vp,
-         const double *__restrict__ t_dev, int kstep, double dt)
+         const StageCoef *__restrict__ coef, float dt)
 {
-    __shared__ StageCoef sc;
-    const double t = t_dev[0] + (double)kstep * dt;
-    fill_stage_coef(vp, t, dt, sc);
-    __syncthreads();
+    const StageCoef &sc = *coef;
 
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
@@ -45,7 +42,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
     const float y = g.lo1 + (float)j * g.h1;
     const float z = g.lo2 + (float)kz * g.h2;
     float d[3], J[9];
-    trace3d<TR, VK>(vp, sc, x, y, z, (float)dt, d, J);
+    trace3d<TR, VK>(vp, sc, x, y, z, dt, d, J);
 
     int k, l, m;
     float xi, eta, zeta;
@@ -159,7 +156,7 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
 {
     dim3 block(BX, BY, BZ);
     dim3 grid((a.geom.n0 + BX - 1) / BX, (a.geom.n1 + BY - 1) / BY, (a.geom.n2 + BZ - 1) / BZ);
-    k_step3d<TR, VK, CR><<<grid, block, 0, s>>>(a.in, a.out, a.geom, a.vp, a.t_dev, a.kstep, a.dt);
+    k_step3d<TR, VK, CR><<<grid, block, 0, s>>>(a.in, a.out, a.geom, a.vp, a.coef, (float)a.dt);
     return cudaGetLastError();
 }
 
