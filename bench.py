@@ -300,7 +300,7 @@ def run_ours(args, wl):
     value = nodes * args.steps * world / (ms * 1e-3)
 
     # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels)
-    launches_per_step = 2 if args.layout == "full" else 1
+    launches_per_step = 2 if (args.layout == "full" and dim == 3) else 1
     bpn = bytes_per_node(dim, args.layout)
     step_s = ms * 1e-3 / args.steps
     achieved = bpn * nodes / step_s / 1e9
@@ -347,7 +347,7 @@ def run_ours(args, wl):
                          "kernel": f"gals step ({launches_per_step} launch(es) per step)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
-            "gpu_launches": args.steps * launches_per_step + 1,
+            "gpu_launches": args.steps * launches_per_step + 2,  # + stage-coefficient table, clock
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:

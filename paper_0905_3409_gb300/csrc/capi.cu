@@ -48,6 +48,8 @@ struct gals_grid {
     double t = 0.0;
     int64_t steps = 0;
     double *t_dev = nullptr;
+    CUtensorMap maps[2][2];       // 2D TMA maps per buffer: [b][0] 3 planes, [b][1] 4 planes
+    int *err_dev = nullptr;       // device error word written by kernels (bounded waits)
     StageCoef *coef = nullptr;    // per-step stage coefficients of the current call
     int coef_cap = 0;
     DiagOut *diag_dev = nullptr;
@@ -140,6 +142,9 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
         a.vp = vp;
         a.coef = g->coef + s;
         a.dt = dt;
+        a.tmap3 = &g->maps[cur][0];
+        a.tmap4 = &g->maps[cur][1];
+        a.err = g->err_dev;
         a.trace = trace == GALS_TRACE_EULER ? TR_EULER : TR_RK3;
         if (g->layout == GALS_LAYOUT_FULL) {
             a.cross_in = CROSS_PLANE;
@@ -226,11 +231,33 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
         }
     }
     if ((e = cudaMalloc(&g->t_dev, sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&g->err_dev, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&g->diag_dev, sizeof(DiagOut))) != cudaSuccess ||
         (e = cudaMalloc(&g->diag_partials, sizeof(double) * diag_partials_needed())) != cudaSuccess) {
         gals_status st = cuda_fail(nullptr, e, "cudaMalloc(aux)");
         gals_destroy_grid(g);
         return st;
+    }
+    if ((e = cudaMemsetAsync(g->err_dev, 0, sizeof(int), g->stream)) != cudaSuccess) {
+        gals_status st = cuda_fail(nullptr, e, "cudaMemset");
+        gals_destroy_grid(g);
+        return st;
+    }
+    if (g->dim == 2) {
+        // TMA maps of each buffer: (x, y, plane) with the step kernel's tile box
+        for (int b = 0; b < 2; ++b)
+            for (int v = 0; v < 2; ++v) {
+                const int np = v == 0 ? 3 : 4;
+                const uint64_t dims[3] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)np};
+                const uint64_t strides[2] = {(uint64_t)G.pitch * 4, (uint64_t)G.plane * 4};
+                uint32_t box[3];
+                tile_box2d(np, box);
+                if ((e = make_tile_map(&g->maps[b][v], g->buf[b], 3, dims, strides, box)) != cudaSuccess) {
+                    gals_status st = cuda_fail(nullptr, e, "TMA descriptor");
+                    gals_destroy_grid(g);
+                    return st;
+                }
+            }
     }
     // zero both buffers so that pitch padding never holds garbage
     for (int b = 0; b < 2; ++b)
@@ -250,6 +277,7 @@ gals_status gals_destroy_grid(gals_grid *g)
     for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
     for (int b = 0; b < 2; ++b) cudaFree(g->buf[b]);
     cudaFree(g->t_dev);
+    cudaFree(g->err_dev);
     cudaFree(g->coef);
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
@@ -359,12 +387,24 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     return GALS_OK;
 }
 
+// After a stream synchronisation: report (and clear) a kernel-side error word.
+static gals_status check_device_error(gals_grid *g)
+{
+    int code = 0;
+    cudaError_t e = cudaMemcpy(&code, g->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(g, e, "error word");
+    if (code == 0) return GALS_OK;
+    cudaMemset(g->err_dev, 0, sizeof(int));
+    return fail(g, GALS_ERR_TIMEOUT, "a bounded device wait ran out (code %d); results of the "
+                "affected steps are invalid", code);
+}
+
 gals_status gals_synchronize(gals_grid *g)
 {
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "synchronize");
-    return GALS_OK;
+    return check_device_error(g);
 }
 
 static gals_status ensure_cross(gals_grid *g)
@@ -403,7 +443,7 @@ gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int
         if (e != cudaSuccess) return cuda_fail(g, e, "read_state copy");
     }
     if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "read_state sync");
-    return GALS_OK;
+    return check_device_error(g);
 }
 
 gals_status gals_state_planes(gals_grid *g, float **planes, int nplanes, int64_t *row_pitch)
@@ -446,6 +486,7 @@ gals_status gals_diagnostics(gals_grid *g, const gals_diag_request *req, gals_di
     if ((e = cudaMemcpyAsync(&h, g->diag_dev, sizeof(h), cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess)
         return cuda_fail(g, e, "diagnostics copy");
     if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "diagnostics sync");
+    if ((st = check_device_error(g)) != GALS_OK) return st;
     std::memset(out, 0, sizeof(*out));
     double cell = 1.0;
     int64_t ncell = 1;

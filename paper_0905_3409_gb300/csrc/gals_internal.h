@@ -1,6 +1,7 @@
 // gals_internal.h -- host-side interface between the C ABI and the kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,7 +19,17 @@ struct StepLaunch {
     int trace;           // TR_EULER / TR_RK3
     int cross_in;        // CROSS_PLANE: read mixed derivatives; CROSS_RECON: rebuild from psi
     int write_cross;     // 1: also write the mixed-derivative planes of the new state
+    const CUtensorMap *tmap4; // TMA map of `in`, box of all 4 planes (2D)
+    const CUtensorMap *tmap3; // TMA map of `in`, box of phi, psi_x, psi_y (2D)
+    int *err;            // device error word (kErrTmaTimeout on a lost tile copy)
 };
+
+// Box of the 2D step kernel's staged tile for np planes.
+void tile_box2d(int np, uint32_t box[3]);
+// Encode a tiled TMA map of FP32 data: rank dims (innermost first), byte strides of
+// dims 1..rank-1, box extents; zero fill outside the tensor.
+cudaError_t make_tile_map(CUtensorMap *map, const float *base, int rank, const uint64_t *dims,
+                          const uint64_t *strides_bytes, const uint32_t *box);
 
 // Kernel launchers; return the launch error (cudaSuccess if launched).
 cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s);

@@ -1,0 +1,203 @@
+// gals_pair.cuh -- the 2D node update for two nodes at once in paired FP32 arithmetic.
+//
+// Blackwell executes fma/add/mul on float2 operands as one instruction (FFMA2 and
+// friends, __ffma2_rn & co.), so a thread that advances two nodes of the same column
+// (rows j and j+1) issues about half the floating-point instructions of two scalar
+// updates, and has twice the independent loads in flight.  Lane x of every float2 is
+// node (i, j), lane y node (i, j+1).  The arithmetic is the one of gals_device.cuh:
+// superconsistent RK3 trace with Jacobian (Sec. 5.1), cell location, bicubic Hermite
+// value and gradient from the nearest-corner-shifted data (Sec. 2.3), J^T grad H.
+// Each lane rounds exactly like a scalar FMA/ADD/MUL chain of the same expression.
+#pragma once
+
+#include "gals_device.cuh"
+
+namespace gals {
+
+typedef float2 F2;
+
+__device__ __forceinline__ F2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return __ffma2_rn(b, bc(-1.f), a); }   // a - b
+__device__ __forceinline__ F2 neg2(F2 a) { return __fmul2_rn(a, bc(-1.f)); }
+
+struct V2p { F2 u, v, d00, d01, d10, d11; };
+
+// per-lane sin(pi s), cos(pi s)
+__device__ __forceinline__ void sincospi2(F2 s, F2 &sn, F2 &cs)
+{
+    sincospi_f(s.x, &sn.x, &cs.x);
+    sincospi_f(s.y, &sn.y, &cs.y);
+}
+
+// Fourier tables duplicated into float2 pairs (both lanes use the same coefficient).
+struct StageCoefPair {
+    F2 A[3][16], Al[3][16], All[3][16];
+};
+
+template <int VK>
+__device__ __forceinline__ V2p vel2d_pair(const VelParams &vp, const StageCoef &sc,
+                                          const StageCoefPair *scp, int stage, F2 x, F2 y)
+{
+    V2p r;
+    if (VK == VK_CONST) {
+        r.u = bc(vp.c0); r.v = bc(vp.c1);
+        r.d00 = r.d01 = r.d10 = r.d11 = bc(0.f);
+    } else if (VK == VK_ROTATION) {
+        const F2 w = bc(vp.omega);
+        r.u = mul2(bc(-vp.omega), sub2(y, bc(vp.cy)));
+        r.v = mul2(w, sub2(x, bc(vp.cx)));
+        r.d00 = bc(0.f); r.d01 = bc(-vp.omega); r.d10 = w; r.d11 = bc(0.f);
+    } else if (VK == VK_VORTEX2D) {
+        F2 sx, cxx, sy, cyy;
+        sincospi2(x, sx, cxx);
+        sincospi2(y, sy, cyy);
+        const float c = sc.mod[stage], cp = c * kPi;
+        const F2 s2x = mul2(bc(2.f), mul2(sx, cxx)), s2y = mul2(bc(2.f), mul2(sy, cyy));
+        const F2 sx2 = mul2(sx, sx), sy2 = mul2(sy, sy);
+        const F2 c2x = fma2(bc(-2.f), sx2, bc(1.f)), c2y = fma2(bc(-2.f), sy2, bc(1.f));
+        r.u = mul2(bc(-c), mul2(sx2, s2y));
+        r.v = mul2(bc(c), mul2(s2x, sy2));
+        r.d00 = mul2(bc(-cp), mul2(s2x, s2y));
+        r.d01 = mul2(bc(-2.f * cp), mul2(sx2, c2y));
+        r.d10 = mul2(bc(2.f * cp), mul2(c2x, sy2));
+        r.d11 = neg2(r.d00);
+    } else if (VK == VK_PSEUDO1D) {
+        const F2 arg = fma2(bc(vp.d0), x, mul2(bc(vp.d1), y));
+        const F2 e = make_float2(__expf(arg.x), __expf(arg.y));
+        r.u = mul2(e, bc(vp.d0)); r.v = mul2(e, bc(vp.d1));
+        r.d00 = mul2(e, bc(vp.d0 * vp.d0)); r.d01 = mul2(e, bc(vp.d0 * vp.d1));
+        r.d10 = r.d01; r.d11 = mul2(e, bc(vp.d1 * vp.d1));
+    } else {  // VK_FOURIER2D: Psi = sum A_kl s_k(x) s_l(y), u = -Psi_y, v = Psi_x
+        F2 s[5], c[5], sy_[5], cy_[5];
+        sincospi2(x, s[1], c[1]);
+        sincospi2(y, sy_[1], cy_[1]);
+        const F2 two = bc(2.f), one = bc(1.f), mtwo = bc(-2.f);
+        s[2] = mul2(two, mul2(s[1], c[1]));            c[2] = fma2(mtwo, mul2(s[1], s[1]), one);
+        s[3] = fma2(s[2], c[1], mul2(c[2], s[1]));     c[3] = fma2(c[2], c[1], neg2(mul2(s[2], s[1])));
+        s[4] = mul2(two, mul2(s[2], c[2]));            c[4] = fma2(mtwo, mul2(s[2], s[2]), one);
+        sy_[2] = mul2(two, mul2(sy_[1], cy_[1]));          cy_[2] = fma2(mtwo, mul2(sy_[1], sy_[1]), one);
+        sy_[3] = fma2(sy_[2], cy_[1], mul2(cy_[2], sy_[1])); cy_[3] = fma2(cy_[2], cy_[1], neg2(mul2(sy_[2], sy_[1])));
+        sy_[4] = mul2(two, mul2(sy_[2], cy_[2]));          cy_[4] = fma2(mtwo, mul2(sy_[2], sy_[2]), one);
+        F2 u = bc(0.f), v = bc(0.f), d00 = bc(0.f), d01 = bc(0.f), d10 = bc(0.f);
+#pragma unroll
+        for (int k = 1; k <= 4; ++k) {
+            F2 Ux = bc(0.f), Vx = bc(0.f), W = bc(0.f);
+#pragma unroll
+            for (int l = 1; l <= 4; ++l) {
+                const int kl = (k - 1) * 4 + (l - 1);
+                Ux = fma2(scp->Al[stage][kl], cy_[l], Ux);
+                Vx = fma2(scp->A[stage][kl], sy_[l], Vx);
+                W = fma2(scp->All[stage][kl], sy_[l], W);
+            }
+            const float kp = (float)k * kPi;
+            u = fma2(neg2(s[k]), Ux, u);
+            v = fma2(mul2(bc(kp), c[k]), Vx, v);
+            d00 = fma2(mul2(bc(-kp), c[k]), Ux, d00);
+            d01 = fma2(s[k], W, d01);
+            d10 = fma2(mul2(bc(-kp * kp), s[k]), Vx, d10);
+        }
+        r.u = u; r.v = v; r.d00 = d00; r.d01 = d01; r.d10 = d10; r.d11 = neg2(d00);
+    }
+    return r;
+}
+
+// Superconsistent trace of Sec. 5.1 for two nodes; a = v(x, t+dt) supplied by the caller.
+template <int TR, int VK>
+__device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
+                                             const StageCoef &sc, const StageCoefPair *scp,
+                                             F2 x, F2 y, float dt, F2 &dx, F2 &dy, F2 J[4])
+{
+    const F2 mdt = bc(-dt), one = bc(1.f);
+    if (TR == TR_EULER) {
+        dx = mul2(mdt, a.u); dy = mul2(mdt, a.v);
+        J[0] = fma2(mdt, a.d00, one); J[1] = mul2(mdt, a.d01);
+        J[2] = mul2(mdt, a.d10);      J[3] = fma2(mdt, a.d11, one);
+        return;
+    }
+    // stage 1: x1 = x - dt v1, J1 = I - dt Dv1
+    const F2 J1_00 = fma2(mdt, a.d00, one), J1_01 = mul2(mdt, a.d01);
+    const F2 J1_10 = mul2(mdt, a.d10), J1_11 = fma2(mdt, a.d11, one);
+    const V2p b = vel2d_pair<VK>(vp, sc, scp, 1, fma2(mdt, a.u, x), fma2(mdt, a.v, y));
+    // M = Dv2 J1
+    const F2 M00 = fma2(b.d00, J1_00, mul2(b.d01, J1_10)), M01 = fma2(b.d00, J1_01, mul2(b.d01, J1_11));
+    const F2 M10 = fma2(b.d10, J1_00, mul2(b.d11, J1_10)), M11 = fma2(b.d10, J1_01, mul2(b.d11, J1_11));
+    // stage 2: x2 = x - dt (v1 + v2)/4, J2 = I - dt (Dv1 + Dv2 J1)/4
+    const F2 mq = bc(-0.25f * dt);
+    const F2 J2_00 = fma2(mq, add2(a.d00, M00), one), J2_01 = mul2(mq, add2(a.d01, M01));
+    const F2 J2_10 = mul2(mq, add2(a.d10, M10)), J2_11 = fma2(mq, add2(a.d11, M11), one);
+    const V2p c = vel2d_pair<VK>(vp, sc, scp, 2, fma2(mq, add2(a.u, b.u), x),
+                                 fma2(mq, add2(a.v, b.v), y));
+    const F2 N00 = fma2(c.d00, J2_00, mul2(c.d01, J2_10)), N01 = fma2(c.d00, J2_01, mul2(c.d01, J2_11));
+    const F2 N10 = fma2(c.d10, J2_00, mul2(c.d11, J2_10)), N11 = fma2(c.d10, J2_01, mul2(c.d11, J2_11));
+    // foot = x - dt (w3 + (w1 + w2 - 2 w3)/6), J = I - dt (N + (Dv1 + M - 2 N)/6): exact for constant v
+    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f);
+    dx = mul2(mdt, fma2(fma2(m2, c.u, add2(a.u, b.u)), i6, c.u));
+    dy = mul2(mdt, fma2(fma2(m2, c.v, add2(a.v, b.v)), i6, c.v));
+    J[0] = fma2(mdt, fma2(fma2(m2, N00, add2(a.d00, M00)), i6, N00), one);
+    J[1] = mul2(mdt, fma2(fma2(m2, N01, add2(a.d01, M01)), i6, N01));
+    J[2] = mul2(mdt, fma2(fma2(m2, N10, add2(a.d10, M10)), i6, N10));
+    J[3] = fma2(mdt, fma2(fma2(m2, N11, add2(a.d11, M11)), i6, N11), one);
+}
+
+// Paired 1D basis (see basis1): near = xi >= 1/2 evaluates the value part from the
+// nearer end so that xi = 0 or 1 reproduce node data exactly.
+struct Basis2 { F2 Sn, dS, hG0, hG1, dG0, dG1; bool n0, n1; };
+
+__device__ __forceinline__ Basis2 basis_pair(F2 xi, float h, float ih)
+{
+    Basis2 b;
+    const F2 om = fma2(xi, bc(-1.f), bc(1.f));
+    const F2 xx = mul2(xi, xi), xo = mul2(xi, om);
+    const F2 S = mul2(xx, fma2(bc(-2.f), xi, bc(3.f)));
+    b.n0 = xi.x >= 0.5f;
+    b.n1 = xi.y >= 0.5f;
+    b.Sn = add2(S, make_float2(b.n0 ? -1.f : 0.f, b.n1 ? -1.f : 0.f));
+    b.dS = mul2(xo, bc(6.f * ih));
+    b.hG0 = mul2(mul2(xo, om), bc(h));
+    b.hG1 = mul2(mul2(om, xx), bc(-h));
+    b.dG0 = mul2(om, fma2(bc(-3.f), xi, bc(1.f)));
+    b.dG1 = mul2(xi, fma2(bc(3.f), xi, bc(-2.f)));
+    return b;
+}
+
+__device__ __forceinline__ F2 pick(const Basis2 &b, F2 p0, F2 p1)
+{
+    return make_float2(b.n0 ? p1.x : p0.x, b.n1 ? p1.y : p0.y);
+}
+
+__device__ __forceinline__ F2 hval2(const Basis2 &b, F2 p0, F2 p1, F2 s0, F2 s1)
+{
+    return fma2(sub2(p1, p0), b.Sn, fma2(s0, b.hG0, fma2(s1, b.hG1, pick(b, p0, p1))));
+}
+__device__ __forceinline__ F2 hder2(const Basis2 &b, F2 p0, F2 p1, F2 s0, F2 s1)
+{
+    return fma2(sub2(p1, p0), b.dS, fma2(s0, b.dG0, mul2(s1, b.dG1)));
+}
+
+// c[v][a]: corner v = vx + 2 vy, data a = 0 phi, 1 phi_x, 2 phi_y, 3 phi_xy (both lanes)
+__device__ __forceinline__ void hermite2d_pair(const F2 c[4][4], const Basis2 &bx,
+                                               const Basis2 &by, F2 &H, F2 &Hx, F2 &Hy)
+{
+    // phi of the corner nearest to each foot
+    const F2 b0 = pick(bx, c[0][0], c[1][0]);
+    const F2 b1 = pick(bx, c[2][0], c[3][0]);
+    const F2 base = pick(by, b0, b1);
+    const F2 p00 = sub2(c[0][0], base), p10 = sub2(c[1][0], base);
+    const F2 p01 = sub2(c[2][0], base), p11 = sub2(c[3][0], base);
+    const F2 P0 = hval2(bx, p00, p10, c[0][1], c[1][1]);
+    const F2 P1 = hval2(bx, p01, p11, c[2][1], c[3][1]);
+    const F2 Pd0 = hder2(bx, p00, p10, c[0][1], c[1][1]);
+    const F2 Pd1 = hder2(bx, p01, p11, c[2][1], c[3][1]);
+    const F2 Q0 = hval2(bx, c[0][2], c[1][2], c[0][3], c[1][3]);
+    const F2 Q1 = hval2(bx, c[2][2], c[3][2], c[2][3], c[3][3]);
+    const F2 Qd0 = hder2(bx, c[0][2], c[1][2], c[0][3], c[1][3]);
+    const F2 Qd1 = hder2(bx, c[2][2], c[3][2], c[2][3], c[3][3]);
+    H = add2(base, hval2(by, P0, P1, Q0, Q1));
+    Hy = hder2(by, P0, P1, Q0, Q1);
+    Hx = hval2(by, Pd0, Pd1, Qd0, Qd1);
+}
+
+}  // namespace gals
