@@ -47,6 +47,16 @@ WORKLOADS = {
     "deform512": dict(dim=3, n=(512, 512, 512), vel=dict(kind="deform3d", T=3.0), vmax=2.0,
                       desc="3D GALS 512^3 nodes on [0,1]^3, FP32, LeVeque deformation T=3, "
                            "sphere SDF r=0.15 at (0.35,0.35,0.35), RK3 trace, CFL 1"),
+    "batch256": dict(dim=2, n=None, batch=256, vel=dict(kind="fourier2d"), vmax=None,
+                     desc="Batched 2D GALS, FP32: 256 independent problems, side lengths uniform "
+                          "in [128,1024] (seed 9053409), each an ellipse SDF advected by its own "
+                          "steady 8-mode Fourier stream-function field, RK3 trace, CFL 1; one "
+                          "launch per step over all problems' tiles, CUDA-graph time loop, "
+                          "autotuned launch shape"),
+    # a smaller case of the same 3D kernel, for profiler captures (state still > L2)
+    "deform256": dict(dim=3, n=(256, 256, 256), vel=dict(kind="deform3d", T=3.0), vmax=2.0,
+                      desc="3D GALS 256^3 nodes on [0,1]^3, FP32, LeVeque deformation T=3, "
+                           "sphere SDF r=0.15 at (0.35,0.35,0.35), RK3 trace, CFL 1"),
 }
 
 
@@ -74,7 +84,7 @@ def initial_state(wl):
         else:
             st = inputs.circle_sdf(n)
     else:
-        st = inputs.sphere_sdf(n)
+        return inputs.sphere_sdf(n, dtype=np.float32)
     return st.astype(np.float32)
 
 
@@ -159,17 +169,28 @@ def recorded_traffic(workload, layout):
 
 # ---------------------------------------------------------------------- CPU oracle leg
 
+def oracle_state(wl, g, slab=None):
+    """FP64 initial state for the oracle.  In 3D only the z-slices of `slab` (with a
+    margin of 2 for the feet) are filled: a band update reads nothing else."""
+    import oracle
+    from paper_0905_3409_gb300 import inputs
+    n = wl["n"]
+    if wl["dim"] == 2:
+        return oracle.recon_cross(g, initial_state(wl).astype(np.float64))
+    st = np.zeros((8, n[2], n[1], n[0]))
+    z0, z1 = max(slab[0] - 2, 0), min(slab[1] + 2, n[2])
+    st[:, z0:z1] = inputs.sphere_sdf(n, z_range=(z0, z1))
+    return st
+
+
 def oracle_leg(wl, budget_s=12.0, max_bands=None):
     """Time the FP64 oracle on row bands (2D) / z-slabs (3D) of the workload: each band
     is an exact, independent part of one step.  Returns (node-updates/s, cores, sample)."""
     import oracle
     n = wl["n"]
-    st = initial_state(wl).astype(np.float64)
-    from paper_0905_3409_gb300 import inputs  # noqa: F401
-    if wl["dim"] == 2:
-        from paper_0905_3409_gb300.inputs import node_coords  # noqa: F401
     g = oracle.grid(n)
-    st = oracle.recon_cross(g, st) if wl["dim"] == 2 else st
+    band3 = (n[-1] // 3, n[-1] // 3 + 8)
+    st = oracle_state(wl, g, band3)
     v = wl["vel"]
     ov = oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
                          center=v.get("center", (0.5, 0.5, 0.5)))
@@ -179,7 +200,7 @@ def oracle_leg(wl, budget_s=12.0, max_bands=None):
     cores = oracle.default_threads()
     outer = n[-1]
     inner_nodes = int(np.prod(n[:-1]))
-    band = 64 if wl["dim"] == 2 else 2
+    band = 64 if wl["dim"] == 2 else 1
     done = 0
     nodes = 0
     t0 = time.perf_counter()
@@ -191,7 +212,11 @@ def oracle_leg(wl, budget_s=12.0, max_bands=None):
         el = time.perf_counter() - t0
         if el > budget_s or (max_bands and done >= max_bands):
             break
-        b0 = (b0 + band) % (outer - band)
+        b0 = b0 + band
+        if wl["dim"] == 2:
+            b0 %= outer - band
+        elif b0 + band > band3[1]:
+            b0 = band3[0]
     return nodes / el, cores, f"{done} bands of {band} {'rows' if wl['dim'] == 2 else 'z-slices'} " \
                               f"({nodes} node updates, one step each) of the {n} grid in {el:.1f} s"
 
@@ -203,9 +228,9 @@ def run_reference(args, wl):
     import oracle
     n = wl["n"]
     g = oracle.grid(n)
-    st = initial_state(wl).astype(np.float64)
-    if wl["dim"] == 2:
-        st = oracle.recon_cross(g, st)
+    band = 8 if wl["dim"] == 2 else 1
+    slab = (n[-1] // 4, n[-1] // 4 + 16)
+    st = oracle_state(wl, g, slab)
     v = wl["vel"]
     ov = oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
                          center=v.get("center", (0.5, 0.5, 0.5)))
@@ -215,13 +240,16 @@ def run_reference(args, wl):
     outer = n[-1]
     inner_nodes = int(np.prod(n[:-1]))
     # each reference step: one band of the grid, sized to keep the run within minutes
-    band = 8 if wl["dim"] == 2 else 1
+    def band_at(s):
+        if wl["dim"] == 2:
+            return (outer // 4 + s * band) % (outer - band)
+        return slab[0] + (s * band) % (slab[1] - slab[0])
     for s in range(args.warmup):
-        oracle.step_band(g, ov, None, 0.0, dt, (s * band) % (outer - band), (s * band) % (outer - band) + band,
-                         planes=planes)
+        b0 = band_at(s)
+        oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        b0 = (outer // 4 + s * band) % (outer - band)
+        b0 = band_at(s)
         oracle.step_band(g, ov, None, s * dt, dt, b0, b0 + band, planes=planes)
     el = time.perf_counter() - t0
     nodes = args.steps * band * inner_nodes
@@ -235,6 +263,177 @@ def run_reference(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": wl["desc"] + " (FP64 CPU oracle)", "nodes_per_step_sample": band * inner_nodes},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------- batched mode
+
+def _batch_state(args):
+    """Initial state of one batch problem (top level: runs in a spawn pool)."""
+    n, center, a, b, angle = args
+    sys.path.insert(0, ROOT)
+    from paper_0905_3409_gb300 import inputs
+    return inputs.ellipse_sdf((n, n), center, a, b, angle, iters=50).astype(np.float32)
+
+
+def batch_inputs(count):
+    import multiprocessing as mp
+    from paper_0905_3409_gb300 import inputs
+    probs = inputs.batch_problems(count)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
+        states = pool.map(_batch_state, [(p.n, p.center, p.a, p.b, p.angle) for p in probs])
+    return probs, states
+
+
+def batch_oracle_leg(probs, states, budget_s=10.0):
+    """FP64 oracle on bands of rows of the largest problems, one step each."""
+    import oracle
+    order = sorted(range(len(probs)), key=lambda k: -probs[k].n)[:4]
+    nodes, t_used, done = 0, 0.0, 0
+    for k in order:
+        p = probs[k]
+        g = oracle.grid((p.n, p.n))
+        st = oracle.recon_cross(g, states[k].astype(np.float64))
+        ov = oracle.velocity("fourier2d", modes=p.modes)
+        planes = oracle.state_planes(g, st)
+        t0 = time.perf_counter()
+        b0 = p.n // 3
+        while time.perf_counter() - t0 < budget_s / len(order):
+            oracle.step_band(g, ov, None, 0.0, p.dt, b0, b0 + 16, planes=planes)
+            nodes += 16 * p.n
+            done += 1
+            b0 = (b0 + 16) % (p.n - 16)
+        t_used += time.perf_counter() - t0
+    return nodes / t_used, oracle.default_threads(), \
+        f"{done} bands of 16 rows of the 4 largest problems ({nodes} node updates, one step each)"
+
+
+def run_batch(args, wl):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    probs, states = batch_inputs(wl["batch"])  # before any CUDA work (spawned pool)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if dist:
+        dist.barrier()
+    from paper_0905_3409_gb300 import gals
+    stream = torch.cuda.Stream()
+    sizes = [(p.n, p.n) for p in probs]
+    b = gals.Batch(sizes, layout=args.layout, stream=stream)
+    for k, st in enumerate(states):
+        b.set_state(k, st, recon=True)
+    vels = [gals.Velocity("fourier2d", modes=p.modes) for p in probs]
+    dts = [p.dt for p in probs]
+    tuning = b.autotune(vels, dts, trial_steps=3)
+    nodes = b.nodes
+    b.step(vels, dts, args.warmup)
+    b.step(vels, dts, args.steps)  # captures the timed graph
+    b.synchronize()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(vels, dts, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if rank == 0 else None
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = nodes * args.steps * world / (ms * 1e-3)
+    bpn = bytes_per_node(2, args.layout)
+    achieved = bpn * nodes / (ms * 1e-3 / args.steps) / 1e9
+    peak, peak_kind = measured_peaks()
+    # e2e: per step, every problem's state from pinned host memory, one batched step,
+    # every state back to pinned host memory
+    pins = [torch.from_numpy(st).pin_memory() for st in states]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, pin in enumerate(pins):
+            b.set_state(k, pin.numpy(), recon=False)
+        b.step(vels, dts, 1)
+        for k in range(len(sizes)):
+            b.read_state(k)
+    el = time.perf_counter() - t0
+    io_bytes = 16 * nodes
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "layout": args.layout, "problems": len(sizes),
+                       "nodes": nodes, "bytes_per_node_update": bpn, "tuning": tuning,
+                       "l2": f"inputs larger than L2 ({nodes * 16 / 1e6:.0f} MB state per buffer)",
+                       "parallelism": f"{world} independent replica(s), one per GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(args.workload, args.layout),
+                         "peak_source": peak_kind, "kernel": "k_batch2d (1 launch per step)"},
+            "e2e": {"value": nodes * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": args.steps + 2,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, cores, sample = batch_oracle_leg(probs, states, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line))
+    b.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference_batch(args, wl):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    import oracle
+    from paper_0905_3409_gb300 import inputs
+    probs = inputs.batch_problems(wl["batch"])
+    p = max(probs, key=lambda q: q.n)
+    st = inputs.ellipse_sdf((p.n, p.n), p.center, p.a, p.b, p.angle, iters=50)
+    g = oracle.grid((p.n, p.n))
+    planes = oracle.state_planes(g, oracle.recon_cross(g, st))
+    ov = oracle.velocity("fourier2d", modes=p.modes)
+    band = 8
+    for s in range(args.warmup):
+        oracle.step_band(g, ov, None, 0.0, p.dt, 8 * s % (p.n - band), 8 * s % (p.n - band) + band, planes=planes)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        b0 = (p.n // 4 + s * band) % (p.n - band)
+        oracle.step_band(g, ov, None, s * p.dt, p.dt, b0, b0 + band, planes=planes)
+    el = time.perf_counter() - t0
+    value = args.steps * band * p.n / el
+    cores = oracle.default_threads()
+    sample = f"each step: one band of {band} rows of the largest problem ({p.n}^2)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl["desc"] + " (FP64 CPU oracle)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -376,7 +575,12 @@ def main():
         args.warmup = 3
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
-        run_reference(args, wl)
+        if wl.get("batch"):
+            run_reference_batch(args, wl)
+        else:
+            run_reference(args, wl)
+    elif wl.get("batch"):
+        run_batch(args, wl)
     else:
         run_ours(args, wl)
 

@@ -182,6 +182,61 @@ const char *gals_last_error(const gals_grid *grid);
 /* Library version string. */
 const char *gals_version(void);
 
+/* ------------------------------------------------------------------------------------
+ * Batched 2D mode: many independent problems of uneven size advanced together, one
+ * kernel launch per step over a work list of (problem, tile) items; runs of steps are
+ * replayed from a cached CUDA graph.  Each problem evolves exactly as it would on its own
+ * grid (same per-node arithmetic, Sec. 4 / Sec. 5.1), with its own velocity and time
+ * step.  This mode is not in the paper: it batches the paper's step for throughput.
+ * ------------------------------------------------------------------------------------ */
+typedef struct gals_batch gals_batch;   /* opaque, owned by the library */
+
+/* Create a batch of `count` 2D problems.  All descriptors must have dim 2 and the same
+ * layout; the stream of descs[0] (or a library stream if NULL) orders all work.
+ * Errors: GALS_ERR_ARG (count < 1, a descriptor invalid as for gals_create_grid),
+ * GALS_ERR_NOMEM, GALS_ERR_CUDA. */
+gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch **out);
+gals_status gals_destroy_batch(gals_batch *batch);
+
+/* Load problem `index` (0-based); arguments as gals_set_state.  In the COMPACT layout the
+ * mixed derivatives are always rebuilt from the gradients. */
+gals_status gals_batch_set_state(gals_batch *batch, int index, const float *const *fields,
+                                 int nfields, int memspace, double t0, int flags);
+
+/* Advance every problem nsteps steps: vels[p] and dt[p] for problem p (host arrays of
+ * count entries).  All velocities must have the same kind (FOURIER2D, VORTEX2D or
+ * ROTATION) and the RK3 trace.  Asynchronous.  Errors: GALS_ERR_ARG, GALS_ERR_STATE (a
+ * problem without state), GALS_ERR_UNSUPPORTED (kind or trace), GALS_ERR_CUDA. */
+gals_status gals_batch_step(gals_batch *batch, const gals_velocity *vels, const double *dt,
+                            int nsteps);
+
+/* Copy problem `index`'s state out (synchronises); arguments as gals_read_state. */
+gals_status gals_batch_read_state(gals_batch *batch, int index, float *const *fields,
+                                  int nfields, int memspace);
+
+gals_status gals_batch_synchronize(gals_batch *batch);
+
+/* Launch shape of the batched step kernel. */
+typedef struct {
+    int variant;          /* 0: tiles of 128 x 8 nodes, 1: 128 x 16 */
+    int blocks;           /* blocks per launch; 0 = one per tile, else persistent blocks */
+    double ms_per_step;   /* measured by gals_batch_autotune (0 if set by hand) */
+} gals_batch_tuning;
+
+/* Time every candidate launch shape (tile variant x {one block per tile, persistent
+ * grids of 1..occupancy blocks per SM}) for trial_steps steps on the current states
+ * (which are left unchanged) and keep the fastest; out (optional) receives it.
+ * Synchronises.  Errors as gals_batch_step. */
+gals_status gals_batch_autotune(gals_batch *batch, const gals_velocity *vels, const double *dt,
+                                int trial_steps, gals_batch_tuning *out);
+gals_status gals_batch_set_tuning(gals_batch *batch, const gals_batch_tuning *tuning);
+gals_status gals_batch_get_tuning(const gals_batch *batch, gals_batch_tuning *tuning);
+
+/* Total number of grid nodes over all problems (node updates per batched step). */
+int64_t gals_batch_nodes(const gals_batch *batch);
+
+const char *gals_batch_last_error(const gals_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@
 
 #include "../../include/gals.h"
 #include "gals_internal.h"
+#include "capi_internal.h"
 
 using namespace gals;
 
@@ -48,7 +49,7 @@ struct gals_grid {
     double t = 0.0;
     int64_t steps = 0;
     double *t_dev = nullptr;
-    CUtensorMap maps[2][2];       // 2D TMA maps per buffer: [b][0] 3 planes, [b][1] 4 planes
+    CUtensorMap maps[2][2];       // TMA maps per buffer: [b][0] COMPACT box, [b][1] FULL box
     int *err_dev = nullptr;       // device error word written by kernels (bounded waits)
     StageCoef *coef = nullptr;    // per-step stage coefficients of the current call
     int coef_cap = 0;
@@ -89,42 +90,9 @@ bool finite3(const double *v, int n)
 
 gals_status make_velparams(gals_grid *g, const gals_velocity *v, VelParams &vp)
 {
-    std::memset(&vp, 0, sizeof(vp));
-    if (!v) return fail(g, GALS_ERR_ARG, "velocity descriptor is NULL");
-    if (v->trace != GALS_TRACE_EULER && v->trace != GALS_TRACE_RK3)
-        return fail(g, GALS_ERR_ARG, "unknown trace scheme %d", v->trace);
-    if (!vel_supported(g->dim, v->kind))
-        return fail(g, GALS_ERR_UNSUPPORTED, "velocity kind %d not available in %dD", v->kind, g->dim);
-    if (!finite3(v->c, 3) || !finite3(v->center, 3) || !std::isfinite(v->omega) || !std::isfinite(v->T))
-        return fail(g, GALS_ERR_ARG, "non-finite velocity parameter");
-    vp.kind = v->kind;
-    vp.omega = (float)v->omega;
-    vp.cx = (float)v->center[0]; vp.cy = (float)v->center[1]; vp.cz = (float)v->center[2];
-    vp.c0 = (float)v->c[0]; vp.c1 = (float)v->c[1]; vp.c2 = (float)v->c[2];
-    const double nrm = std::sqrt(2.0 + M_PI);
-    vp.d0 = (float)(std::sqrt(2.0) / nrm);
-    vp.d1 = (float)(std::sqrt(M_PI) / nrm);
-    if (v->kind == GALS_VEL_VORTEX2D || v->kind == GALS_VEL_DEFORM3D) {
-        if (!(v->T > 0.0)) return fail(g, GALS_ERR_ARG, "modulation period T must be > 0");
-        vp.invT = 1.0 / v->T;
-    }
-    if (v->kind == GALS_VEL_FOURIER2D) {
-        if (v->nmodes < 1 || v->nmodes > GALS_MAX_MODES || !v->modes)
-            return fail(g, GALS_ERR_ARG, "FOURIER2D needs 1..%d modes", GALS_MAX_MODES);
-        vp.nmodes = v->nmodes;
-        for (int m = 0; m < v->nmodes; ++m) {
-            const double *md = v->modes + 5 * m;
-            if (!finite3(md, 5)) return fail(g, GALS_ERR_ARG, "non-finite mode %d", m);
-            int k = (int)md[1], l = (int)md[2];
-            if (k != md[1] || l != md[2] || k < 1 || k > 4 || l < 1 || l > 4)
-                return fail(g, GALS_ERR_ARG, "mode %d: k, l must be integers in 1..4", m);
-            if (md[3] < 0) return fail(g, GALS_ERR_ARG, "mode %d: n must be >= 0", m);
-            vp.mode_a[m] = (float)md[0];
-            vp.mode_kl[m] = k | (l << 8);
-            vp.mode_n[m] = md[3];
-            vp.mode_chi[m] = md[4] / (2.0 * M_PI);
-        }
-    }
+    char msg[200];
+    gals_status st = gals::velparams_from(g->dim, v, vp, msg, sizeof(msg));
+    if (st != GALS_OK) return fail(g, st, "%s", msg);
     return GALS_OK;
 }
 
@@ -243,22 +211,31 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
         gals_destroy_grid(g);
         return st;
     }
-    if (g->dim == 2) {
-        // TMA maps of each buffer: (x, y, plane) with the step kernel's tile box
-        for (int b = 0; b < 2; ++b)
-            for (int v = 0; v < 2; ++v) {
+    // TMA maps of each buffer with the step kernels' tile boxes:
+    // 2D (x, y, plane), 3D (x, y, z, plane)
+    for (int b = 0; b < 2; ++b)
+        for (int v = 0; v < 2; ++v) {
+            if (g->dim == 2) {
                 const int np = v == 0 ? 3 : 4;
                 const uint64_t dims[3] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)np};
                 const uint64_t strides[2] = {(uint64_t)G.pitch * 4, (uint64_t)G.plane * 4};
                 uint32_t box[3];
                 tile_box2d(np, box);
-                if ((e = make_tile_map(&g->maps[b][v], g->buf[b], 3, dims, strides, box)) != cudaSuccess) {
-                    gals_status st = cuda_fail(nullptr, e, "TMA descriptor");
-                    gals_destroy_grid(g);
-                    return st;
-                }
+                e = make_tile_map(&g->maps[b][v], g->buf[b], 3, dims, strides, box);
+            } else {
+                uint32_t box[4];
+                tile_box3d(v == 0, box);
+                const uint64_t dims[4] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)G.n2, (uint64_t)box[3]};
+                const uint64_t strides[3] = {(uint64_t)G.pitch * 4, (uint64_t)G.pitch * G.n1 * 4,
+                                             (uint64_t)G.plane * 4};
+                e = make_tile_map(&g->maps[b][v], g->buf[b], 4, dims, strides, box);
             }
-    }
+            if (e != cudaSuccess) {
+                gals_status st = cuda_fail(nullptr, e, "TMA descriptor");
+                gals_destroy_grid(g);
+                return st;
+            }
+        }
     // zero both buffers so that pitch padding never holds garbage
     for (int b = 0; b < 2; ++b)
         if ((e = cudaMemsetAsync(g->buf[b], 0, bytes, g->stream)) != cudaSuccess) {

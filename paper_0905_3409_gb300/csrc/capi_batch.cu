@@ -1,0 +1,520 @@
+// capi_batch.cu -- C ABI of the batched 2D mode (include/gals.h, gals_batch_*).
+//
+// All problems share one allocation per ping-pong buffer (problem p's planes at offset
+// off_p, each with its own row pitch and plane stride), one TMA map per problem and buffer,
+// a device table of problem descriptors and a work list of 128 x TY tiles sorted by
+// problem size (largest first).  gals_batch_step fills the per-step, per-problem stage
+// coefficients from each problem's device clock, issues one batched launch per step and
+// advances the clocks; runs of steps are captured once into a CUDA graph.  The launch
+// shape (tile height, one block per tile or persistent blocks) comes from the autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "batch_internal.h"
+#include "capi_internal.h"
+
+using namespace gals;
+
+namespace {
+
+char g_batch_create_err[256] = "";
+
+struct BatchGraph {
+    int nsteps, cur, variant, blocks;
+    std::vector<VelParams> vps;
+    std::vector<double> dts;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct gals_batch {
+    int count = 0;
+    int layout = GALS_LAYOUT_FULL;
+    std::vector<gals_grid_desc> descs;
+    std::vector<BatchProb> probs;          // host copy of the descriptors
+    std::vector<int> has_state;
+    int64_t total_floats = 0, nodes = 0;
+    float *buf[2] = {nullptr, nullptr};
+    BatchProb *probs_dev = nullptr;
+    VelParams *vps_dev = nullptr;
+    double *t_dev = nullptr;
+    std::vector<double> t_host;
+    std::vector<int64_t> steps;
+    CUtensorMap *maps_dev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [variant][buffer]
+    BatchItem *items_dev[2] = {nullptr, nullptr};                             // per variant
+    int nitems[2] = {0, 0};
+    StageCoef *coef = nullptr;
+    int64_t coef_cap = 0;
+    int *err_dev = nullptr;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    gals_batch_tuning tuning{1, 0, 0.0};
+    std::vector<BatchGraph> graphs;
+    char err[256] = "";
+};
+
+namespace {
+
+gals_status bfail(gals_batch *b, gals_status st, const char *fmt, ...)
+{
+    char *dst = b ? b->err : g_batch_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+gals_status bcuda(gals_batch *b, cudaError_t e, const char *what)
+{
+    return bfail(b, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+void drop_graphs(gals_batch *b)
+{
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
+// Validate the per-problem velocities and dt, fill host VelParams.
+gals_status prepare(gals_batch *b, const gals_velocity *vels, const double *dt,
+                    std::vector<VelParams> &vps)
+{
+    if (!vels || !dt) return bfail(b, GALS_ERR_ARG, "vels/dt is NULL");
+    vps.resize(b->count);
+    for (int p = 0; p < b->count; ++p) {
+        char msg[200];
+        gals_status st = velparams_from(2, &vels[p], vps[p], msg, sizeof(msg));
+        if (st != GALS_OK) return bfail(b, st, "problem %d: %s", p, msg);
+        if (vels[p].kind != vels[0].kind)
+            return bfail(b, GALS_ERR_ARG, "problem %d: all problems must share the velocity kind", p);
+        if (vels[p].trace != GALS_TRACE_RK3)
+            return bfail(b, GALS_ERR_UNSUPPORTED, "problem %d: the batched mode uses the RK3 trace", p);
+        if (!(dt[p] > 0.0) || !std::isfinite(dt[p]))
+            return bfail(b, GALS_ERR_ARG, "problem %d: dt must be finite and > 0", p);
+        if (!b->has_state[p]) return bfail(b, GALS_ERR_STATE, "problem %d has no state", p);
+    }
+    if (!batch_kind_supported(vels[0].kind))
+        return bfail(b, GALS_ERR_UNSUPPORTED, "velocity kind %d not available in the batched mode",
+                     vels[0].kind);
+    return GALS_OK;
+}
+
+// Upload per-problem dt (into the descriptors) and velocity parameters.
+cudaError_t upload_params(gals_batch *b, const std::vector<VelParams> &vps, const double *dt)
+{
+    for (int p = 0; p < b->count; ++p) {
+        b->probs[p].dt = (float)dt[p];
+        b->probs[p].dt_d = dt[p];
+    }
+    cudaError_t e = cudaMemcpyAsync(b->probs_dev, b->probs.data(), sizeof(BatchProb) * b->count,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(b->vps_dev, vps.data(), sizeof(VelParams) * b->count, cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(b->stream);  // host sources are temporaries
+}
+
+cudaError_t ensure_coef(gals_batch *b, int nsteps)
+{
+    const int64_t need = (int64_t)nsteps * b->count;
+    if (need <= b->coef_cap) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return e;
+    drop_graphs(b);
+    cudaFree(b->coef);
+    b->coef = nullptr;
+    b->coef_cap = 0;
+    e = cudaMalloc(&b->coef, sizeof(StageCoef) * (size_t)need);
+    if (e == cudaSuccess) b->coef_cap = need;
+    return e;
+}
+
+BatchLaunch make_launch(gals_batch *b, int src, int variant, int blocks, int step, int kind)
+{
+    BatchLaunch a;
+    a.in = b->buf[src];
+    a.out = b->buf[src ^ 1];
+    a.probs = b->probs_dev;
+    a.vps = b->vps_dev;
+    a.coef = b->coef + (int64_t)step * b->count;
+    a.maps = b->maps_dev[variant][src];
+    a.items = b->items_dev[variant];
+    a.nitems = b->nitems[variant];
+    a.grid = blocks > 0 ? std::min(blocks, a.nitems) : 0;
+    a.variant = variant;
+    a.kind = kind;
+    a.compact = b->layout == GALS_LAYOUT_COMPACT;
+    a.err = b->err_dev;
+    return a;
+}
+
+cudaError_t issue(gals_batch *b, int kind, int nsteps)
+{
+    cudaError_t e = launch_batch_coef(b->coef, b->vps_dev, b->t_dev, b->probs_dev, b->count, nsteps,
+                                      b->stream);
+    if (e != cudaSuccess) return e;
+    int src = b->cur;
+    for (int s = 0; s < nsteps; ++s) {
+        e = launch_batch2d(make_launch(b, src, b->tuning.variant, b->tuning.blocks, s, kind), b->stream);
+        if (e != cudaSuccess) return e;
+        src ^= 1;
+    }
+    return launch_batch_advance(b->t_dev, b->probs_dev, b->count, nsteps, b->stream);
+}
+
+gals_status check_err(gals_batch *b)
+{
+    int code = 0;
+    cudaError_t e = cudaMemcpy(&code, b->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "error word");
+    if (code == 0) return GALS_OK;
+    cudaMemset(b->err_dev, 0, sizeof(int));
+    return bfail(b, GALS_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", code);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gals_batch_last_error(const gals_batch *b) { return b ? b->err : g_batch_create_err; }
+
+int64_t gals_batch_nodes(const gals_batch *b) { return b ? b->nodes : 0; }
+
+gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch **out)
+{
+    if (!out) return bfail(nullptr, GALS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || count < 1) return bfail(nullptr, GALS_ERR_ARG, "need count >= 1 descriptors");
+    for (int p = 0; p < count; ++p) {
+        const gals_grid_desc &d = descs[p];
+        if (d.dim != 2) return bfail(nullptr, GALS_ERR_ARG, "problem %d: the batched mode is 2D", p);
+        if (d.layout != descs[0].layout || (d.layout != GALS_LAYOUT_FULL && d.layout != GALS_LAYOUT_COMPACT))
+            return bfail(nullptr, GALS_ERR_ARG, "problem %d: layouts must agree", p);
+        for (int i = 0; i < 2; ++i) {
+            if (d.n[i] < 4) return bfail(nullptr, GALS_ERR_ARG, "problem %d: n[%d] < 4", p, i);
+            if (!std::isfinite(d.lo[i]) || !std::isfinite(d.hi[i]) || !(d.hi[i] > d.lo[i]))
+                return bfail(nullptr, GALS_ERR_ARG, "problem %d: need finite lo < hi", p);
+        }
+    }
+    gals_batch *b = new (std::nothrow) gals_batch();
+    if (!b) return bfail(nullptr, GALS_ERR_NOMEM, "host allocation failed");
+    b->count = count;
+    b->layout = descs[0].layout;
+    b->descs.assign(descs, descs + count);
+    b->probs.resize(count);
+    b->has_state.assign(count, 0);
+    b->t_host.assign(count, 0.0);
+    b->steps.assign(count, 0);
+    int64_t off = 0;
+    for (int p = 0; p < count; ++p) {
+        const gals_grid_desc &d = descs[p];
+        BatchProb &P = b->probs[p];
+        Geom &G = P.g;
+        std::memset(&P, 0, sizeof(P));
+        const double h0 = (d.hi[0] - d.lo[0]) / (d.n[0] - 1), h1 = (d.hi[1] - d.lo[1]) / (d.n[1] - 1);
+        G.n0 = d.n[0]; G.n1 = d.n[1]; G.n2 = 1;
+        G.pitch = (d.n[0] + 3) / 4 * 4;
+        G.plane = ((int64_t)G.pitch * G.n1 + 63) / 64 * 64;
+        G.h0 = (float)h0; G.h1 = (float)h1; G.h2 = 1.f;
+        G.ih0 = (float)(1.0 / h0); G.ih1 = (float)(1.0 / h1); G.ih2 = 1.f;
+        G.i2h0 = (float)(0.5 / h0); G.i2h1 = (float)(0.5 / h1); G.i2h2 = 0.5f;
+        G.lo0 = (float)d.lo[0]; G.lo1 = (float)d.lo[1]; G.lo2 = 0.f;
+        P.off = off;
+        off += 4 * G.plane;
+        b->nodes += (int64_t)d.n[0] * d.n[1];
+    }
+    b->total_floats = off;
+    cudaError_t e;
+    auto bail = [&](cudaError_t err, const char *what) {
+        gals_status st = bcuda(nullptr, err, what);
+        gals_destroy_batch(b);
+        return st;
+    };
+    if (descs[0].cuda_stream) {
+        b->stream = (cudaStream_t)descs[0].cuda_stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e, "cudaStreamCreate");
+        b->own_stream = true;
+    }
+    for (int s = 0; s < 2; ++s) {
+        if ((e = cudaMalloc(&b->buf[s], sizeof(float) * (size_t)off)) != cudaSuccess) return bail(e, "cudaMalloc(state)");
+        if ((e = cudaMemsetAsync(b->buf[s], 0, sizeof(float) * (size_t)off, b->stream)) != cudaSuccess)
+            return bail(e, "cudaMemset");
+    }
+    if ((e = cudaMalloc(&b->probs_dev, sizeof(BatchProb) * count)) != cudaSuccess ||
+        (e = cudaMalloc(&b->vps_dev, sizeof(VelParams) * count)) != cudaSuccess ||
+        (e = cudaMalloc(&b->t_dev, sizeof(double) * count)) != cudaSuccess ||
+        (e = cudaMalloc(&b->err_dev, sizeof(int))) != cudaSuccess)
+        return bail(e, "cudaMalloc(descriptors)");
+    if ((e = cudaMemsetAsync(b->err_dev, 0, sizeof(int), b->stream)) != cudaSuccess) return bail(e, "cudaMemset");
+    if ((e = cudaMemcpyAsync(b->probs_dev, b->probs.data(), sizeof(BatchProb) * count, cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess)
+        return bail(e, "descriptor upload");
+
+    // per tile variant: work list (largest problems first) and TMA maps per buffer
+    const int np = b->layout == GALS_LAYOUT_COMPACT ? 3 : 4;
+    std::vector<int> order(count);
+    for (int p = 0; p < count; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (int64_t)descs[a].n[0] * descs[a].n[1] > (int64_t)descs[c].n[0] * descs[c].n[1];
+    });
+    for (int v = 0; v < 2; ++v) {
+        const int ty = batch_tile_rows(v);
+        std::vector<BatchItem> items;
+        for (int p : order)
+            for (int y0 = 0; y0 < descs[p].n[1]; y0 += ty)
+                for (int x0 = 0; x0 < descs[p].n[0]; x0 += 128) items.push_back(BatchItem{p, x0, y0});
+        b->nitems[v] = (int)items.size();
+        if ((e = cudaMalloc(&b->items_dev[v], sizeof(BatchItem) * items.size())) != cudaSuccess)
+            return bail(e, "cudaMalloc(work list)");
+        if ((e = cudaMemcpy(b->items_dev[v], items.data(), sizeof(BatchItem) * items.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "work list upload");
+        uint32_t box[3];
+        batch_tile_box(v, np, box);
+        for (int s = 0; s < 2; ++s) {
+            std::vector<CUtensorMap> maps(count);
+            for (int p = 0; p < count; ++p) {
+                const Geom &G = b->probs[p].g;
+                const uint64_t dims[3] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)np};
+                const uint64_t strides[2] = {(uint64_t)G.pitch * 4, (uint64_t)G.plane * 4};
+                if ((e = make_tile_map(&maps[p], b->buf[s] + b->probs[p].off, 3, dims, strides, box)) != cudaSuccess)
+                    return bail(e, "TMA descriptor");
+            }
+            if ((e = cudaMalloc(&b->maps_dev[v][s], sizeof(CUtensorMap) * count)) != cudaSuccess)
+                return bail(e, "cudaMalloc(maps)");
+            if ((e = cudaMemcpy(b->maps_dev[v][s], maps.data(), sizeof(CUtensorMap) * count,
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return bail(e, "map upload");
+        }
+    }
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bail(e, "create sync");
+    *out = b;
+    return GALS_OK;
+}
+
+gals_status gals_destroy_batch(gals_batch *b)
+{
+    if (!b) return GALS_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (int s = 0; s < 2; ++s) cudaFree(b->buf[s]);
+    for (int v = 0; v < 2; ++v) {
+        cudaFree(b->items_dev[v]);
+        for (int s = 0; s < 2; ++s) cudaFree(b->maps_dev[v][s]);
+    }
+    cudaFree(b->probs_dev);
+    cudaFree(b->vps_dev);
+    cudaFree(b->t_dev);
+    cudaFree(b->coef);
+    cudaFree(b->err_dev);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return GALS_OK;
+}
+
+gals_status gals_batch_set_state(gals_batch *b, int index, const float *const *fields, int nfields,
+                                 int memspace, double t0, int flags)
+{
+    if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
+    if (index < 0 || index >= b->count) return bfail(b, GALS_ERR_ARG, "index %d out of range", index);
+    if (!fields || (nfields != 3 && nfields != 4)) return bfail(b, GALS_ERR_ARG, "nfields must be 3 or 4");
+    if (memspace != GALS_MEM_HOST && memspace != GALS_MEM_DEVICE) return bfail(b, GALS_ERR_ARG, "bad memspace");
+    if (!std::isfinite(t0)) return bfail(b, GALS_ERR_ARG, "t0 is not finite");
+    for (int p = 0; p < nfields; ++p)
+        if (!fields[p]) return bfail(b, GALS_ERR_ARG, "fields[%d] is NULL", p);
+    const BatchProb &P = b->probs[index];
+    const Geom &G = P.g;
+    const size_t row = (size_t)G.n0 * sizeof(float);
+    const cudaMemcpyKind kind = memspace == GALS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    float *dst = b->buf[b->cur] + P.off;
+    cudaError_t e;
+    for (int p = 0; p < nfields; ++p)
+        if ((e = cudaMemcpy2DAsync(dst + p * G.plane, (size_t)G.pitch * 4, fields[p], row, row, G.n1, kind,
+                                   b->stream)) != cudaSuccess)
+            return bcuda(b, e, "set_state copy");
+    const bool recon = nfields == 3 || (flags & GALS_SET_RECON_CROSS) || b->layout == GALS_LAYOUT_COMPACT;
+    if (recon && (e = launch_recon(2, G, dst, b->stream)) != cudaSuccess) return bcuda(b, e, "recon");
+    b->t_host[index] = t0;
+    b->steps[index] = 0;
+    if ((e = cudaMemcpyAsync(b->t_dev + index, &b->t_host[index], sizeof(double), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess)
+        return bcuda(b, e, "set time");
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(b, e, "set_state sync");
+    b->has_state[index] = 1;
+    return GALS_OK;
+}
+
+gals_status gals_batch_step(gals_batch *b, const gals_velocity *vels, const double *dt, int nsteps)
+{
+    if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
+    if (nsteps < 0) return bfail(b, GALS_ERR_ARG, "nsteps must be >= 0");
+    std::vector<VelParams> vps;
+    gals_status st = prepare(b, vels, dt, vps);
+    if (st != GALS_OK) return st;
+    if (nsteps == 0) return GALS_OK;
+    cudaError_t e;
+    if ((e = ensure_coef(b, nsteps)) != cudaSuccess) return bcuda(b, e, "coefficient table");
+    std::vector<double> dts(dt, dt + b->count);
+    BatchGraph *hit = nullptr;
+    for (auto &g : b->graphs)
+        if (g.nsteps == nsteps && g.cur == b->cur && g.variant == b->tuning.variant &&
+            g.blocks == b->tuning.blocks && g.dts == dts &&
+            std::memcmp(g.vps.data(), vps.data(), sizeof(VelParams) * b->count) == 0) {
+            hit = &g;
+            break;
+        }
+    if (!hit) {
+        // descriptors are baked into the graph's kernels through device pointers, so the
+        // uploaded parameters must match this entry; they do, by the key
+        if ((e = upload_params(b, vps, dt)) != cudaSuccess) return bcuda(b, e, "parameter upload");
+        cudaGraph_t graph;
+        if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return bcuda(b, e, "begin capture");
+        cudaError_t le = issue(b, vels[0].kind, nsteps);
+        e = cudaStreamEndCapture(b->stream, &graph);
+        if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return bcuda(b, le, "capture launch"); }
+        if (e != cudaSuccess) return bcuda(b, e, "end capture");
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+        if (b->graphs.size() >= 4) {
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.erase(b->graphs.begin());
+        }
+        BatchGraph bg;
+        bg.nsteps = nsteps; bg.cur = b->cur; bg.variant = b->tuning.variant; bg.blocks = b->tuning.blocks;
+        bg.vps = vps; bg.dts = dts; bg.exec = exec;
+        b->graphs.push_back(std::move(bg));
+        hit = &b->graphs.back();
+    } else {
+        // the device copies of the parameters belong to the last uploaded entry
+        if ((e = upload_params(b, vps, dt)) != cudaSuccess) return bcuda(b, e, "parameter upload");
+    }
+    if ((e = cudaGraphLaunch(hit->exec, b->stream)) != cudaSuccess) return bcuda(b, e, "graph launch");
+    if (nsteps & 1) b->cur ^= 1;
+    for (int p = 0; p < b->count; ++p) {
+        b->t_host[p] = b->t_host[p] + (double)nsteps * dt[p];
+        b->steps[p] += nsteps;
+    }
+    return GALS_OK;
+}
+
+gals_status gals_batch_synchronize(gals_batch *b)
+{
+    if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "synchronize");
+    return check_err(b);
+}
+
+gals_status gals_batch_read_state(gals_batch *b, int index, float *const *fields, int nfields, int memspace)
+{
+    if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
+    if (index < 0 || index >= b->count) return bfail(b, GALS_ERR_ARG, "index %d out of range", index);
+    if (!b->has_state[index]) return bfail(b, GALS_ERR_STATE, "problem %d has no state", index);
+    if (!fields || nfields < 1 || nfields > 4) return bfail(b, GALS_ERR_ARG, "nfields must be in 1..4");
+    if (memspace != GALS_MEM_HOST && memspace != GALS_MEM_DEVICE) return bfail(b, GALS_ERR_ARG, "bad memspace");
+    for (int p = 0; p < nfields; ++p)
+        if (!fields[p]) return bfail(b, GALS_ERR_ARG, "fields[%d] is NULL", p);
+    const BatchProb &P = b->probs[index];
+    const Geom &G = P.g;
+    float *src = b->buf[b->cur] + P.off;
+    cudaError_t e;
+    if (nfields > 3 && b->layout == GALS_LAYOUT_COMPACT)
+        if ((e = launch_recon(2, G, src, b->stream)) != cudaSuccess) return bcuda(b, e, "recon");
+    const size_t row = (size_t)G.n0 * sizeof(float);
+    const cudaMemcpyKind kind = memspace == GALS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    for (int p = 0; p < nfields; ++p)
+        if ((e = cudaMemcpy2DAsync(fields[p], row, src + p * G.plane, (size_t)G.pitch * 4, row, G.n1, kind,
+                                   b->stream)) != cudaSuccess)
+            return bcuda(b, e, "read_state copy");
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bcuda(b, e, "read_state sync");
+    return check_err(b);
+}
+
+gals_status gals_batch_set_tuning(gals_batch *b, const gals_batch_tuning *t)
+{
+    if (!b || !t) return bfail(b, GALS_ERR_ARG, "NULL argument");
+    if (t->variant < 0 || t->variant > 1 || t->blocks < 0) return bfail(b, GALS_ERR_ARG, "bad tuning");
+    b->tuning = *t;
+    return GALS_OK;
+}
+
+gals_status gals_batch_get_tuning(const gals_batch *b, gals_batch_tuning *t)
+{
+    if (!b || !t) return GALS_ERR_ARG;
+    *t = b->tuning;
+    return GALS_OK;
+}
+
+gals_status gals_batch_autotune(gals_batch *b, const gals_velocity *vels, const double *dt,
+                                int trial_steps, gals_batch_tuning *out)
+{
+    if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
+    if (trial_steps < 1) return bfail(b, GALS_ERR_ARG, "trial_steps must be >= 1");
+    std::vector<VelParams> vps;
+    gals_status st = prepare(b, vels, dt, vps);
+    if (st != GALS_OK) return st;
+    cudaError_t e;
+    if ((e = ensure_coef(b, 1)) != cudaSuccess) return bcuda(b, e, "coefficient table");
+    if ((e = upload_params(b, vps, dt)) != cudaSuccess) return bcuda(b, e, "parameter upload");
+    // coefficients of the current step only; trials read buffer cur and write cur^1, so
+    // the states are unchanged (no clock advance)
+    if ((e = launch_batch_coef(b->coef, b->vps_dev, b->t_dev, b->probs_dev, b->count, 1, b->stream)) != cudaSuccess)
+        return bcuda(b, e, "coefficients");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int kind = vels[0].kind;
+    const int compact = b->layout == GALS_LAYOUT_COMPACT;
+    std::vector<gals_batch_tuning> cands;
+    for (int v = 0; v < 2; ++v) {
+        // a first launch sets the kernel's shared-memory attribute, which the occupancy
+        // query needs
+        if ((e = launch_batch2d(make_launch(b, b->cur, v, 0, 0, kind), b->stream)) != cudaSuccess)
+            return bcuda(b, e, "autotune launch");
+        cands.push_back({v, 0, 0.0});
+        const int occ = std::max(1, batch_max_blocks_per_sm(v, kind, compact));
+        for (int k = 1; k <= occ; ++k) cands.push_back({v, k * sms, 0.0});
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    gals_batch_tuning best{1, 0, 1e30};
+    for (auto &c : cands) {
+        // one untimed launch (first-use attributes, cold caches), then the timed trials
+        BatchLaunch a = make_launch(b, b->cur, c.variant, c.blocks, 0, kind);
+        if ((e = launch_batch2d(a, b->stream)) != cudaSuccess) break;
+        cudaEventRecord(e0, b->stream);
+        for (int s = 0; s < trial_steps && e == cudaSuccess; ++s) e = launch_batch2d(a, b->stream);
+        cudaEventRecord(e1, b->stream);
+        if (e != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c.ms_per_step = ms / trial_steps;
+        if (c.ms_per_step < best.ms_per_step) best = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return bcuda(b, e, "autotune launch");
+    if ((st = check_err(b)) != GALS_OK) return st;
+    b->tuning = best;
+    if (out) *out = best;
+    return GALS_OK;
+}
+
+}  // extern "C"

@@ -278,18 +278,33 @@ __device__ __forceinline__ void matmul3(const float *A, const float *B, float *C
             C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
 }
 
+template <int VK>
+__device__ __forceinline__ void trace3d_rk3(const V3 &a, const VelParams &vp, const StageCoef &sc,
+                                            float x, float y, float z, float dt, float d[3],
+                                            float J[9]);
+
+// 3D trace from node position (x, y, z); a = v(x, t+dt) and its Jacobian supplied by the
+// caller.  d = foot - x, J[3i+j] = d foot_i / d x_j.
 template <int TR, int VK>
-__device__ __forceinline__ void trace3d(const VelParams &vp, const StageCoef &sc, float x,
-                                        float y, float z, float dt, float d[3], float J[9])
+__device__ __forceinline__ void trace3d_from(const V3 &a, const VelParams &vp,
+                                             const StageCoef &sc, float x, float y, float z,
+                                             float dt, float d[3], float J[9])
 {
-    V3 a = vel3d<VK>(vp, sc, 0, x, y, z);
     if (TR == TR_EULER) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) d[i] = -dt * a.v[i];
 #pragma unroll
         for (int e = 0; e < 9; ++e) J[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * a.d[e];
-        return;
+    } else {
+        trace3d_rk3<VK>(a, vp, sc, x, y, z, dt, d, J);
     }
+}
+
+template <int VK>
+__device__ __forceinline__ void trace3d_rk3(const V3 &a, const VelParams &vp, const StageCoef &sc,
+                                            float x, float y, float z, float dt, float d[3],
+                                            float J[9])
+{
     float J1[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) J1[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * a.d[e];

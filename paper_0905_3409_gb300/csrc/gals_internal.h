@@ -19,13 +19,15 @@ struct StepLaunch {
     int trace;           // TR_EULER / TR_RK3
     int cross_in;        // CROSS_PLANE: read mixed derivatives; CROSS_RECON: rebuild from psi
     int write_cross;     // 1: also write the mixed-derivative planes of the new state
-    const CUtensorMap *tmap4; // TMA map of `in`, box of all 4 planes (2D)
-    const CUtensorMap *tmap3; // TMA map of `in`, box of phi, psi_x, psi_y (2D)
+    const CUtensorMap *tmap4; // TMA map of `in` for reading stored mixed derivatives
+    const CUtensorMap *tmap3; // TMA map of `in` for rebuilding them (COMPACT)
     int *err;            // device error word (kErrTmaTimeout on a lost tile copy)
 };
 
 // Box of the 2D step kernel's staged tile for np planes.
 void tile_box2d(int np, uint32_t box[3]);
+// Box (x, y, z, planes) of the 3D step kernel's staged tile.
+void tile_box3d(int cross_recon, uint32_t box[4]);
 // Encode a tiled TMA map of FP32 data: rank dims (innermost first), byte strides of
 // dims 1..rank-1, box extents; zero fill outside the tensor.
 cudaError_t make_tile_map(CUtensorMap *map, const float *base, int rank, const uint64_t *dims,

@@ -1,0 +1,290 @@
+// step2d_tile.cuh -- one 2D GALS step over one tile of nodes, shared by the single-grid
+// kernel (step2d.cu) and the batched kernels (batch2d.cu).
+//
+// Per grid node (Sec. 4, steps 1-2 in the superconsistent form of Sec. 5.1):
+//   trace back with the Jacobian -> locate the foot cell -> gather the 4 corners x 4 data
+//   -> bicubic Hermite value and gradient -> phi+ = H, psi+ = J^T grad H,
+// then (Sec. 2.3, approach A) phi_xy+ = d/dx psi_y+ by central differences.
+//
+// A block of 128 threads owns a tile of 128 columns x TY rows; each thread walks its
+// column two rows at a time in paired FP32 arithmetic (gals_pair.cuh).  The input tile
+// (all state planes, halo 4 columns x 2 rows) is staged into shared memory by one TMA copy;
+// feet whose cell leaves the staged tile read global memory instead.  With WC the new
+// psi_y of the tile plus one halo column on each side (2 extra node updates per 128 per
+// row) stays in shared memory and phi_xy+ is written by the same kernel.
+#pragma once
+
+#include "gals_internal.h"
+#include "gals_pair.cuh"
+#include "tma.cuh"
+
+namespace gals {
+namespace t2 {
+
+constexpr int TX = 128;               // output tile columns (one thread each)
+constexpr int HX = 4, HY = 2;         // input halo (x rounded to 16 bytes for TMA)
+constexpr int TW = TX + 2 * HX;
+
+template <int TY> struct Geo {
+    static constexpr int TH = TY + 2 * HY;
+    static constexpr int PS = TW * TH;  // floats per staged plane
+    static constexpr int bytes(int np) { return np * PS * 4; }
+};
+
+// static shared memory of a tile step (the staged tile itself is dynamic)
+template <int TY, int WC> struct Smem {
+    float psy[WC ? TY : 1][TX + 3];   // psi_y+ of columns x0-2 .. x0+TX
+    StageCoefPair scp;
+    uint64_t bar;
+};
+
+// phi_xy at corner column q (q = k + o, o in {0,1}) from the psi_y row window
+// w[0..3] = psi_y[k-1 .. k+2]: the same stencils as the reconstruction kernel.
+template <int O>
+__device__ __forceinline__ float cross_from_window(const float w[4], int q, int n, float i2h)
+{
+    constexpr int c = 1 + O;  // position of column q in the window
+    if (O == 0) {
+        if (q == 0) return dfirst(w[c], w[c + 1], w[c + 2], i2h);
+    } else {
+        if (q == n - 1) return dlast(w[c], w[c - 1], w[c - 2], i2h);
+    }
+    return dcentral(w[c + 1], w[c - 1], i2h);
+}
+
+// Separable factors of the single-vortex field on a grid line: sin^2(pi s),
+// sin(2 pi s), cos(2 pi s) (one float2 lane per node).
+struct Sep2 { F2 s2, s2x, c2x; };
+
+__device__ __forceinline__ Sep2 sep_factors2(F2 s)
+{
+    F2 sn, cs;
+    sincospi2(s, sn, cs);
+    Sep2 f;
+    f.s2 = mul2(sn, sn);
+    f.s2x = mul2(bc(2.f), mul2(sn, cs));
+    f.c2x = fma2(bc(-2.f), f.s2, bc(1.f));
+    return f;
+}
+
+// v(x, t+dt) at two nodes of one column; the single vortex uses the separable
+// column factors cx (shared) and row factors ry.
+template <int VK>
+__device__ __forceinline__ V2p stage1_pair(const VelParams &vp, const StageCoef &sc,
+                                           const StageCoefPair *scp, F2 x, F2 y, const Sep2 &cx,
+                                           const Sep2 &ry)
+{
+    if (VK == VK_VORTEX2D) {
+        V2p r;
+        const float c = sc.mod[0], cp = c * kPi;
+        r.u = mul2(bc(-c), mul2(cx.s2, ry.s2x));
+        r.v = mul2(bc(c), mul2(cx.s2x, ry.s2));
+        r.d00 = mul2(bc(-cp), mul2(cx.s2x, ry.s2x));
+        r.d01 = mul2(bc(-2.f * cp), mul2(cx.s2, ry.c2x));
+        r.d10 = mul2(bc(2.f * cp), mul2(cx.c2x, ry.s2));
+        r.d11 = neg2(r.d00);
+        return r;
+    }
+    return vel2d_pair<VK>(vp, sc, scp, 0, x, y);
+}
+
+// The 4 corners x 4 data of the cell (k, l) for one node, from the staged tile when the
+// cell (and, for COMPACT, its psi_y window k-1..k+2) lies inside it, else from global
+// memory (feet farther than the halo: CFL well above 1).
+template <int TY, int CR>
+__device__ __forceinline__ void gather_lane(const float *__restrict__ in, const Geom &g,
+                                            const float *__restrict__ tile, int x0, int y0, int k,
+                                            int l, float c[4][4])
+{
+    constexpr int TH = Geo<TY>::TH, PS = Geo<TY>::PS;
+    const int tx = k - x0 + HX, ty = l - y0 + HY;
+    if (tx >= 1 && tx <= TW - 3 && ty >= 0 && ty <= TH - 2) {
+        const float *t = tile + ty * TW + tx;
+#pragma unroll
+        for (int B = 0; B < 2; ++B) {
+#pragma unroll
+            for (int A = 0; A < 2; ++A) {
+                const int v = A + 2 * B, o = B * TW + A;
+                c[v][0] = t[o];
+                c[v][1] = t[PS + o];
+                c[v][2] = t[2 * PS + o];
+                if (CR == CROSS_PLANE) c[v][3] = t[3 * PS + o];
+            }
+            if (CR == CROSS_RECON) {
+                const float w[4] = {t[2 * PS + B * TW - 1], c[2 * B][2], c[2 * B + 1][2],
+                                    t[2 * PS + B * TW + 2]};
+                c[2 * B][3] = cross_from_window<0>(w, k, g.n0, g.i2h0);
+                c[2 * B + 1][3] = cross_from_window<1>(w, k + 1, g.n0, g.i2h0);
+            }
+        }
+        return;
+    }
+    const float *Pphi = in, *Ppx = in + g.plane, *Ppy = in + 2 * g.plane;
+#pragma unroll
+    for (int B = 0; B < 2; ++B) {
+        const int r = (l + B) * g.pitch + k;
+#pragma unroll
+        for (int A = 0; A < 2; ++A) {
+            const int v = A + 2 * B;
+            c[v][0] = __ldg(Pphi + r + A);
+            c[v][1] = __ldg(Ppx + r + A);
+            c[v][2] = __ldg(Ppy + r + A);
+            if (CR == CROSS_PLANE) c[v][3] = __ldg(in + 3 * g.plane + r + A);
+        }
+        if (CR == CROSS_RECON) {
+            const float w[4] = {__ldg(Ppy + r - (k > 0 ? 1 : 0)), c[2 * B][2], c[2 * B + 1][2],
+                                __ldg(Ppy + r + (k + 2 < g.n0 ? 2 : 1))};
+            c[2 * B][3] = cross_from_window<0>(w, k, g.n0, g.i2h0);
+            c[2 * B + 1][3] = cross_from_window<1>(w, k + 1, g.n0, g.i2h0);
+        }
+    }
+}
+
+// Update of two nodes (i0, j0) and (i1, j1): phi+, psi_x+, psi_y+ per lane.
+template <int TY, int TR, int VK, int CR>
+__device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const Geom &g,
+                                            const float *__restrict__ tile, int x0, int y0,
+                                            const VelParams &vp, const StageCoef &sc,
+                                            const StageCoefPair *scp, float dt, int i0, int j0,
+                                            int i1, int j1, F2 x, F2 y, const Sep2 &cx,
+                                            const Sep2 &ry, F2 &phi, F2 &px, F2 &py)
+{
+    F2 dx, dy, J[4];
+    trace2d_pair<TR, VK>(stage1_pair<VK>(vp, sc, scp, x, y, cx, ry), vp, sc, scp, x, y, dt, dx,
+                         dy, J);
+    int k0, l0, k1, l1;
+    F2 xi, eta;
+    locate(i0, dx.x * g.ih0, g.n0, k0, xi.x);
+    locate(i1, dx.y * g.ih0, g.n0, k1, xi.y);
+    locate(j0, dy.x * g.ih1, g.n1, l0, eta.x);
+    locate(j1, dy.y * g.ih1, g.n1, l1, eta.y);
+
+    float c0[4][4], c1[4][4];
+    gather_lane<TY, CR>(in, g, tile, x0, y0, k0, l0, c0);
+    gather_lane<TY, CR>(in, g, tile, x0, y0, k1, l1, c1);
+    F2 c[4][4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) c[v][a] = make_float2(c0[v][a], c1[v][a]);
+
+    const Basis2 bx = basis_pair(xi, g.h0, g.ih0);
+    const Basis2 by = basis_pair(eta, g.h1, g.ih1);
+    F2 H, Hx, Hy;
+    hermite2d_pair(c, bx, by, H, Hx, Hy);
+    phi = H;
+    px = fma2(J[0], Hx, mul2(J[2], Hy));  // (J^T grad H)_x
+    py = fma2(J[1], Hx, mul2(J[3], Hy));  // (J^T grad H)_y
+}
+
+// One tile step: origin (x0, y0).  `tile` is the dynamic shared buffer for the staged
+// input, `sm` the static part; the barrier sm.bar must be initialised (count 1) and
+// `parity` is the phase this tile's copy completes.  Returns false (after recording
+// kErrTmaTimeout) if the staged copy did not arrive within the wait limit.
+// Must be called by all TX threads of the block.
+template <int TY, int TR, int VK, int CR, int WC>
+__device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float *__restrict__ out,
+                                            const Geom &g, const VelParams &vp,
+                                            const StageCoef *__restrict__ coef, float dt,
+                                            const CUtensorMap *tmap, int *__restrict__ err,
+                                            int x0, int y0, float *tile, Smem<TY, WC> &sm,
+                                            uint32_t parity)
+{
+    auto &psy = sm.psy;
+    auto &scp_s = sm.scp;
+    const int tid = threadIdx.x;
+    constexpr int NP = CR == CROSS_PLANE ? 4 : 3;
+
+    // stage the input tile (all planes, halo HX x HY) with one TMA copy
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&sm.bar, Geo<TY>::bytes(NP));
+        tma_load_3d(tile, tmap, x0 - HX, y0 - HY, 0, &sm.bar);
+    }
+    const StageCoef &sc = *coef;
+    if (VK == VK_FOURIER2D) {
+        // duplicate the step's 4x4 tables into float2 pairs in shared memory
+        for (int e = tid; e < 3 * 3 * 16; e += TX) {
+            const int tab = e / 48, rest = e % 48, st = rest / 16, kl = rest % 16;
+            const float v = tab == 0 ? __ldg(&coef->A[st][kl])
+                          : (tab == 1 ? __ldg(&coef->Al[st][kl]) : __ldg(&coef->All[st][kl]));
+            F2 *dst = tab == 0 ? &scp_s.A[st][kl] : (tab == 1 ? &scp_s.Al[st][kl] : &scp_s.All[st][kl]);
+            *dst = bc(v);
+        }
+        __syncthreads();
+    }
+    const StageCoefPair *scp = &scp_s;
+    (void)psy;
+
+    const int i = x0 + tid;
+    const int rows = min(TY, g.n1 - y0);
+    const float xs = g.lo0 + (float)i * g.h0;
+    const F2 x = bc(xs);
+    const Sep2 cx = (VK == VK_VORTEX2D) ? sep_factors2(x) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+
+    // bounded wait for the tile; a block-uniform verdict so no thread is left at a barrier
+    const bool ok = mbar_wait_bounded(&sm.bar, parity);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicExch(err, kErrTmaTimeout);
+            mbar_wait_bounded(&sm.bar, parity);  // let a late copy land before giving up
+        }
+        return false;
+    }
+
+    if (i < g.n0) {
+        for (int r = 0; r < rows; r += 2) {
+            const int j0 = y0 + r, j1 = min(j0 + 1, g.n1 - 1);
+            const F2 y = make_float2(g.lo1 + (float)j0 * g.h1, g.lo1 + (float)j1 * g.h1);
+            const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+            F2 phi, px, py;
+            node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y, cx, ry,
+                                    phi, px, py);
+            const int o = j0 * g.pitch + i;
+            out[o] = phi.x;
+            out[g.plane + o] = px.x;
+            out[2 * g.plane + o] = py.x;
+            if (WC) psy[WC ? r : 0][tid + 2] = py.x;
+            if (r + 1 < rows) {
+                const int o1 = o + g.pitch;
+                out[o1] = phi.y;
+                out[g.plane + o1] = px.y;
+                out[2 * g.plane + o1] = py.y;
+                if (WC) psy[WC ? r + 1 : 0][tid + 2] = py.y;
+            }
+        }
+    }
+    if (WC) {
+        // halo columns of psi_y+: x0-1 and x0+TX (x0-2 too when the tile is one column
+        // wide, for the one-sided stencil of the last node); two rows per task
+        const int width = min(TX, g.n0 - x0);
+        const int npairs = (rows + 1) / 2;
+        for (int hh = tid; hh < 3 * npairs; hh += TX) {
+            const int rp = hh / 3, which = hh % 3;
+            const int ih = which == 0 ? x0 - 2 : (which == 1 ? x0 - 1 : x0 + TX);
+            const bool need = which == 0 ? (width == 1 && ih >= 0) : (ih >= 0 && ih < g.n0);
+            if (!need) continue;
+            const int r = 2 * rp, j0 = y0 + r, j1 = min(j0 + 1, g.n1 - 1);
+            const F2 xh = bc(g.lo0 + (float)ih * g.h0);
+            const F2 y = make_float2(g.lo1 + (float)j0 * g.h1, g.lo1 + (float)j1 * g.h1);
+            const Sep2 cxh = (VK == VK_VORTEX2D) ? sep_factors2(xh) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+            const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+            F2 phi, px, py;
+            node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
+                                    ry, phi, px, py);
+            psy[WC ? r : 0][ih - x0 + 2] = py.x;
+            if (r + 1 < rows) psy[WC ? r + 1 : 0][ih - x0 + 2] = py.y;
+        }
+        __syncthreads();
+        if (i < g.n0) {
+            for (int r = 0; r < rows; ++r) {
+                const float *line = psy[WC ? r : 0];
+                const float v = dline(i, g.n0, g.i2h0, [&](int q) { return line[q - x0 + 2]; });
+                out[3 * g.plane + (y0 + r) * g.pitch + i] = v;
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace t2
+}  // namespace gals

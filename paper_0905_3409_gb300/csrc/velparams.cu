@@ -1,0 +1,71 @@
+// velparams.cu -- validation of a gals_velocity descriptor and its conversion to the
+// kernels' VelParams (shared by the single-grid and batched C ABI).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "capi_internal.h"
+
+namespace gals {
+
+namespace {
+bool finite3(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+gals_status vfail(char *msg, size_t len, gals_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, len, fmt, ap);
+    va_end(ap);
+    return st;
+}
+}  // namespace
+
+gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char *msg, size_t len)
+{
+    std::memset(&vp, 0, sizeof(vp));
+    if (!v) return vfail(msg, len, GALS_ERR_ARG, "velocity descriptor is NULL");
+    if (v->trace != GALS_TRACE_EULER && v->trace != GALS_TRACE_RK3)
+        return vfail(msg, len, GALS_ERR_ARG, "unknown trace scheme %d", v->trace);
+    if (!vel_supported(dim, v->kind))
+        return vfail(msg, len, GALS_ERR_UNSUPPORTED, "velocity kind %d not available in %dD", v->kind, dim);
+    if (!finite3(v->c, 3) || !finite3(v->center, 3) || !std::isfinite(v->omega) || !std::isfinite(v->T))
+        return vfail(msg, len, GALS_ERR_ARG, "non-finite velocity parameter");
+    vp.kind = v->kind;
+    vp.omega = (float)v->omega;
+    vp.cx = (float)v->center[0]; vp.cy = (float)v->center[1]; vp.cz = (float)v->center[2];
+    vp.c0 = (float)v->c[0]; vp.c1 = (float)v->c[1]; vp.c2 = (float)v->c[2];
+    const double nrm = std::sqrt(2.0 + M_PI);
+    vp.d0 = (float)(std::sqrt(2.0) / nrm);
+    vp.d1 = (float)(std::sqrt(M_PI) / nrm);
+    if (v->kind == GALS_VEL_VORTEX2D || v->kind == GALS_VEL_DEFORM3D) {
+        if (!(v->T > 0.0)) return vfail(msg, len, GALS_ERR_ARG, "modulation period T must be > 0");
+        vp.invT = 1.0 / v->T;
+    }
+    if (v->kind == GALS_VEL_FOURIER2D) {
+        if (v->nmodes < 1 || v->nmodes > GALS_MAX_MODES || !v->modes)
+            return vfail(msg, len, GALS_ERR_ARG, "FOURIER2D needs 1..%d modes", GALS_MAX_MODES);
+        vp.nmodes = v->nmodes;
+        for (int m = 0; m < v->nmodes; ++m) {
+            const double *md = v->modes + 5 * m;
+            if (!finite3(md, 5)) return vfail(msg, len, GALS_ERR_ARG, "non-finite mode %d", m);
+            int k = (int)md[1], l = (int)md[2];
+            if (k != md[1] || l != md[2] || k < 1 || k > 4 || l < 1 || l > 4)
+                return vfail(msg, len, GALS_ERR_ARG, "mode %d: k, l must be integers in 1..4", m);
+            if (md[3] < 0) return vfail(msg, len, GALS_ERR_ARG, "mode %d: n must be >= 0", m);
+            vp.mode_a[m] = (float)md[0];
+            vp.mode_kl[m] = k | (l << 8);
+            vp.mode_n[m] = md[3];
+            vp.mode_chi[m] = md[4] / (2.0 * M_PI);
+        }
+    }
+    return GALS_OK;
+}
+
+}  // namespace gals

@@ -31,7 +31,14 @@ EXPORTS = [
     "gals_create_grid", "gals_destroy_grid", "gals_set_state", "gals_step", "gals_read_state",
     "gals_diagnostics", "gals_synchronize", "gals_time", "gals_state_planes", "gals_last_error",
     "gals_version",
+    "gals_create_batch", "gals_destroy_batch", "gals_batch_set_state", "gals_batch_step",
+    "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
+    "gals_batch_set_tuning", "gals_batch_get_tuning", "gals_batch_nodes", "gals_batch_last_error",
 ]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("blocks", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
 
 
 class GalsError(RuntimeError):
@@ -90,6 +97,24 @@ def lib() -> ctypes.CDLL:
         L.gals_last_error.argtypes = [vp]
         L.gals_last_error.restype = ctypes.c_char_p
         L.gals_version.restype = ctypes.c_char_p
+        L.gals_create_batch.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int, ctypes.POINTER(vp)]
+        L.gals_destroy_batch.argtypes = [vp]
+        L.gals_batch_set_state.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_int]
+        L.gals_batch_step.argtypes = [vp, ctypes.POINTER(VelocityDesc),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+        L.gals_batch_read_state.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int,
+                                            ctypes.c_int]
+        L.gals_batch_synchronize.argtypes = [vp]
+        L.gals_batch_autotune.argtypes = [vp, ctypes.POINTER(VelocityDesc),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                          ctypes.POINTER(BatchTuning)]
+        L.gals_batch_set_tuning.argtypes = [vp, ctypes.POINTER(BatchTuning)]
+        L.gals_batch_get_tuning.argtypes = [vp, ctypes.POINTER(BatchTuning)]
+        L.gals_batch_nodes.argtypes = [vp]
+        L.gals_batch_nodes.restype = ctypes.c_int64
+        L.gals_batch_last_error.argtypes = [vp]
+        L.gals_batch_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -246,3 +271,91 @@ class Grid:
 
 def version() -> str:
     return lib().gals_version().decode()
+
+
+def _bcheck(status: int, handle=None):
+    if status != OK:
+        msg = lib().gals_batch_last_error(handle)
+        raise GalsError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Independent 2D problems advanced together (gals_batch_* of gals.h).
+    ``sizes``: list of (nx, ny); every problem lives on [0,1]^2 unless lo/hi given."""
+
+    def __init__(self, sizes, lo=None, hi=None, layout: str = "full", stream=None):
+        count = len(sizes)
+        descs = (GridDesc * count)()
+        for p, n in enumerate(sizes):
+            d = descs[p]
+            d.dim = 2
+            for i in range(2):
+                d.n[i] = int(n[i])
+                d.lo[i] = 0.0 if lo is None else float(lo[p][i])
+                d.hi[i] = 1.0 if hi is None else float(hi[p][i])
+            d.n[2] = 1
+            d.layout = LAYOUT_FULL if layout == "full" else LAYOUT_COMPACT
+            if stream is not None and p == 0:
+                d.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        h = ctypes.c_void_p()
+        _bcheck(lib().gals_create_batch(descs, count, ctypes.byref(h)))
+        self._h = h
+        self.sizes = [tuple(int(v) for v in n) for n in sizes]
+        self.count = count
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gals_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nodes(self) -> int:
+        return lib().gals_batch_nodes(self._h)
+
+    def set_state(self, index, state, t0=0.0, recon=False):
+        st = np.ascontiguousarray(state, dtype=np.float32)
+        nf = st.shape[0]
+        ptrs = (ctypes.c_void_p * nf)(*[st[p].ctypes.data for p in range(nf)])
+        _bcheck(lib().gals_batch_set_state(self._h, int(index), ptrs, nf, MEM_HOST, float(t0),
+                                           SET_RECON_CROSS if recon else 0), self._h)
+
+    def _vels(self, vels, dts):
+        assert len(vels) == self.count and len(dts) == self.count
+        descs = (VelocityDesc * self.count)()
+        keep = []
+        for p, v in enumerate(vels):
+            d = v.desc()
+            keep.append(d)
+            descs[p] = d
+        dt = (ctypes.c_double * self.count)(*[float(x) for x in dts])
+        return descs, dt, keep
+
+    def step(self, vels, dts, nsteps=1):
+        descs, dt, keep = self._vels(vels, dts)
+        _bcheck(lib().gals_batch_step(self._h, descs, dt, int(nsteps)), self._h)
+
+    def autotune(self, vels, dts, trial_steps=3):
+        descs, dt, keep = self._vels(vels, dts)
+        t = BatchTuning()
+        _bcheck(lib().gals_batch_autotune(self._h, descs, dt, int(trial_steps), ctypes.byref(t)), self._h)
+        return {"variant": t.variant, "blocks": t.blocks, "ms_per_step": t.ms_per_step}
+
+    def set_tuning(self, variant, blocks):
+        t = BatchTuning(int(variant), int(blocks), 0.0)
+        _bcheck(lib().gals_batch_set_tuning(self._h, ctypes.byref(t)), self._h)
+
+    def read_state(self, index, nfields=4):
+        nx, ny = self.sizes[index]
+        out = np.empty((nfields, ny, nx), dtype=np.float32)
+        ptrs = (ctypes.c_void_p * nfields)(*[out[p].ctypes.data for p in range(nfields)])
+        _bcheck(lib().gals_batch_read_state(self._h, int(index), ptrs, nfields, MEM_HOST), self._h)
+        return out
+
+    def synchronize(self):
+        _bcheck(lib().gals_batch_synchronize(self._h), self._h)

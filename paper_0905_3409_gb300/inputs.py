@@ -232,12 +232,25 @@ def polynomial2d(n, coef, lo=None, hi=None):
 
 # ------------------------------------------------------------------ 3D initial data
 
-def sphere_sdf(n, center=(0.35, 0.35, 0.35), r=0.15, lo=None, hi=None):
-    X, Y, Z = _mesh(n, lo, hi)
-    dx, dy, dz = X - center[0], Y - center[1], Z - center[2]
-    d = np.sqrt(dx * dx + dy * dy + dz * dz)
-    ux, uy, uz = _unit(dx, dy, dz)
-    return _state3d(d - r, ux, uy, uz)
+def sphere_sdf(n, center=(0.35, 0.35, 0.35), r=0.15, lo=None, hi=None, dtype=np.float64,
+               z_range=None):
+    """Signed distance to a sphere with exact gradient and zero cross planes, built one
+    z-slice at a time (so 512^3 fits in memory as float32).  z_range=(z0, z1) returns
+    only those slices."""
+    axes = node_coords(n, lo, hi)
+    z0, z1 = (0, n[2]) if z_range is None else z_range
+    out = np.zeros((8, z1 - z0, n[1], n[0]), dtype=dtype)
+    Y, X = np.meshgrid(axes[1], axes[0], indexing="ij")
+    dx, dy = X - center[0], Y - center[1]
+    for k in range(z0, z1):
+        dz = axes[2][k] - center[2]
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        safe = np.where(d > 0, d, 1.0)
+        out[0, k - z0] = d - r
+        out[1, k - z0] = np.where(d > 0, dx / safe, 0.0)
+        out[2, k - z0] = np.where(d > 0, dy / safe, 0.0)
+        out[3, k - z0] = np.where(d > 0, dz / safe, 0.0)
+    return out
 
 
 def cube_sdf(n, center=(0.35, 0.35, 0.35), half=0.15, lo=None, hi=None):
