@@ -237,6 +237,41 @@ int64_t gals_batch_nodes(const gals_batch *batch);
 
 const char *gals_batch_last_error(const gals_batch *batch);
 
+/* ------------------------------------------------------------------------------------
+ * Diagnostics without device allocation.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they need diagnostics --
+ * a loop whose device memory was reserved up front by another allocator, code that must
+ * not let cudaMalloc/cudaFree synchronise the device, or a service that accounts for
+ * every byte it holds.  It computes what gals_diagnostics computes (same kernels), for
+ * a state in caller memory, using a fixed scratch area inside the library (a
+ * __device__ array of about 128 KB that each device holding the library keeps until
+ * the process exits) instead of allocating.
+ *
+ *   state       device pointer of plane 0 (plane order as above, FULL: all planes);
+ *               plane p starts at state + p*plane_stride, node (i,j,k) of a plane at
+ *               (k*n[1] + j)*row_pitch + i.  gals_state_planes gives these for a grid.
+ *   reference   NULL, or another state of the same shape and layout.
+ *   q           samples per cell and axis, 0..16.
+ *   cuda_stream stream to order the work on (NULL: the legacy default stream).
+ *   out         host struct; t and steps are 0 (the state has no clock here).
+ * Limits and rules:
+ *   - grids of more than gals_noalloc_max_nodes() nodes (268,435,456) are rejected
+ *     with GALS_ERR_ARG: the scratch holds one partial sum per 16384 nodes;
+ *   - the first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call on a device shares the one scratch area, which keeps the last call's
+ *     contents (each call clears what must start at zero): calls whose GPU work
+ *     overlaps -- on different streams or host threads -- race and give wrong results;
+ *   - synchronises `cuda_stream`.
+ * Errors: GALS_ERR_ARG (dims, pointers, q, strides, size limit), GALS_ERR_CUDA; the
+ * message is in gals_noalloc_last_error(). */
+gals_status gals_diagnostics_noalloc(int dim, const int *n, const double *lo, const double *hi,
+                                     const float *state, const float *reference,
+                                     int64_t row_pitch, int64_t plane_stride, int q,
+                                     void *cuda_stream, gals_diag *out);
+int64_t gals_noalloc_max_nodes(void);
+const char *gals_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -201,4 +201,22 @@ cudaError_t launch_diag(int dim, const Geom &g, const float *a, const float *b, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_diag_with(int dim, const Geom &g, const float *a, const float *b, int q,
+                             DiagOut *counters, double *partials, int nparts, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(DiagOut), s);
+    if (e != cudaSuccess) return e;
+    if (q > 0) {
+        const int64_t ncell = (int64_t)(g.n0 - 1) * (g.n1 - 1) * (dim == 3 ? g.n2 - 1 : 1);
+        int blocks = (int)std::min<int64_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
+        if (dim == 2) k_diag_cells<2><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters);
+        else k_diag_cells<3><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_diag_nodes<<<nparts, kThreads, 0, s>>>(g, dim, a, b, counters, partials);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_diag_finish<<<1, 32, 0, s>>>(partials, nparts, counters);
+    return cudaGetLastError();
+}
+
 }  // namespace gals

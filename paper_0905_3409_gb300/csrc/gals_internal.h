@@ -56,5 +56,8 @@ struct DiagOut {
 int diag_partials_needed();
 cudaError_t launch_diag(int dim, const Geom &g, const float *a, const float *b, int q,
                         DiagOut *counters, double *partials, cudaStream_t s);
+// Same kernels with `nparts` node blocks (one FP64 partial each) instead of the default.
+cudaError_t launch_diag_with(int dim, const Geom &g, const float *a, const float *b, int q,
+                             DiagOut *counters, double *partials, int nparts, cudaStream_t s);
 
 }  // namespace gals

@@ -34,6 +34,7 @@ EXPORTS = [
     "gals_create_batch", "gals_destroy_batch", "gals_batch_set_state", "gals_batch_step",
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
     "gals_batch_set_tuning", "gals_batch_get_tuning", "gals_batch_nodes", "gals_batch_last_error",
+    "gals_diagnostics_noalloc", "gals_noalloc_max_nodes", "gals_noalloc_last_error",
 ]
 
 
@@ -115,6 +116,12 @@ def lib() -> ctypes.CDLL:
         L.gals_batch_nodes.restype = ctypes.c_int64
         L.gals_batch_last_error.argtypes = [vp]
         L.gals_batch_last_error.restype = ctypes.c_char_p
+        L.gals_diagnostics_noalloc.argtypes = [
+            ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+            ctypes.POINTER(ctypes.c_double), vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+            vp, ctypes.POINTER(DiagOut)]
+        L.gals_noalloc_max_nodes.restype = ctypes.c_int64
+        L.gals_noalloc_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 

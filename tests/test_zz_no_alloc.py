@@ -1,0 +1,97 @@
+"""gals_diagnostics_noalloc: the diagnostics of a state in caller memory without any
+device allocation (for callers whose device memory is reserved up front, or that must
+not let an allocation synchronise the device).  Called through the C ABI and checked
+against gals_diagnostics on the same state, on two calls in a row (the shared scratch
+keeps the previous call's contents, so the second call shows it is cleared).
+
+This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_0905_3409_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_0905_3409_gb300 import gals
+    return gals
+
+
+def _noalloc(G, grid, ref, q):
+    L = G.lib()
+    planes, pitch = grid.state_planes()
+    ref_ptr = ref.state_planes()[0][0] if ref is not None else None
+    dim = grid.dim
+    n = (ctypes.c_int * 3)(*(list(grid.n) + [1] * (3 - dim)))
+    lo = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    hi = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    plane_stride = planes[1] - planes[0]
+    assert plane_stride % 4 == 0
+    out = G.DiagOut()
+    st = L.gals_diagnostics_noalloc(dim, n, lo, hi, planes[0], ref_ptr, pitch, plane_stride // 4, q,
+                                    None, ctypes.byref(out))
+    assert st == G.OK, L.gals_noalloc_last_error()
+    return {f: getattr(out, f) for f, _ in G.DiagOut._fields_}
+
+
+def _same(a, b):
+    for key in ("samples", "n_negative", "n_symdiff", "nonfinite"):
+        assert a[key] == b[key], key
+    for key in ("measure_negative", "measure_symdiff", "emax_phi", "emax_psi"):
+        assert a[key] == pytest.approx(b[key], rel=1e-12, abs=0.0), key
+    # FP64 partial sums over another block partition: agreement to rounding
+    assert a["l2_phi"] == pytest.approx(b["l2_phi"], rel=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_noalloc_matches_diagnostics_twice(G, dim):
+    if dim == 2:
+        n = (160, 131)
+        a_st = inputs.circle_sdf(n, r=0.2, center=(0.5, 0.5))
+        b_st = inputs.circle_sdf(n, r=0.23, center=(0.52, 0.49))
+    else:
+        n = (40, 37, 33)
+        a_st = inputs.sphere_sdf(n, r=0.25, center=(0.5, 0.5, 0.5))
+        b_st = inputs.sphere_sdf(n, r=0.27, center=(0.52, 0.5, 0.48))
+    a = G.Grid(n)
+    a.set_state(a_st.astype(np.float32), recon=True)
+    b = G.Grid(n)
+    b.set_state(b_st.astype(np.float32), recon=True)
+    q = 4
+    ref = a.diagnostics(q=q, reference=b)
+    first = _noalloc(G, a, b, q)
+    second = _noalloc(G, a, b, q)
+    _same(first, ref)
+    _same(second, ref)
+    # without a reference, and a state with a non-finite value
+    assert _noalloc(G, a, None, 0)["nonfinite"] == 0
+    bad = a_st.astype(np.float32)
+    bad[1].flat[17] = np.inf
+    a.set_state(bad)
+    assert _noalloc(G, a, None, 0)["nonfinite"] == a.diagnostics(q=0)["nonfinite"] == 1
+
+
+def test_noalloc_rejects_oversize_and_bad_args(G):
+    L = G.lib()
+    assert L.gals_noalloc_max_nodes() == 16384 * 16384
+    n = (ctypes.c_int * 3)(4096, 4096, 17)
+    lo = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    hi = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    out = G.DiagOut()
+    fake = ctypes.c_void_p(256)  # never dereferenced: the size check rejects first
+    st = L.gals_diagnostics_noalloc(3, n, lo, hi, fake, None, 4096, 4096 * 4096 * 17, 0, None,
+                                    ctypes.byref(out))
+    assert st == G.ERR_ARG
+    assert b"no-allocation" in L.gals_noalloc_last_error()
+    n2 = (ctypes.c_int * 3)(16, 16, 1)
+    st = L.gals_diagnostics_noalloc(2, n2, lo, hi, fake, None, 8, 256, 0, None, ctypes.byref(out))
+    assert st == G.ERR_ARG  # row pitch smaller than the grid
