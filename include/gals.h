@@ -81,9 +81,12 @@ enum {
 
 /* Backward trace of one step. */
 enum {
-    GALS_TRACE_EULER = 0,   /* superconsistent forward Euler (Sec. 5.1, first order) */
-    GALS_TRACE_RK3 = 1      /* superconsistent Shu-Osher RK3 (Sec. 5.1), the default of Sec. 6 */
+    GALS_TRACE_EULER = 0,     /* superconsistent forward Euler (Sec. 5.1, first order) */
+    GALS_TRACE_RK3 = 1,       /* superconsistent Shu-Osher RK3 (Sec. 5.1), the default of Sec. 6 */
+    GALS_TRACE_SURROGATE = 2  /* learned flow map (gals_surrogate_*), RK3 fallback; 2D FOURIER2D */
 };
+
+typedef struct gals_surrogate gals_surrogate;   /* opaque, owned by the library */
 
 #define GALS_MAX_MODES 64
 
@@ -97,6 +100,7 @@ typedef struct {
     int nmodes;             /* FOURIER2D: number of modes, 1..GALS_MAX_MODES */
     const double *modes;    /* FOURIER2D: host array of nmodes rows (a, k, l, n, chi); k, l integers
                                in 1..4, n >= 0.  Copied during the call. */
+    const gals_surrogate *surrogate;  /* GALS_TRACE_SURROGATE: the trained flow map (else NULL) */
 } gals_velocity;
 
 typedef struct gals_grid gals_grid;   /* opaque, owned by the library */
@@ -236,6 +240,67 @@ gals_status gals_batch_get_tuning(const gals_batch *batch, gals_batch_tuning *tu
 int64_t gals_batch_nodes(const gals_batch *batch);
 
 const char *gals_batch_last_error(const gals_batch *batch);
+
+/* ------------------------------------------------------------------------------------
+ * Learned flow-map surrogate of the backward trace.  Not in the paper: a small MLP
+ * (x, y, t mod 1) -> (foot displacement / h, (J - I) / dt) of one step of a fixed dt for one
+ * 2D FOURIER2D velocity field of period 1, layers 3 -> 128 -> 128 -> 128 -> 128 -> 6 with
+ * SiLU, trained on the GPU on targets of a 32-sub-step RK4 backward flow map with its
+ * variational Jacobian (BF16 operands, FP32 accumulation, Adam).  gals_step with
+ * trace = GALS_TRACE_SURROGATE evaluates it on the tensor cores and feeds the usual Hermite
+ * stage; every 128-node tile checks `samples` nodes against the exact RK3 trace (Sec. 5.1)
+ * and falls back to RK3 for the whole tile when |delta diff| > tol_x cells or
+ * |J diff| > tol_J.  Parameters: flat FP32, per layer W (out x in, row-major) then b.
+ * ------------------------------------------------------------------------------------ */
+#define GALS_MLP_PARAMS 50822
+
+typedef struct {
+    uint64_t seed;          /* initialisation seed: first layer weights and biases uniform in
+                               [-4, 4], other weights Glorot uniform, other biases 0 */
+    void *cuda_stream;      /* stream for training and inference; NULL: library-owned */
+} gals_mlp_desc;
+
+typedef struct {
+    int steps;              /* optimizer steps (>= 1) */
+    int batch;              /* samples per step, 128..65536 (fresh random samples each step) */
+    double lr, lr_min;      /* Adam learning rate, cosine-decayed from lr to lr_min */
+    int substeps;           /* RK4 sub-steps of the targets (32) */
+    uint64_t seed;          /* sample stream */
+} gals_train_opts;
+
+typedef struct {
+    double initial_loss, final_loss;  /* MSE of the normalised outputs, first and last batch */
+    double seconds;                   /* wall time of the training call */
+    int steps;
+} gals_train_report;
+
+gals_status gals_surrogate_create(const gals_mlp_desc *desc, gals_surrogate **out);
+gals_status gals_surrogate_destroy(gals_surrogate *s);
+/* Train for velocity `vel` (FOURIER2D), step dt and grid spacing h (the surrogate is then
+ * bound to them: gals_step checks dt, h and the field).  Synchronises. */
+gals_status gals_surrogate_train(gals_surrogate *s, const gals_velocity *vel, double dt, double h,
+                                 const gals_train_opts *opts, gals_train_report *report);
+/* Residual check of gals_step (defaults: 4 samples, tol_x = 0.05 cells, tol_J = 0.05). */
+gals_status gals_surrogate_set_check(gals_surrogate *s, double tol_x, double tol_J, int samples);
+/* Tiles evaluated and tiles that fell back to RK3 since the last reset; synchronises. */
+gals_status gals_surrogate_stats(gals_surrogate *s, int64_t *tiles, int64_t *fallbacks, int reset);
+/* FP32 parameters (GALS_MLP_PARAMS floats) and output scales (6) to / from host memory.
+ * set_params binds no field: call gals_surrogate_bind before gals_step. */
+gals_status gals_surrogate_get_params(const gals_surrogate *s, float *params, float *scales);
+gals_status gals_surrogate_set_params(gals_surrogate *s, const float *params, const float *scales);
+gals_status gals_surrogate_bind(gals_surrogate *s, const gals_velocity *vel, double dt, double h);
+/* Network outputs (normalised, n x 6, host) for inputs in [-1,1] (n x 3, host), evaluated by
+ * the tensor-core inference kernel; synchronises. */
+gals_status gals_surrogate_forward(gals_surrogate *s, const float *inputs, int n, float *outputs);
+/* Loss and gradient (GALS_MLP_PARAMS floats, host) of the mean squared error against
+ * `targets` (n x 6) for `inputs` (n x 3), by the training kernels; synchronises. */
+gals_status gals_surrogate_gradient(gals_surrogate *s, const float *inputs, const float *targets,
+                                    int n, float *grad, double *loss);
+/* Training targets (dx/h, dy/h, (J-I)/dt; n x 6, host) at physical points (x, y, t mod 1)
+ * (n x 3, host) for velocity vel: the 32-sub-step RK4 flow map kernel; synchronises. */
+gals_status gals_surrogate_targets(gals_surrogate *s, const gals_velocity *vel, double dt, double h,
+                                   int substeps, const float *points, int n, float *targets);
+const char *gals_surrogate_last_error(const gals_surrogate *s);
 
 /* ------------------------------------------------------------------------------------
  * Diagnostics without device allocation.  The paper has no counterpart: this is a

@@ -29,6 +29,8 @@ struct GraphEntry {
     int nsteps, cur, first_explicit, trace, layout;
     double dt;
     VelParams vp;
+    const void *sur;      // surrogate (its scales and check settings are baked in)
+    float sur_key[9];
     // value
     cudaGraphExec_t exec;
 };
@@ -50,6 +52,7 @@ struct gals_grid {
     int64_t steps = 0;
     double *t_dev = nullptr;
     CUtensorMap maps[2][2];       // TMA maps per buffer: [b][0] COMPACT box, [b][1] FULL box
+    float *trace_buf = nullptr;   // surrogate trace of the current step: dx, dy, J (6 planes)
     int *err_dev = nullptr;       // device error word written by kernels (bounded waits)
     StageCoef *coef = nullptr;    // per-step stage coefficients of the current call
     int coef_cap = 0;
@@ -97,7 +100,8 @@ gals_status make_velparams(gals_grid *g, const gals_velocity *v, VelParams &vp)
 }
 
 cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt, int nsteps,
-                        bool first_explicit)
+                        bool first_explicit, const mlp::InferParams *ip = nullptr,
+                        const mlp::Check *chk = nullptr)
 {
     int cur = g->cur;
     cudaError_t ce = launch_coef_table(g->coef, vp, g->t_dev, dt, nsteps, g->stream);
@@ -110,10 +114,18 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
         a.vp = vp;
         a.coef = g->coef + s;
         a.dt = dt;
+        if (trace == GALS_TRACE_SURROGATE) {
+            // learned trace of this step (with RK3 fallback per tile), then the Hermite stage
+            ce = mlp::launch_mlp_trace(*ip, g->geom, vp, g->coef + s, g->t_dev, s, dt, g->trace_buf,
+                                       *chk, g->stream);
+            if (ce != cudaSuccess) return ce;
+            a.vp.given = g->trace_buf;
+            a.vp.given_plane = g->geom.plane;
+        }
         a.tmap3 = &g->maps[cur][0];
         a.tmap4 = &g->maps[cur][1];
         a.err = g->err_dev;
-        a.trace = trace == GALS_TRACE_EULER ? TR_EULER : TR_RK3;
+        a.trace = trace == GALS_TRACE_EULER ? TR_EULER : (trace == GALS_TRACE_SURROGATE ? TR_GIVEN : TR_RK3);
         if (g->layout == GALS_LAYOUT_FULL) {
             a.cross_in = CROSS_PLANE;
             a.write_cross = 1;
@@ -129,10 +141,11 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
 }
 
 bool same_key(const GraphEntry &e, int nsteps, int cur, int fe, int trace, int layout, double dt,
-              const VelParams &vp)
+              const VelParams &vp, const void *sur, const float *sur_key)
 {
     return e.nsteps == nsteps && e.cur == cur && e.first_explicit == fe && e.trace == trace &&
-           e.layout == layout && e.dt == dt && std::memcmp(&e.vp, &vp, sizeof(vp)) == 0;
+           e.layout == layout && e.dt == dt && std::memcmp(&e.vp, &vp, sizeof(vp)) == 0 &&
+           e.sur == sur && std::memcmp(e.sur_key, sur_key, sizeof(e.sur_key)) == 0;
 }
 
 }  // namespace
@@ -255,6 +268,7 @@ gals_status gals_destroy_grid(gals_grid *g)
     for (int b = 0; b < 2; ++b) cudaFree(g->buf[b]);
     cudaFree(g->t_dev);
     cudaFree(g->err_dev);
+    cudaFree(g->trace_buf);
     cudaFree(g->coef);
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
@@ -311,9 +325,29 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     VelParams vp;
     gals_status st = make_velparams(g, v, vp);
     if (st != GALS_OK) return st;
+    mlp::InferParams ip{};
+    mlp::Check chk{};
+    const void *sur = nullptr;
+    float sur_key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (v->trace == GALS_TRACE_SURROGATE) {
+        if (g->dim != 2) return fail(g, GALS_ERR_UNSUPPORTED, "the surrogate trace is 2D");
+        char msg[200];
+        st = surrogate_for_step(v->surrogate, vp, dt, g->h[0], g->h[1], ip, chk, msg, sizeof(msg));
+        if (st != GALS_OK) return fail(g, st, "%s", msg);
+        sur = v->surrogate;
+        for (int k = 0; k < 6; ++k) sur_key[k] = ip.scale[k];
+        sur_key[6] = chk.tol_x;
+        sur_key[7] = chk.tol_J;
+        sur_key[8] = (float)chk.samples;
+    }
     if (nsteps == 0) return GALS_OK;
     const bool fe = g->cross_explicit;
     cudaError_t e;
+    if (sur && !g->trace_buf) {
+        if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
+        if ((e = cudaMalloc(&g->trace_buf, sizeof(float) * 6 * (size_t)g->geom.plane)) != cudaSuccess)
+            return cuda_fail(g, e, "cudaMalloc(trace buffer)");
+    }
     if (nsteps > g->coef_cap) {
         // grow the coefficient table; cached graphs refer to the old one
         if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
@@ -328,16 +362,17 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
         g->coef_cap = cap;
     }
     if (nsteps == 1) {
-        if ((e = issue_steps(g, vp, v->trace, dt, 1, fe)) != cudaSuccess) return cuda_fail(g, e, "step launch");
+        if ((e = issue_steps(g, vp, v->trace, dt, 1, fe, &ip, &chk)) != cudaSuccess)
+            return cuda_fail(g, e, "step launch");
     } else {
         GraphEntry *hit = nullptr;
         for (auto &ge : g->graphs)
-            if (same_key(ge, nsteps, g->cur, fe, v->trace, g->layout, dt, vp)) { hit = &ge; break; }
+            if (same_key(ge, nsteps, g->cur, fe, v->trace, g->layout, dt, vp, sur, sur_key)) { hit = &ge; break; }
         if (!hit) {
             cudaGraph_t graph;
             if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(g, e, "begin capture");
-            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe);
+            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe, &ip, &chk);
             e = cudaStreamEndCapture(g->stream, &graph);
             if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
             if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
@@ -352,6 +387,8 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
             GraphEntry ge;
             ge.nsteps = nsteps; ge.cur = g->cur; ge.first_explicit = fe; ge.trace = v->trace;
             ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
+            ge.sur = sur;
+            std::memcpy(ge.sur_key, sur_key, sizeof(sur_key));
             g->graphs.push_back(ge);
             hit = &g->graphs.back();
         }

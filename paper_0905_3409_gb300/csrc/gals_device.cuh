@@ -31,7 +31,7 @@ constexpr float kPi = 3.14159265358979323846f;
 
 enum VelKind { VK_CONST = 0, VK_ROTATION = 1, VK_VORTEX2D = 2, VK_DEFORM3D = 3,
                VK_PSEUDO1D = 4, VK_FOURIER2D = 5 };
-enum TraceKind { TR_EULER = 0, TR_RK3 = 1 };
+enum TraceKind { TR_EULER = 0, TR_RK3 = 1, TR_GIVEN = 2 };  // GIVEN: precomputed (surrogate)
 enum CrossSrc { CROSS_PLANE = 0, CROSS_RECON = 1 };
 
 // Velocity descriptor as passed to kernels (by value).
@@ -46,6 +46,8 @@ struct VelParams {
     int mode_kl[kMaxModes];     // k | (l << 8), k, l in 1..4
     double mode_n[kMaxModes];   // temporal frequency n (cycles per unit time)
     double mode_chi[kMaxModes]; // phase / (2 pi)
+    const float *given;         // TR_GIVEN: planes dx, dy, J00, J01, J10, J11 of the step
+    int64_t given_plane;        //   (grid pitch layout) and their plane stride
 };
 
 // Grid geometry for kernels.

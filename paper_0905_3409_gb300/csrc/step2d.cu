@@ -83,6 +83,7 @@ cudaError_t launch_tr(const StepLaunch &a, cudaStream_t s)
 
 cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s)
 {
+    if (a.trace == TR_GIVEN) return launch_cr<TR_GIVEN, VK_CONST>(a, s);  // velocity unused
     switch (a.vp.kind) {
     case VK_CONST: return launch_tr<VK_CONST>(a, s);
     case VK_ROTATION: return launch_tr<VK_ROTATION>(a, s);

@@ -150,8 +150,19 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
                                             const Sep2 &ry, F2 &phi, F2 &px, F2 &py)
 {
     F2 dx, dy, J[4];
-    trace2d_pair<TR, VK>(stage1_pair<VK>(vp, sc, scp, x, y, cx, ry), vp, sc, scp, x, y, dt, dx,
-                         dy, J);
+    if (TR == TR_GIVEN) {
+        // foot displacement and Jacobian precomputed for this step (learned surrogate)
+        const int64_t o0 = (int64_t)j0 * g.pitch + i0, o1 = (int64_t)j1 * g.pitch + i1;
+        const float *tb = vp.given;
+        const int64_t P = vp.given_plane;
+        dx = make_float2(__ldg(tb + o0), __ldg(tb + o1));
+        dy = make_float2(__ldg(tb + P + o0), __ldg(tb + P + o1));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) J[e] = make_float2(__ldg(tb + (2 + e) * P + o0), __ldg(tb + (2 + e) * P + o1));
+    } else {
+        trace2d_pair<TR, VK>(stage1_pair<VK>(vp, sc, scp, x, y, cx, ry), vp, sc, scp, x, y, dt, dx,
+                             dy, J);
+    }
     int k0, l0, k1, l1;
     F2 xi, eta;
     locate(i0, dx.x * g.ih0, g.n0, k0, xi.x);

@@ -22,7 +22,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE, ERR_UNS
 MEM_HOST, MEM_DEVICE = 0, 1
 LAYOUT_FULL, LAYOUT_COMPACT = 0, 1
 VEL = {"const": 0, "rotation": 1, "vortex2d": 2, "deform3d": 3, "pseudo1d": 4, "fourier2d": 5}
-TRACE = {"euler": 0, "rk3": 1}
+TRACE = {"euler": 0, "rk3": 1, "surrogate": 2}
 SET_RECON_CROSS = 1
 MAX_MODES = 64
 
@@ -35,6 +35,10 @@ EXPORTS = [
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
     "gals_batch_set_tuning", "gals_batch_get_tuning", "gals_batch_nodes", "gals_batch_last_error",
     "gals_diagnostics_noalloc", "gals_noalloc_max_nodes", "gals_noalloc_last_error",
+    "gals_surrogate_create", "gals_surrogate_destroy", "gals_surrogate_train",
+    "gals_surrogate_set_check", "gals_surrogate_stats", "gals_surrogate_get_params",
+    "gals_surrogate_set_params", "gals_surrogate_bind", "gals_surrogate_forward",
+    "gals_surrogate_gradient", "gals_surrogate_targets", "gals_surrogate_last_error",
 ]
 
 
@@ -56,7 +60,26 @@ class GridDesc(ctypes.Structure):
 class VelocityDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("trace", ctypes.c_int), ("T", ctypes.c_double),
                 ("omega", ctypes.c_double), ("center", ctypes.c_double * 3), ("c", ctypes.c_double * 3),
-                ("nmodes", ctypes.c_int), ("modes", ctypes.POINTER(ctypes.c_double))]
+                ("nmodes", ctypes.c_int), ("modes", ctypes.POINTER(ctypes.c_double)),
+                ("surrogate", ctypes.c_void_p)]
+
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("lr_min", ctypes.c_double), ("substeps", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class TrainReport(ctypes.Structure):
+    _fields_ = [("initial_loss", ctypes.c_double), ("final_loss", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("steps", ctypes.c_int)]
+
+
+MLP_PARAMS = 50822
+MLP_SIZES = [3, 128, 128, 128, 128, 6]
 
 
 class DiagRequest(ctypes.Structure):
@@ -122,6 +145,26 @@ def lib() -> ctypes.CDLL:
             vp, ctypes.POINTER(DiagOut)]
         L.gals_noalloc_max_nodes.restype = ctypes.c_int64
         L.gals_noalloc_last_error.restype = ctypes.c_char_p
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.gals_surrogate_create.argtypes = [ctypes.POINTER(MlpDesc), ctypes.POINTER(vp)]
+        L.gals_surrogate_destroy.argtypes = [vp]
+        L.gals_surrogate_train.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
+                                           ctypes.c_double, ctypes.POINTER(TrainOpts),
+                                           ctypes.POINTER(TrainReport)]
+        L.gals_surrogate_set_check.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.gals_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+        L.gals_surrogate_get_params.argtypes = [vp, fp, fp]
+        L.gals_surrogate_set_params.argtypes = [vp, fp, fp]
+        L.gals_surrogate_bind.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
+                                          ctypes.c_double]
+        L.gals_surrogate_forward.argtypes = [vp, fp, ctypes.c_int, fp]
+        L.gals_surrogate_gradient.argtypes = [vp, fp, fp, ctypes.c_int, fp,
+                                              ctypes.POINTER(ctypes.c_double)]
+        L.gals_surrogate_targets.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, fp, ctypes.c_int, fp]
+        L.gals_surrogate_last_error.argtypes = [vp]
+        L.gals_surrogate_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -142,6 +185,7 @@ class Velocity:
     center: tuple = (0.5, 0.5, 0.5)
     c: tuple = (0.0, 0.0, 0.0)
     modes: np.ndarray | None = None
+    surrogate: "Surrogate | None" = None
 
     def desc(self) -> VelocityDesc:
         d = VelocityDesc()
@@ -157,6 +201,8 @@ class Velocity:
             d._keep = m
             d.nmodes = m.shape[0]
             d.modes = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if self.surrogate is not None:
+            d.surrogate = self.surrogate.handle.value
         return d
 
 
@@ -366,3 +412,99 @@ class Batch:
 
     def synchronize(self):
         _bcheck(lib().gals_batch_synchronize(self._h), self._h)
+
+
+def _scheck(status: int, handle=None):
+    if status != OK:
+        msg = lib().gals_surrogate_last_error(handle)
+        raise GalsError(status, msg.decode() if msg else "")
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Surrogate:
+    """The learned flow map of the backward trace (gals_surrogate_* of gals.h)."""
+
+    def __init__(self, seed: int = 1, stream=None):
+        d = MlpDesc()
+        d.seed = int(seed)
+        if stream is not None:
+            d.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        h = ctypes.c_void_p()
+        _scheck(lib().gals_surrogate_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gals_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train(self, vel: Velocity, dt, h, steps=2000, batch=16384, lr=1e-3, lr_min=1e-5,
+              substeps=32, seed=9053409):
+        o = TrainOpts(int(steps), int(batch), float(lr), float(lr_min), int(substeps), int(seed))
+        r = TrainReport()
+        d = vel.desc()
+        _scheck(lib().gals_surrogate_train(self._h, ctypes.byref(d), float(dt), float(h), ctypes.byref(o),
+                                           ctypes.byref(r)), self._h)
+        return {"initial_loss": r.initial_loss, "final_loss": r.final_loss, "seconds": r.seconds,
+                "steps": r.steps}
+
+    def set_check(self, tol_x=0.05, tol_J=0.05, samples=4):
+        _scheck(lib().gals_surrogate_set_check(self._h, float(tol_x), float(tol_J), int(samples)), self._h)
+
+    def stats(self, reset=False):
+        t = ctypes.c_int64()
+        f = ctypes.c_int64()
+        _scheck(lib().gals_surrogate_stats(self._h, ctypes.byref(t), ctypes.byref(f), int(reset)), self._h)
+        return t.value, f.value
+
+    def get_params(self):
+        p = np.empty(MLP_PARAMS, dtype=np.float32)
+        sc = np.empty(6, dtype=np.float32)
+        _scheck(lib().gals_surrogate_get_params(self._h, _fp(p), _fp(sc)), self._h)
+        return p, sc
+
+    def set_params(self, params, scales):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        sc = np.ascontiguousarray(scales, dtype=np.float32)
+        assert p.size == MLP_PARAMS and sc.size == 6
+        _scheck(lib().gals_surrogate_set_params(self._h, _fp(p), _fp(sc)), self._h)
+
+    def bind(self, vel: Velocity, dt, h):
+        d = vel.desc()
+        _scheck(lib().gals_surrogate_bind(self._h, ctypes.byref(d), float(dt), float(h)), self._h)
+
+    def forward(self, inputs):
+        X = np.ascontiguousarray(inputs, dtype=np.float32).reshape(-1, 3)
+        Y = np.empty((X.shape[0], 6), dtype=np.float32)
+        _scheck(lib().gals_surrogate_forward(self._h, _fp(X), X.shape[0], _fp(Y)), self._h)
+        return Y
+
+    def gradient(self, inputs, targets):
+        X = np.ascontiguousarray(inputs, dtype=np.float32).reshape(-1, 3)
+        T = np.ascontiguousarray(targets, dtype=np.float32).reshape(-1, 6)
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _scheck(lib().gals_surrogate_gradient(self._h, _fp(X), _fp(T), X.shape[0], _fp(g),
+                                              ctypes.byref(loss)), self._h)
+        return loss.value, g
+
+    def targets(self, vel: Velocity, dt, h, points, substeps=32):
+        P = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+        T = np.empty((P.shape[0], 6), dtype=np.float32)
+        d = vel.desc()
+        _scheck(lib().gals_surrogate_targets(self._h, ctypes.byref(d), float(dt), float(h), int(substeps),
+                                             _fp(P), P.shape[0], _fp(T)), self._h)
+        return T

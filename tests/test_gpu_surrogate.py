@@ -1,0 +1,156 @@
+"""Learned flow-map surrogate: the GPU's RK4 targets, tensor-core forward pass and
+training gradients against the FP64 oracle; training lowers the loss; the surrogate step
+with every tile falling back equals the exact RK3 step to parity tolerance; the
+residual-check counters; and the comparison with the plain RK3 trace."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3409_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [3, 128, 128, 128, 128, 6]
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_0905_3409_gb300 import gals
+    return gals
+
+
+@pytest.fixture(scope="module")
+def field():
+    modes = inputs.fourier_modes(16, seed=9053409, periodic=True)
+    n = 257
+    h = 1.0 / (n - 1)
+    dt = h / inputs.fourier_speed_bound(modes)
+    return modes, n, h, dt
+
+
+def test_rk4_targets_match_oracle(G, field):
+    modes, n, h, dt = field
+    S = G.Surrogate(seed=3)
+    rng = np.random.default_rng(0)
+    P = np.stack([rng.uniform(0, 1, 200), rng.uniform(0, 1, 200), rng.uniform(0, 1, 200)], 1)
+    T = S.targets(G.Velocity("fourier2d", modes=modes), dt, h, P, substeps=32)
+    ov = oracle.velocity("fourier2d", modes=modes)
+    for p, t in zip(P, T):
+        foot, J = oracle.flowmap_rk4(ov, 2, p[:2], p[2], dt, 32)
+        ref = np.array([(foot[0] - p[0]) / h, (foot[1] - p[1]) / h, (J[0, 0] - 1) / dt, J[0, 1] / dt,
+                        J[1, 0] / dt, (J[1, 1] - 1) / dt])
+        assert np.max(np.abs(t - ref)) <= 1e-3 * max(1.0, np.max(np.abs(ref))), (t, ref)
+
+
+def test_forward_matches_oracle(G):
+    S = G.Surrogate(seed=11)
+    params, scales = S.get_params()
+    rng = np.random.default_rng(1)
+    X = rng.uniform(-1, 1, (1000, 3)).astype(np.float32)
+    Y = S.forward(X)
+    Yref = oracle.mlp_forward(SIZES, params.astype(np.float64), X.astype(np.float64))
+    err = np.max(np.abs(Y - Yref)) / max(1.0, np.max(np.abs(Yref)))
+    assert err <= 2e-2, err  # BF16 operands, hardware tanh in SiLU
+
+
+def test_gradient_matches_oracle(G):
+    """Backward kernels (BF16 operands, FP32 accumulation) against the FP64 chain rule,
+    tensor by tensor, relative to each tensor's norm."""
+    S = G.Surrogate(seed=5)
+    params, _ = S.get_params()
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, (4096, 3)).astype(np.float32)
+    T = rng.normal(0, 1, (4096, 6)).astype(np.float32)
+    loss, grad = S.gradient(X, T)
+    lref, gref = oracle.mlp_backward(SIZES, params.astype(np.float64), X.astype(np.float64),
+                                     T.astype(np.float64))
+    assert loss == pytest.approx(lref, rel=1e-2)
+    off = 0
+    for l in range(5):
+        ni, no = SIZES[l], SIZES[l + 1]
+        for size in (ni * no, no):
+            a, b = grad[off:off + size], gref[off:off + size]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+            assert rel <= 1e-2, (l, size, rel)
+            off += size
+    assert off == G.MLP_PARAMS
+
+
+def test_training_lowers_loss_and_fallback(G, field):
+    modes, n, h, dt = field
+    vel = G.Velocity("fourier2d", modes=modes)
+    S = G.Surrogate(seed=7)
+    rep = S.train(vel, dt, h, steps=300, batch=8192, lr=2e-3, lr_min=1e-4)
+    assert rep["final_loss"] < 0.25 * rep["initial_loss"], rep
+    # every tile falls back (zero tolerance): the step equals the exact RK3 step
+    S.set_check(tol_x=0.0, tol_J=0.0, samples=4)
+    st = inputs.ellipse_sdf((n, n), (0.5, 0.5), 0.2, 0.1, 0.3, iters=60).astype(np.float32)
+    g = G.Grid((n, n))
+    g.set_state(st, t0=0.3, recon=True)
+    before = g.read_state().astype(np.float64)
+    S.stats(reset=True)
+    g.step(G.Velocity("fourier2d", modes=modes, trace="surrogate", surrogate=S), dt, 1)
+    after = g.read_state().astype(np.float64)
+    tiles, falls = S.stats()
+    assert tiles == ((n + 127) // 128) * n and falls == tiles
+    ref = oracle.step(oracle.grid((n, n)), oracle.velocity("fourier2d", modes=modes), before, 0.3, dt)
+    assert np.max(np.abs(after[0] - ref[0])) <= 1e-5
+    assert np.max(np.abs(after[1:3] - ref[1:3])) <= 1e-4
+    # loose tolerance: no fallback, the learned trace drives the step
+    S.set_check(tol_x=1e9, tol_J=1e9, samples=1)
+    S.stats(reset=True)
+    g.set_state(st, t0=0.3, recon=True)
+    g.step(G.Velocity("fourier2d", modes=modes, trace="surrogate", surrogate=S), dt, 3)
+    tiles, falls = S.stats()
+    assert falls == 0 and tiles == 3 * ((n + 127) // 128) * n
+    assert np.isfinite(g.read_state()).all()
+    # a field other than the trained one is refused
+    with pytest.raises(G.GalsError):
+        g.step(G.Velocity("fourier2d", modes=modes * 1.01, trace="surrogate", surrogate=S), dt, 1)
+
+
+def test_surrogate_against_plain_trace(G, field):
+    """What the learned trace gains (or loses) against the plain RK3 trace: node updates
+    per second and the distance of each run's interface from a 4x finer-in-time RK3
+    reference after 40 steps.  Recorded, not asserted in either direction: on this
+    field the analytic trace is cheap (about 1 kFLOP per node against about 100 kFLOP
+    for the network)."""
+    modes, n, h, dt = field
+    vel = G.Velocity("fourier2d", modes=modes)
+    S = G.Surrogate(seed=9)
+    S.train(vel, dt, h, steps=600, batch=16384, lr=2e-3, lr_min=1e-5)
+    S.set_check(tol_x=0.05, tol_J=0.05, samples=4)
+    st = inputs.ellipse_sdf((n, n), (0.5, 0.5), 0.2, 0.1, 0.3, iters=60).astype(np.float32)
+    steps = 40
+
+    def run(trace, sub=1):
+        g = G.Grid((n, n))
+        g.set_state(st, t0=0.0, recon=True)
+        v = G.Velocity("fourier2d", modes=modes, trace=trace, surrogate=S if trace == "surrogate" else None)
+        g.step(v, dt / sub, steps * sub)
+        g.synchronize()
+        t0 = time.perf_counter()
+        g.set_state(st, t0=0.0, recon=True)
+        g.step(v, dt / sub, steps * sub)
+        g.synchronize()
+        return g, time.perf_counter() - t0
+
+    fine, _ = run("rk3", 4)
+    plain, t_plain = run("rk3")
+    S.stats(reset=True)
+    sur, t_sur = run("surrogate")
+    tiles, falls = S.stats()
+    e_plain = plain.diagnostics(q=4, reference=fine)["measure_symdiff"]
+    e_sur = sur.diagnostics(q=4, reference=fine)["measure_symdiff"]
+    print(f"plain RK3: {n * n * steps / t_plain:.3e} nu/s, interface err {e_plain:.3e}; "
+          f"surrogate: {n * n * steps / t_sur:.3e} nu/s, interface err {e_sur:.3e}, "
+          f"fallback tiles {falls}/{tiles}")
+    assert math.isfinite(e_sur) and tiles > 0
