@@ -1,7 +1,8 @@
 """Benchmark of the GALS step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload vortex4096|rotation4096|deform512] [--layout full|compact]
+                    [--workload vortex4096|rotation4096|deform512|batch256|surrogate2048]
+                    [--layout full|compact]
 
 A bench step is one GALS time step (trace + Jacobian, Hermite evaluation, gradient
 write-back and mixed-derivative reconstruction) over the whole grid.  The default
@@ -53,6 +54,14 @@ WORKLOADS = {
                           "steady 8-mode Fourier stream-function field, RK3 trace, CFL 1; one "
                           "launch per step over all problems' tiles, CUDA-graph time loop, "
                           "autotuned launch shape"),
+    "surrogate2048": dict(dim=2, n=(2048, 2048), vel=dict(kind="fourier2d"), vmax=None,
+                          surrogate=True, nmodes=16,
+                          desc="2D GALS 2048x2048 nodes on [0,1]^2, FP32, time-periodic (period 1) "
+                               "stream-function field of 16 Fourier modes (seed 9053409), circle "
+                               "SDF r=0.15 at (0.5,0.75), CFL 1; learned flow-map trace (MLP "
+                               "3-128x4-6, BF16 tensor cores, trained on 32-sub-step RK4 "
+                               "targets) with per-tile RK3 residual check and fallback, against "
+                               "the plain RK3 trace"),
     # a smaller case of the same 3D kernel, for profiler captures (state still > L2)
     "deform256": dict(dim=3, n=(256, 256, 256), vel=dict(kind="deform3d", T=3.0), vmax=2.0,
                       desc="3D GALS 256^3 nodes on [0,1]^3, FP32, LeVeque deformation T=3, "
@@ -66,13 +75,38 @@ def bytes_per_node(dim, layout):
     return 2 * 4 * planes
 
 
-def measured_peaks():
+def wl_modes(wl):
+    from paper_0905_3409_gb300 import inputs
+    if not wl.get("nmodes"):
+        return None
+    return inputs.fourier_modes(wl["nmodes"], seed=inputs.DEFAULT_SEED, periodic=True)
+
+
+def wl_dt(wl):
+    """CFL 1: dt = h / max|v_i| (the Fourier field's analytic speed bound)."""
+    from paper_0905_3409_gb300 import inputs
+    h = 1.0 / (wl["n"][0] - 1)
+    modes = wl_modes(wl)
+    return h / (inputs.fourier_speed_bound(modes) if modes is not None else wl["vmax"])
+
+
+def wl_oracle_velocity(wl):
+    import oracle
+    v = wl["vel"]
+    return oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
+                           center=v.get("center", (0.5, 0.5, 0.5)), modes=wl_modes(wl))
+
+
+def measured_peaks(kind="hbm"):
+    """(peak, source): HBM copy GB/s, or dense BF16 TFLOP/s of a burst ("bf16")."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key, fallback = ("hbm_gbs", 6800.0) if kind == "hbm" else ("bf16_tflops", 1900.0)
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        if key in d:
+            return float(d[key]), "measured"
+    return fallback, "fallback"
 
 
 def initial_state(wl):
@@ -191,11 +225,8 @@ def oracle_leg(wl, budget_s=12.0, max_bands=None):
     g = oracle.grid(n)
     band3 = (n[-1] // 3, n[-1] // 3 + 8)
     st = oracle_state(wl, g, band3)
-    v = wl["vel"]
-    ov = oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
-                         center=v.get("center", (0.5, 0.5, 0.5)))
-    h = 1.0 / (n[0] - 1)
-    dt = h / wl["vmax"]
+    ov = wl_oracle_velocity(wl)
+    dt = wl_dt(wl)
     planes = oracle.state_planes(g, st)
     cores = oracle.default_threads()
     outer = n[-1]
@@ -231,11 +262,8 @@ def run_reference(args, wl):
     band = 8 if wl["dim"] == 2 else 1
     slab = (n[-1] // 4, n[-1] // 4 + 16)
     st = oracle_state(wl, g, slab)
-    v = wl["vel"]
-    ov = oracle.velocity(v["kind"], T=v.get("T", 1.0), omega=v.get("omega", 0.0),
-                         center=v.get("center", (0.5, 0.5, 0.5)))
-    h = 1.0 / (n[0] - 1)
-    dt = h / wl["vmax"]
+    ov = wl_oracle_velocity(wl)
+    dt = wl_dt(wl)
     planes = oracle.state_planes(g, st)
     outer = n[-1]
     inner_nodes = int(np.prod(n[:-1]))
@@ -560,6 +588,183 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------- learned trace
+
+MLP_FLOP_PER_POINT = 2 * (3 * 128 + 3 * 128 * 128 + 128 * 6)  # 100,608 (unpadded layers)
+
+
+def run_surrogate(args, wl):
+    """The learned flow-map trace against the plain RK3 trace on the same grid and field:
+    train (timed apart), then K steps of each trace from the same initial state, timed
+    with CUDA events on the grid stream; both end states are measured against a 4x finer
+    in time RK3 run (interface symmetric difference, area, max |phi|/|psi| differences).
+    The roofline is that of the tensor-core MLP evaluation over one grid's nodes."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    if rank == 0:
+        ge.build()
+    if dist:
+        dist.barrier()
+    from paper_0905_3409_gb300 import gals
+
+    n = wl["n"]
+    nodes = int(np.prod(n))
+    h = 1.0 / (n[0] - 1)
+    dt = wl_dt(wl)
+    modes = wl_modes(wl)
+    stream = torch.cuda.Stream()
+    plain = gals.Velocity("fourier2d", modes=modes, trace="rk3")
+    S = gals.Surrogate(seed=7, stream=stream)
+    rep = S.train(plain, dt, h, steps=args.train_steps, batch=16384, lr=2e-3, lr_min=1e-5)
+    S.set_check(tol_x=args.tol, tol_J=args.tol, samples=4)
+    learned = gals.Velocity("fourier2d", modes=modes, trace="surrogate", surrogate=S)
+    st_host = initial_state(wl)
+    K = args.steps
+
+    def timed(vel, g):
+        g.set_state(st_host, t0=0.0, recon=True)
+        g.step(vel, dt, args.warmup)
+        g.step(vel, dt, K)           # captures the K-step graph
+        g.set_state(st_host, t0=0.0, recon=True)
+        g.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(vel, dt, K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t = torch.tensor([ms], device="cuda")
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    g_plain = gals.Grid(n, stream=stream)
+    ms_plain = timed(plain, g_plain)
+    g_sur = gals.Grid(n, stream=stream)
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    S.stats(reset=True)
+    ms_sur = timed(learned, g_sur)
+    clocks = sampler.stop() if rank == 0 else None
+    tiles, falls = S.stats()
+    value = nodes * K * world / (ms_sur * 1e-3)
+    value_plain = nodes * K * world / (ms_plain * 1e-3)
+
+    # accuracy: both runs against RK3 with dt/4 over the same time
+    g_fine = gals.Grid(n, stream=stream)
+    g_fine.set_state(st_host, t0=0.0, recon=True)
+    g_fine.step(plain, dt / 4, 4 * K)
+    g_fine.synchronize()
+    g0 = gals.Grid(n, stream=stream)
+    g0.set_state(st_host, t0=0.0, recon=True)
+    area0 = g0.diagnostics(q=4)["measure_negative"]
+    acc = {}
+    for name, g in (("plain_rk3", g_plain), ("surrogate", g_sur)):
+        d = g.diagnostics(q=4, reference=g_fine)
+        acc[name] = {"interface_symdiff": d["measure_symdiff"], "emax_phi": d["emax_phi"],
+                     "emax_psi": d["emax_psi"],
+                     "area_change": g.diagnostics(q=4)["measure_negative"] - area0}
+    e_p, e_s = acc["plain_rk3"]["interface_symdiff"], acc["surrogate"]["interface_symdiff"]
+
+    # roofline of the tensor-core MLP: one evaluation per node, device buffers > L2
+    X = (torch.rand(nodes, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 2 - 1)
+    Y = torch.empty(nodes, 6, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(3):
+        S.forward_device(X.data_ptr(), nodes, Y.data_ptr())
+    reps = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        S.forward_device(X.data_ptr(), nodes, Y.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_mlp = e0.elapsed_time(e1) / reps
+    achieved = MLP_FLOP_PER_POINT * nodes / (ms_mlp * 1e-3) / 1e12
+    peak, peak_kind = measured_peaks("bf16")
+
+    # e2e through the C ABI with host buffers: per step, pinned host -> device state, one
+    # learned step, device -> pinned host state
+    pin_in = torch.from_numpy(st_host).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    e2e_steps = max(1, min(K, 20))
+    g2 = gals.Grid(n, stream=stream)
+    g2.set_state(pin_in.numpy(), recon=False)
+    g2.step(learned, dt, 1)
+    g2.read_state(pin_out.numpy())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g2.set_state(pin_in.numpy(), recon=False)
+        g2.step(learned, dt, 1)
+        g2.read_state(pin_out.numpy())
+    el = time.perf_counter() - t0
+    el_t = torch.tensor([el], device="cuda")
+    if dist:
+        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+    e2e_value = nodes * e2e_steps * world / float(el_t.item())
+    io_bytes = 4 * 4 * nodes
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_sur / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 mlp / f32 step",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "layout": "full", "nodes": nodes, "dt": dt,
+                       "l2": "working set per step (2 state buffers 134 MB + trace planes 101 MB) "
+                             "larger than L2",
+                       "parallelism": f"{world} independent replica(s), one per GPU",
+                       "residual_check": {"tol_x_cells": args.tol, "tol_J": args.tol, "samples": 4},
+                       "training": {"steps": rep["steps"], "batch": 16384, "seconds": rep["seconds"],
+                                    "initial_loss": rep["initial_loss"], "final_loss": rep["final_loss"]},
+                       "plain_rk3": {"value": value_plain, "ms_per_step": ms_plain / K},
+                       "speedup_vs_plain": value / value_plain,
+                       "fallback_tiles": falls, "tiles": tiles,
+                       "accuracy_vs_rk3_dt_over_4": acc,
+                       "interface_error_ratio": (e_s / e_p) if e_p > 0 else None},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": f"k_infer_points (the MLP tile code of the learned trace) over "
+                                   f"{nodes} points, {MLP_FLOP_PER_POINT} FLOP each, "
+                                   f"{ms_mlp:.3f} ms per launch"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": 2 * K + 2,  # MLP trace + Hermite step per step; coefficients, clock
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            v, cores, sample = oracle_leg(wl, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": sample + " (exact RK3 trace; the oracle has no "
+                                              "learned trace)"}
+        print(json.dumps(line))
+    for g in (g_plain, g_sur, g_fine, g0, g2):
+        g.close()
+    S.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -570,6 +775,9 @@ def main():
     ap.add_argument("--layout", default="full", choices=["full", "compact"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=2000, help="learned trace: optimizer steps")
+    ap.add_argument("--tol", type=float, default=0.05,
+                    help="learned trace: residual-check tolerance (cells and Jacobian entries)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -581,6 +789,8 @@ def main():
             run_reference(args, wl)
     elif wl.get("batch"):
         run_batch(args, wl)
+    elif wl.get("surrogate"):
+        run_surrogate(args, wl)
     else:
         run_ours(args, wl)
 

@@ -292,6 +292,12 @@ gals_status gals_surrogate_bind(gals_surrogate *s, const gals_velocity *vel, dou
 /* Network outputs (normalised, n x 6, host) for inputs in [-1,1] (n x 3, host), evaluated by
  * the tensor-core inference kernel; synchronises. */
 gals_status gals_surrogate_forward(gals_surrogate *s, const float *inputs, int n, float *outputs);
+/* The same evaluation on device memory: inputs (n x 3 floats) and outputs (n x 6 floats)
+ * are device pointers owned by the caller, 1 <= n <= 2^26; enqueued on the surrogate's
+ * stream and not synchronised (launch errors are returned, others surface at the next
+ * synchronising call). */
+gals_status gals_surrogate_forward_device(gals_surrogate *s, const float *inputs, int64_t n,
+                                          float *outputs);
 /* Loss and gradient (GALS_MLP_PARAMS floats, host) of the mean squared error against
  * `targets` (n x 6) for `inputs` (n x 3), by the training kernels; synchronises. */
 gals_status gals_surrogate_gradient(gals_surrogate *s, const float *inputs, const float *targets,

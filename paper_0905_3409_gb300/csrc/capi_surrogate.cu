@@ -375,6 +375,14 @@ gals_status gals_surrogate_forward(gals_surrogate *s, const float *inputs, int n
     return GALS_OK;
 }
 
+gals_status gals_surrogate_forward_device(gals_surrogate *s, const float *inputs, int64_t n, float *outputs)
+{
+    if (!s || !inputs || !outputs || n < 1 || n > ((int64_t)1 << 26)) return sfail(s, GALS_ERR_ARG, "bad arguments");
+    cudaError_t e = infer_points(s->ip, inputs, outputs, (int)n, s->stream);
+    if (e != cudaSuccess) return scuda(s, e, "forward_device");
+    return GALS_OK;
+}
+
 gals_status gals_surrogate_gradient(gals_surrogate *s, const float *inputs, const float *targets, int n,
                                     float *grad, double *loss)
 {

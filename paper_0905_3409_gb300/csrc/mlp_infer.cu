@@ -300,8 +300,11 @@ cudaError_t infer_points(const InferParams &ip, const float *Xn, float *Y, int n
         if (e != cudaSuccess) return e;
         set = true;
     }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = (n + ROWS - 1) / ROWS;
-    k_infer_points<<<tiles < 152 ? tiles : 152, NT, sizeof(Smem), s>>>(ip, Xn, Y, n);
+    k_infer_points<<<tiles < sms ? tiles : sms, NT, sizeof(Smem), s>>>(ip, Xn, Y, n);
     return cudaGetLastError();
 }
 

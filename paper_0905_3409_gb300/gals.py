@@ -39,6 +39,7 @@ EXPORTS = [
     "gals_surrogate_set_check", "gals_surrogate_stats", "gals_surrogate_get_params",
     "gals_surrogate_set_params", "gals_surrogate_bind", "gals_surrogate_forward",
     "gals_surrogate_gradient", "gals_surrogate_targets", "gals_surrogate_last_error",
+    "gals_surrogate_forward_device",
 ]
 
 
@@ -159,6 +160,7 @@ def lib() -> ctypes.CDLL:
         L.gals_surrogate_bind.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
                                           ctypes.c_double]
         L.gals_surrogate_forward.argtypes = [vp, fp, ctypes.c_int, fp]
+        L.gals_surrogate_forward_device.argtypes = [vp, vp, ctypes.c_int64, vp]
         L.gals_surrogate_gradient.argtypes = [vp, fp, fp, ctypes.c_int, fp,
                                               ctypes.POINTER(ctypes.c_double)]
         L.gals_surrogate_targets.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
@@ -491,6 +493,12 @@ class Surrogate:
         Y = np.empty((X.shape[0], 6), dtype=np.float32)
         _scheck(lib().gals_surrogate_forward(self._h, _fp(X), X.shape[0], _fp(Y)), self._h)
         return Y
+
+    def forward_device(self, inputs_ptr: int, n: int, outputs_ptr: int):
+        """Device-memory forward pass (n x 3 floats in, n x 6 out), enqueued on the
+        surrogate's stream; the pointers are raw device addresses (e.g. tensor.data_ptr())."""
+        _scheck(lib().gals_surrogate_forward_device(self._h, ctypes.c_void_p(inputs_ptr), int(n),
+                                                    ctypes.c_void_p(outputs_ptr)), self._h)
 
     def gradient(self, inputs, targets):
         X = np.ascontiguousarray(inputs, dtype=np.float32).reshape(-1, 3)

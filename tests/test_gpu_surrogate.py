@@ -61,6 +61,23 @@ def test_forward_matches_oracle(G):
     assert err <= 2e-2, err  # BF16 operands, hardware tanh in SiLU
 
 
+def test_forward_device_matches_host_forward(G):
+    """The device-pointer entry runs the same kernel: bit-identical outputs, including a
+    ragged last tile."""
+    import torch
+    S = G.Surrogate(seed=11)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (1000, 3)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.full((1000, 6), float("nan"), device="cuda")
+    torch.cuda.synchronize()
+    S.forward_device(Xd.data_ptr(), 1000, Yd.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(Yd.cpu().numpy(), S.forward(X))
+    with pytest.raises(G.GalsError):
+        S.forward_device(Xd.data_ptr(), 0, Yd.data_ptr())
+
+
 def test_gradient_matches_oracle(G):
     """Backward kernels (BF16 operands, FP32 accumulation) against the FP64 chain rule,
     tensor by tensor, relative to each tensor's norm."""
