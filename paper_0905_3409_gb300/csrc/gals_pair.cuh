@@ -1,12 +1,13 @@
-// gals_pair.cuh -- the 2D node update for two nodes at once in paired FP32 arithmetic.
+// gals_pair.cuh -- the node update for two nodes at once in paired FP32 arithmetic.
 //
 // Blackwell executes fma/add/mul on float2 operands as one instruction (FFMA2 and
 // friends, __ffma2_rn & co.), so a thread that advances two nodes of the same column
-// (rows j and j+1) issues about half the floating-point instructions of two scalar
-// updates, and has twice the independent loads in flight.  Lane x of every float2 is
-// node (i, j), lane y node (i, j+1).  The arithmetic is the one of gals_device.cuh:
-// superconsistent RK3 trace with Jacobian (Sec. 5.1), cell location, bicubic Hermite
-// value and gradient from the nearest-corner-shifted data (Sec. 2.3), J^T grad H.
+// (2D: rows j and j+1; 3D: z-levels k and k+1) issues about half the floating-point
+// instructions of two scalar updates, and has twice the independent loads in flight.
+// Lane x of every float2 is the first node, lane y the second.  The arithmetic is the one
+// of gals_device.cuh: superconsistent RK3 trace with Jacobian (Sec. 5.1), cell location,
+// bi-/tricubic Hermite value and gradient from the nearest-corner-shifted data (Sec. 2.3),
+// J^T grad H.
 // Each lane rounds exactly like a scalar FMA/ADD/MUL chain of the same expression.
 #pragma once
 
@@ -198,6 +199,155 @@ __device__ __forceinline__ void hermite2d_pair(const F2 c[4][4], const Basis2 &b
     H = add2(base, hval2(by, P0, P1, Q0, Q1));
     Hy = hder2(by, P0, P1, Q0, Q1);
     Hx = hval2(by, Pd0, Pd1, Qd0, Qd1);
+}
+
+// ---------------------------------------------------------------- 3D, two nodes per thread
+
+struct V3p { F2 v[3]; F2 d[9]; };
+
+// v and Dv (Dv[3i+j] = dv_i/dx_j) at two points; DEFORM3D is LeVeque's field
+// u = 2 sin^2(pi x) sin(2 pi y) sin(2 pi z) c, v = -sin(2 pi x) sin^2(pi y) sin(2 pi z) c,
+// w = -sin(2 pi x) sin(2 pi y) sin^2(pi z) c with c = cos(pi t / T).
+template <int VK>
+__device__ __forceinline__ V3p vel3d_pair(const VelParams &vp, const StageCoef &sc, int stage,
+                                          F2 x, F2 y, F2 z)
+{
+    V3p r;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) r.d[a] = bc(0.f);
+    if (VK == VK_CONST) {
+        r.v[0] = bc(vp.c0); r.v[1] = bc(vp.c1); r.v[2] = bc(vp.c2);
+    } else if (VK == VK_ROTATION) {
+        r.v[0] = mul2(bc(-vp.omega), sub2(y, bc(vp.cy)));
+        r.v[1] = mul2(bc(vp.omega), sub2(x, bc(vp.cx)));
+        r.v[2] = bc(0.f);
+        r.d[1] = bc(-vp.omega); r.d[3] = bc(vp.omega);
+    } else {  // VK_DEFORM3D
+        F2 sx, cx, sy, cy, sz, cz;
+        sincospi2(x, sx, cx);
+        sincospi2(y, sy, cy);
+        sincospi2(z, sz, cz);
+        const float c = sc.mod[stage], cp = c * kPi;
+        const F2 two = bc(2.f), one = bc(1.f), mtwo = bc(-2.f);
+        const F2 s2x = mul2(two, mul2(sx, cx)), s2y = mul2(two, mul2(sy, cy)), s2z = mul2(two, mul2(sz, cz));
+        const F2 sx2 = mul2(sx, sx), sy2 = mul2(sy, sy), sz2 = mul2(sz, sz);
+        const F2 c2x = fma2(mtwo, sx2, one), c2y = fma2(mtwo, sy2, one), c2z = fma2(mtwo, sz2, one);
+        const F2 sxy = mul2(s2x, s2y), sss = mul2(sxy, s2z);
+        r.v[0] = mul2(bc(2.f * c), mul2(sx2, mul2(s2y, s2z)));
+        r.v[1] = mul2(bc(-c), mul2(mul2(s2x, sy2), s2z));
+        r.v[2] = mul2(bc(-c), mul2(sxy, sz2));
+        r.d[0] = mul2(bc(2.f * cp), sss);
+        r.d[1] = mul2(bc(4.f * cp), mul2(sx2, mul2(c2y, s2z)));
+        r.d[2] = mul2(bc(4.f * cp), mul2(sx2, mul2(s2y, c2z)));
+        r.d[3] = mul2(bc(-2.f * cp), mul2(c2x, mul2(sy2, s2z)));
+        r.d[4] = mul2(bc(-cp), sss);
+        r.d[5] = mul2(bc(-2.f * cp), mul2(s2x, mul2(sy2, c2z)));
+        r.d[6] = mul2(bc(-2.f * cp), mul2(c2x, mul2(s2y, sz2)));
+        r.d[7] = mul2(bc(-2.f * cp), mul2(s2x, mul2(c2y, sz2)));
+        r.d[8] = r.d[4];
+    }
+    return r;
+}
+
+__device__ __forceinline__ void matmul3_pair(const F2 *A, const F2 *B, F2 *C)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            C[3 * i + j] = fma2(A[3 * i], B[j], fma2(A[3 * i + 1], B[3 + j], mul2(A[3 * i + 2], B[6 + j])));
+}
+
+// Superconsistent RK3 trace of Sec. 5.1 for two nodes (a = v(x, t+dt) from the caller):
+// d = foot - x and J[3i+j] = d foot_i / d x_j.
+template <int TR, int VK>
+__device__ __forceinline__ void trace3d_pair(const V3p &a, const VelParams &vp, const StageCoef &sc,
+                                             F2 x, F2 y, F2 z, float dt, F2 d[3], F2 J[9])
+{
+    const F2 mdt = bc(-dt), one = bc(1.f);
+    if (TR == TR_EULER) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d[i] = mul2(mdt, a.v[i]);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) J[e] = (e % 4) == 0 ? fma2(mdt, a.d[e], one) : mul2(mdt, a.d[e]);
+        return;
+    }
+    F2 J1[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) J1[e] = (e % 4) == 0 ? fma2(mdt, a.d[e], one) : mul2(mdt, a.d[e]);
+    const V3p b = vel3d_pair<VK>(vp, sc, 1, fma2(mdt, a.v[0], x), fma2(mdt, a.v[1], y),
+                                 fma2(mdt, a.v[2], z));
+    F2 M[9];
+    matmul3_pair(b.d, J1, M);
+    const F2 mq = bc(-0.25f * dt);
+    F2 J2[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        J2[e] = (e % 4) == 0 ? fma2(mq, add2(a.d[e], M[e]), one) : mul2(mq, add2(a.d[e], M[e]));
+    F2 s1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s1[i] = add2(a.v[i], b.v[i]);
+    const V3p c = vel3d_pair<VK>(vp, sc, 2, fma2(mq, s1[0], x), fma2(mq, s1[1], y), fma2(mq, s1[2], z));
+    F2 N[9];
+    matmul3_pair(c.d, J2, N);
+    // w3 + (w1 + w2 - 2 w3)/6: exact for constant v
+    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = mul2(mdt, fma2(fma2(m2, c.v[i], s1[i]), i6, c.v[i]));
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        const F2 w = fma2(fma2(m2, N[e], add2(a.d[e], M[e])), i6, N[e]);
+        J[e] = (e % 4) == 0 ? fma2(mdt, w, one) : mul2(mdt, w);
+    }
+}
+
+// Tricubic Hermite value and gradient for two feet, streamed over the four x-lines of
+// the cell (B = y corner, C = z corner).  row(B, C, lo, hi) must fill lo[a], hi[a] with
+// plane a (0 phi, 1 x, 2 y, 3 z, 4 xy, 5 xz, 6 yz, 7 xyz) at the line's x = k and x = k+1
+// corners, for both lanes; base is phi at each foot's nearest corner.  The reduction
+// order is x, then y, then z, as in the sum-factorised form of Sec. 2.3.
+struct XRed2 { F2 P, Pd, Qy, Qyd, Qz, Qzd, Qyz, Qyzd; };
+
+__device__ __forceinline__ XRed2 xreduce2(const Basis2 &bx, const F2 lo[8], const F2 hi[8], F2 base)
+{
+    XRed2 r;
+    const F2 p0 = sub2(lo[0], base), p1 = sub2(hi[0], base);
+    r.P = hval2(bx, p0, p1, lo[1], hi[1]);
+    r.Pd = hder2(bx, p0, p1, lo[1], hi[1]);
+    r.Qy = hval2(bx, lo[2], hi[2], lo[4], hi[4]);
+    r.Qyd = hder2(bx, lo[2], hi[2], lo[4], hi[4]);
+    r.Qz = hval2(bx, lo[3], hi[3], lo[5], hi[5]);
+    r.Qzd = hder2(bx, lo[3], hi[3], lo[5], hi[5]);
+    r.Qyz = hval2(bx, lo[6], hi[6], lo[7], hi[7]);
+    r.Qyzd = hder2(bx, lo[6], hi[6], lo[7], hi[7]);
+    return r;
+}
+
+template <class Row>
+__device__ __forceinline__ void hermite3d_pair(const Basis2 &bx, const Basis2 &by, const Basis2 &bz,
+                                               F2 base, Row row, F2 &H, F2 g[3])
+{
+    F2 R[2], Rx[2], Ry[2], Rz[2], Rzx[2], Rzy[2];
+#pragma unroll
+    for (int C = 0; C < 2; ++C) {
+        XRed2 q[2];
+#pragma unroll
+        for (int B = 0; B < 2; ++B) {
+            F2 lo[8], hi[8];
+            row(B, C, lo, hi);
+            q[B] = xreduce2(bx, lo, hi, base);
+        }
+        R[C] = hval2(by, q[0].P, q[1].P, q[0].Qy, q[1].Qy);
+        Ry[C] = hder2(by, q[0].P, q[1].P, q[0].Qy, q[1].Qy);
+        Rx[C] = hval2(by, q[0].Pd, q[1].Pd, q[0].Qyd, q[1].Qyd);
+        Rz[C] = hval2(by, q[0].Qz, q[1].Qz, q[0].Qyz, q[1].Qyz);
+        Rzy[C] = hder2(by, q[0].Qz, q[1].Qz, q[0].Qyz, q[1].Qyz);
+        Rzx[C] = hval2(by, q[0].Qzd, q[1].Qzd, q[0].Qyzd, q[1].Qyzd);
+    }
+    H = add2(base, hval2(bz, R[0], R[1], Rz[0], Rz[1]));
+    g[2] = hder2(bz, R[0], R[1], Rz[0], Rz[1]);
+    g[0] = hval2(bz, Rx[0], Rx[1], Rzx[0], Rzx[1]);
+    g[1] = hval2(bz, Ry[0], Ry[1], Rzy[0], Rzy[1]);
 }
 
 }  // namespace gals

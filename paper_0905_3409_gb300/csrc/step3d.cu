@@ -1,12 +1,14 @@
 // step3d.cu -- the 3D GALS step kernel and the 3D mixed-derivative reconstruction.
 //
-// One thread per grid node: trace back with the 3x3 Jacobian (Sec. 5.1, Ex.
-// superconsistent Shu-Osher) -> locate the foot cell -> gather 8 corners x 8 data ->
-// tricubic Hermite value and gradient (Sec. 2.3) -> phi+ = H, psi+ = J^T grad H.
+// One thread per two grid nodes of a z-column, in paired FP32 (FFMA2): trace back with the
+// 3x3 Jacobian (Sec. 5.1, superconsistent Shu-Osher RK3) -> locate the foot cell -> stream
+// the cell's 4 x-lines (2 corners x 8 data) from the TMA-staged tile -> tricubic Hermite
+// value and gradient (Sec. 2.3) -> phi+ = H, psi+ = J^T grad H.
 // Mixed derivatives (Sec. 2.3, approach A): phi_xy = Dx psi_y, phi_xz = Dx psi_z,
 // phi_yz = Dy psi_z, phi_xyz = Dx Dy psi_z, read from their planes (FULL) or rebuilt
 // from psi windows around the cell (COMPACT) with the same stencils.
 #include "gals_internal.h"
+#include "gals_pair.cuh"
 #include "tma.cuh"
 
 namespace gals {
@@ -36,44 +38,123 @@ template <int CR> struct Tile3 {
     static constexpr int BYTES = NP * PS * 4;
 };
 
-// Separable factors of the deformation field on a grid line.
-struct Sep { float s2, s2x, c2x; };
-__device__ __forceinline__ Sep sep3(float s)
-{
-    float sn, cs;
-    sincospi_f(s, &sn, &cs);
-    return Sep{sn * sn, 2.f * sn * cs, 1.f - 2.f * sn * sn};
-}
+// v(x, t+dt) and Dv at the two nodes (x, y, z0) and (x, y, z1) of a thread.  For
+// DEFORM3D the x- and y-factors of every term are products fixed per thread (Pre3),
+// so only the z-factors are evaluated per node.
+struct Pre3 { float v0, v1, v2, sxy, d1, d2, d3, d5, d6, d7; };
 
-// v(x, t+dt) at a node; DEFORM3D from per-axis factors
 template <int VK>
-__device__ __forceinline__ V3 stage1_3d(const VelParams &vp, const StageCoef &sc, float x,
-                                        float y, float z, const Sep &fx, const Sep &fy,
-                                        const Sep &fz)
+__device__ __forceinline__ Pre3 pre3(const StageCoef &sc, float x, float y)
 {
+    Pre3 p{};
     if (VK == VK_DEFORM3D) {
-        V3 r;
+        float sx, cx, sy, cy;
+        sincospi_f(x, &sx, &cx);
+        sincospi_f(y, &sy, &cy);
         const float c = sc.mod[0], cp = c * kPi;
-        const float sss = fx.s2x * fy.s2x * fz.s2x;
-        r.v[0] = 2.f * c * fx.s2 * fy.s2x * fz.s2x;
-        r.v[1] = -c * fx.s2x * fy.s2 * fz.s2x;
-        r.v[2] = -c * fx.s2x * fy.s2x * fz.s2;
-        r.d[0] = 2.f * cp * sss;
-        r.d[1] = 4.f * cp * fx.s2 * fy.c2x * fz.s2x;
-        r.d[2] = 4.f * cp * fx.s2 * fy.s2x * fz.c2x;
-        r.d[3] = -2.f * cp * fx.c2x * fy.s2 * fz.s2x;
-        r.d[4] = -cp * sss;
-        r.d[5] = -2.f * cp * fx.s2x * fy.s2 * fz.c2x;
-        r.d[6] = -2.f * cp * fx.c2x * fy.s2x * fz.s2;
-        r.d[7] = -2.f * cp * fx.s2x * fy.c2x * fz.s2;
-        r.d[8] = r.d[4];
-        return r;
+        const float s2x = 2.f * sx * cx, s2y = 2.f * sy * cy;
+        const float sx2 = sx * sx, sy2 = sy * sy;
+        const float c2x = 1.f - 2.f * sx2, c2y = 1.f - 2.f * sy2;
+        p.v0 = 2.f * c * sx2 * s2y;
+        p.v1 = -c * s2x * sy2;
+        p.v2 = -c * s2x * s2y;
+        p.sxy = cp * s2x * s2y;
+        p.d1 = 4.f * cp * sx2 * c2y;
+        p.d2 = 4.f * cp * sx2 * s2y;
+        p.d3 = -2.f * cp * c2x * sy2;
+        p.d5 = -2.f * cp * s2x * sy2;
+        p.d6 = -2.f * cp * c2x * s2y;
+        p.d7 = -2.f * cp * s2x * c2y;
     }
-    return vel3d<VK>(vp, sc, 0, x, y, z);
+    return p;
 }
 
+template <int VK>
+__device__ __forceinline__ V3p stage1_pair(const VelParams &vp, const StageCoef &sc, const Pre3 &p,
+                                           F2 x, F2 y, F2 z)
+{
+    if (VK != VK_DEFORM3D) return vel3d_pair<VK>(vp, sc, 0, x, y, z);
+    F2 sz, cz;
+    sincospi2(z, sz, cz);
+    const F2 s2z = mul2(bc(2.f), mul2(sz, cz)), sz2 = mul2(sz, sz);
+    const F2 c2z = fma2(bc(-2.f), sz2, bc(1.f));
+    V3p r;
+    const F2 sss = mul2(bc(p.sxy), s2z);
+    r.v[0] = mul2(bc(p.v0), s2z);
+    r.v[1] = mul2(bc(p.v1), s2z);
+    r.v[2] = mul2(bc(p.v2), sz2);
+    r.d[0] = mul2(bc(2.f), sss);
+    r.d[1] = mul2(bc(p.d1), s2z);
+    r.d[2] = mul2(bc(p.d2), c2z);
+    r.d[3] = mul2(bc(p.d3), s2z);
+    r.d[4] = neg2(sss);
+    r.d[5] = mul2(bc(p.d5), c2z);
+    r.d[6] = mul2(bc(p.d6), sz2);
+    r.d[7] = mul2(bc(p.d7), sz2);
+    r.d[8] = r.d[4];
+    return r;
+}
+
+// One x-line (y corner B, z corner C) of a foot cell with base corner (k, l, m): the data
+// of planes 0..7 at x = k (lo) and x = k+1 (hi).  ld(a, z, y, x) reads plane a at a grid
+// index.  With CROSS_RECON the mixed derivatives come from psi_y, psi_z windows with the
+// approach-A stencils (central, one-sided at the ends), as in the reconstruction kernels.
+template <int CR, class Ld>
+__device__ __forceinline__ void cell_line(const Ld &ld, const Geom &g, int k, int l, int m, int B,
+                                          int C, float lo[8], float hi[8])
+{
+    const int zz = m + C, yy = l + B;
+    if (CR == CROSS_PLANE) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            lo[a] = ld(a, zz, yy, k);
+            hi[a] = ld(a, zz, yy, k + 1);
+        }
+        return;
+    }
+    const int xs[4] = {max(k - 1, 0), k, k + 1, min(k + 2, g.n0 - 1)};
+    const int ys[4] = {max(l - 1, 0), l, l + 1, min(l + 2, g.n1 - 1)};
+    lo[0] = ld(0, zz, yy, k);
+    hi[0] = ld(0, zz, yy, k + 1);
+    lo[1] = ld(1, zz, yy, k);
+    hi[1] = ld(1, zz, yy, k + 1);
+    float wy[4], wz[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) wy[p] = ld(2, zz, yy, xs[p]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) wz[q][p] = ld(3, zz, ys[q], xs[p]);
+    // Dy psi_z on row yy at every x-window position
+    float dyw[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float col[4] = {wz[0][p], wz[1][p], wz[2][p], wz[3][p]};
+        dyw[p] = B == 0 ? dwin<0>(col, l, g.n1, g.i2h1) : dwin<1>(col, l + 1, g.n1, g.i2h1);
+    }
+    const float zrow[4] = {wz[B + 1][0], wz[B + 1][1], wz[B + 1][2], wz[B + 1][3]};
+    lo[2] = wy[1];
+    hi[2] = wy[2];
+    lo[3] = zrow[1];
+    hi[3] = zrow[2];
+    lo[4] = dwin<0>(wy, k, g.n0, g.i2h0);
+    hi[4] = dwin<1>(wy, k + 1, g.n0, g.i2h0);
+    lo[5] = dwin<0>(zrow, k, g.n0, g.i2h0);
+    hi[5] = dwin<1>(zrow, k + 1, g.n0, g.i2h0);
+    lo[6] = dyw[1];
+    hi[6] = dyw[2];
+    lo[7] = dwin<0>(dyw, k, g.n0, g.i2h0);
+    hi[7] = dwin<1>(dyw, k + 1, g.n0, g.i2h0);
+}
+
+// Two nodes per thread, (i, j, kz) and (i, j, kz+1), in paired FP32: trace with the 3x3
+// Jacobian, cell location, tricubic Hermite value and gradient from the staged tile,
+// phi+ = H and psi+ = J^T grad H.  Feet whose cell data lie outside the staged tile
+// (large CFL) read global memory instead.
+// FULL layout: at most 128 registers (4 blocks per SM; a few words spill), measured faster
+// than 166 registers at 3 blocks per SM.
 template <int TR, int VK, int CR>
-__global__ void __launch_bounds__(TX *TY)
+__global__ void __launch_bounds__(TX *TY, CR == CROSS_PLANE ? 4 : 1)
 k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParams vp,
          const StageCoef *__restrict__ coef, float dt, const __grid_constant__ CUtensorMap tmap,
          int *__restrict__ err)
@@ -90,184 +171,142 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
         tma_load_4d(tile, &tmap, x0 - HX, y0 - T::HY, z0 - HZ, 0, &bar);
     }
     const StageCoef &sc = *coef;
-    const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+    // threads past a ragged edge trace a clamped node and store nothing
+    const bool valid = x0 + (int)threadIdx.x < g.n0 && y0 + (int)threadIdx.y < g.n1;
+    const int i = min(x0 + (int)threadIdx.x, g.n0 - 1), j = min(y0 + (int)threadIdx.y, g.n1 - 1);
     const float x = g.lo0 + (float)i * g.h0;
     const float y = g.lo1 + (float)j * g.h1;
-    const Sep fx = VK == VK_DEFORM3D ? sep3(x) : Sep{0.f, 0.f, 0.f};
-    const Sep fy = VK == VK_DEFORM3D ? sep3(y) : Sep{0.f, 0.f, 0.f};
-
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-            atomicExch(err, kErrTmaTimeout);
-            mbar_wait_bounded(&bar, 0);
-        }
-        return;
-    }
-    if (i >= g.n0 || j >= g.n1) return;
+    const Pre3 pre = pre3<VK>(sc, x, y);
     const int64_t P = g.plane;
+    const int64_t zstride = (int64_t)g.n1 * g.pitch;
     const int zend = min(z0 + TZ, g.n2);
-    for (int kz = z0; kz < zend; ++kz) {
-        const float z = g.lo2 + (float)kz * g.h2;
-        const Sep fz = VK == VK_DEFORM3D ? sep3(z) : Sep{0.f, 0.f, 0.f};
-        float d[3], J[9];
-        trace3d_from<TR, VK>(stage1_3d<VK>(vp, sc, x, y, z, fx, fy, fz), vp, sc, x, y, z, dt, d, J);
-
-        int k, l, m;
-        float xi, eta, zeta;
-        locate(i, d[0] * g.ih0, g.n0, k, xi);
-        locate(j, d[1] * g.ih1, g.n1, l, eta);
-        locate(kz, d[2] * g.ih2, g.n2, m, zeta);
-
-        // staged-tile coordinates of the cell's base corner
-        const int tx = k - x0 + HX, ty = l - y0 + T::HY, tz = m - z0 + HZ;
-        const bool inside = CR == CROSS_PLANE
-            ? (tx >= 0 && tx <= T::W - 2 && ty >= 0 && ty <= T::H - 2 && tz >= 0 && tz <= T::D - 2)
-            : (tx >= 1 && tx <= T::W - 3 && ty >= 1 && ty <= T::H - 3 && tz >= 0 && tz <= T::D - 2);
-        // element (plane a, corner offsets dz, dy, dx relative to the cell base)
-        auto sm = [&](int a, int dz, int dy, int dx) {
-            return tile[a * T::PS + ((tz + dz) * T::H + ty + dy) * T::W + tx + dx];
-        };
-        auto gm = [&](int a, int zz, int yy, int xx) {
-            return __ldg(in + a * P + ((int64_t)zz * g.n1 + yy) * g.pitch + xx);
-        };
-        float c[8][8];
-        if (CR == CROSS_PLANE) {
-            if (inside) {
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-#pragma unroll
-                    for (int a = 0; a < 8; ++a) c[v][a] = sm(a, v >> 2, (v >> 1) & 1, v & 1);
-            } else {
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-#pragma unroll
-                    for (int a = 0; a < 8; ++a)
-                        c[v][a] = gm(a, m + (v >> 2), l + ((v >> 1) & 1), k + (v & 1));
-            }
-        } else {
-            // psi_y on the x-window [k-1, k+2] of the 4 corner lines; psi_z on the
-            // x-window [k-1, k+2] x y-window [l-1, l+2] of both corner z-planes
-            const int xs[4] = {max(k - 1, 0), k, k + 1, min(k + 2, g.n0 - 1)};
-            const int ys[4] = {max(l - 1, 0), l, l + 1, min(l + 2, g.n1 - 1)};
-            float wy[2][2][4], wz[2][4][4];
-#pragma unroll
-            for (int C = 0; C < 2; ++C) {
-#pragma unroll
-                for (int B = 0; B < 2; ++B) {
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        wy[C][B][p] = inside ? sm(2, C, B, p - 1) : gm(2, m + C, l + B, xs[p]);
-#pragma unroll
-                    for (int A = 0; A < 2; ++A) {
-                        const int v = A + 2 * B + 4 * C;
-                        c[v][0] = inside ? sm(0, C, B, A) : gm(0, m + C, l + B, k + A);
-                        c[v][1] = inside ? sm(1, C, B, A) : gm(1, m + C, l + B, k + A);
-                        c[v][2] = wy[C][B][1 + A];
-                    }
+    const F2 X = bc(x), Y = bc(y);
+    for (int kz = z0; kz < zend; kz += 2) {
+        const bool two = kz + 1 < zend;
+        const int kz1 = two ? kz + 1 : kz;
+        const F2 Z = make_float2(g.lo2 + (float)kz * g.h2, g.lo2 + (float)kz1 * g.h2);
+        F2 d[3], J[9];
+        if (kz == z0) {
+            const bool ok = mbar_wait_bounded(&bar, 0);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicExch(err, kErrTmaTimeout);
+                    mbar_wait_bounded(&bar, 0);
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p)
-                        wz[C][q][p] = inside ? sm(3, C, q - 1, p - 1) : gm(3, m + C, ys[q], xs[p]);
-            }
-#pragma unroll
-            for (int C = 0; C < 2; ++C) {
-#pragma unroll
-                for (int B = 0; B < 2; ++B) {
-                    // Dy psi_z at every x-window position for row l+B
-                    float dyw[4];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        float col[4] = {wz[C][0][p], wz[C][1][p], wz[C][2][p], wz[C][3][p]};
-                        dyw[p] = (B == 0) ? dwin<0>(col, l, g.n1, g.i2h1) : dwin<1>(col, l + 1, g.n1, g.i2h1);
-                    }
-                    float zrow[4] = {wz[C][B + 1][0], wz[C][B + 1][1], wz[C][B + 1][2], wz[C][B + 1][3]};
-#pragma unroll
-                    for (int A = 0; A < 2; ++A) {
-                        const int v = A + 2 * B + 4 * C;
-                        c[v][3] = zrow[1 + A];
-                        if (A == 0) {
-                            c[v][4] = dwin<0>(wy[C][B], k, g.n0, g.i2h0);
-                            c[v][5] = dwin<0>(zrow, k, g.n0, g.i2h0);
-                            c[v][7] = dwin<0>(dyw, k, g.n0, g.i2h0);
-                        } else {
-                            c[v][4] = dwin<1>(wy[C][B], k + 1, g.n0, g.i2h0);
-                            c[v][5] = dwin<1>(zrow, k + 1, g.n0, g.i2h0);
-                            c[v][7] = dwin<1>(dyw, k + 1, g.n0, g.i2h0);
-                        }
-                        c[v][6] = dyw[1 + A];
-                    }
-                }
+                return;
             }
         }
+        trace3d_pair<TR, VK>(stage1_pair<VK>(vp, sc, pre, X, Y, Z), vp, sc, X, Y, Z, dt, d, J);
 
-        const Basis1 bx = basis1(xi, g.h0, g.ih0);
-        const Basis1 by = basis1(eta, g.h1, g.ih1);
-        const Basis1 bz = basis1(zeta, g.h2, g.ih2);
-        float H, gr[3];
-        hermite3d(c, bx, by, bz, H, gr);
+        int k0, l0, m0, k1, l1, m1;
+        float xi0, eta0, zeta0, xi1, eta1, zeta1;
+        locate(i, d[0].x * g.ih0, g.n0, k0, xi0);
+        locate(j, d[1].x * g.ih1, g.n1, l0, eta0);
+        locate(kz, d[2].x * g.ih2, g.n2, m0, zeta0);
+        locate(i, d[0].y * g.ih0, g.n0, k1, xi1);
+        locate(j, d[1].y * g.ih1, g.n1, l1, eta1);
+        locate(kz1, d[2].y * g.ih2, g.n2, m1, zeta1);
+        const Basis2 bx = basis_pair(make_float2(xi0, xi1), g.h0, g.ih0);
+        const Basis2 by = basis_pair(make_float2(eta0, eta1), g.h1, g.ih1);
+        const Basis2 bz = basis_pair(make_float2(zeta0, zeta1), g.h2, g.ih2);
 
-        const int64_t o = ((int64_t)kz * g.n1 + j) * g.pitch + i;
-        out[o] = H;
+        // a cell is served from the tile if every value its line reads is staged
+        auto in_tile = [&](int k, int l, int m) {
+            const int tx = k - x0 + HX, ty = l - y0 + T::HY, tz = m - z0 + HZ;
+            return CR == CROSS_PLANE
+                ? (tx >= 0 && tx <= T::W - 2 && ty >= 0 && ty <= T::H - 2 && tz >= 0 && tz <= T::D - 2)
+                : (tx >= 1 && tx <= T::W - 3 && ty >= 1 && ty <= T::H - 3 && tz >= 0 && tz <= T::D - 2);
+        };
+        auto lds = [&](int a, int zz, int yy, int xx) {
+            return tile[a * T::PS + ((zz - z0 + HZ) * T::H + yy - y0 + T::HY) * T::W + xx - x0 + HX];
+        };
+        auto ldg = [&](int a, int zz, int yy, int xx) {
+            return __ldg(in + a * P + (int64_t)zz * zstride + (int64_t)yy * g.pitch + xx);
+        };
+        const bool in0 = in_tile(k0, l0, m0), in1 = in_tile(k1, l1, m1);
+        // phi at each foot's nearest corner
+        const int nk0 = k0 + (bx.n0 ? 1 : 0), nl0 = l0 + (by.n0 ? 1 : 0), nm0 = m0 + (bz.n0 ? 1 : 0);
+        const int nk1 = k1 + (bx.n1 ? 1 : 0), nl1 = l1 + (by.n1 ? 1 : 0), nm1 = m1 + (bz.n1 ? 1 : 0);
+        F2 H, gr[3];
+        if (in0 && in1) {
+            const F2 base = make_float2(lds(0, nm0, nl0, nk0), lds(0, nm1, nl1, nk1));
+            hermite3d_pair(bx, by, bz, base, [&](int B, int C, F2 lo[8], F2 hi[8]) {
+                float a0[8], b0[8], a1[8], b1[8];
+                cell_line<CR>(lds, g, k0, l0, m0, B, C, a0, b0);
+                cell_line<CR>(lds, g, k1, l1, m1, B, C, a1, b1);
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    lo[a] = make_float2(a0[a], a1[a]);
+                    hi[a] = make_float2(b0[a], b1[a]);
+                }
+            }, H, gr);
+        } else {
+            auto ld0 = [&](int a, int zz, int yy, int xx) { return in0 ? lds(a, zz, yy, xx) : ldg(a, zz, yy, xx); };
+            auto ld1 = [&](int a, int zz, int yy, int xx) { return in1 ? lds(a, zz, yy, xx) : ldg(a, zz, yy, xx); };
+            const F2 base = make_float2(ld0(0, nm0, nl0, nk0), ld1(0, nm1, nl1, nk1));
+            hermite3d_pair(bx, by, bz, base, [&](int B, int C, F2 lo[8], F2 hi[8]) {
+                float a0[8], b0[8], a1[8], b1[8];
+                cell_line<CR>(ld0, g, k0, l0, m0, B, C, a0, b0);
+                cell_line<CR>(ld1, g, k1, l1, m1, B, C, a1, b1);
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    lo[a] = make_float2(a0[a], a1[a]);
+                    hi[a] = make_float2(b0[a], b1[a]);
+                }
+            }, H, gr);
+        }
+        F2 psi[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)  // (J^T grad H)_a = sum_b J[b][a] dH/dx_b
-            out[(a + 1) * P + o] = fmaf(J[a], gr[0], fmaf(J[3 + a], gr[1], J[6 + a] * gr[2]));
+            psi[a] = fma2(J[a], gr[0], fma2(J[3 + a], gr[1], mul2(J[6 + a], gr[2])));
+        if (!valid) continue;
+        const int64_t o = (int64_t)kz * zstride + (int64_t)j * g.pitch + i;
+        out[o] = H.x;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[(a + 1) * P + o] = psi[a].x;
+        if (two) {
+            out[o + zstride] = H.y;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out[(a + 1) * P + o + zstride] = psi[a].y;
+        }
     }
 }
 
 // Mixed derivatives at every node from psi_y, psi_z (approach A, one-sided ends):
 // phi_xy = Dx psi_y, phi_xz = Dx psi_z, phi_yz = Dy psi_z, phi_xyz = Dx (Dy psi_z).
-// A block of 32 x 8 threads walks RZ slices of a 32 x 8 xy-tile; each slice's psi_y,
-// psi_z (x-halo 2, y-halo 2 for the one-sided ends) and the y-differences of psi_z are
-// staged in shared memory, so every input is read once with coalesced loads.  The
-// stencil functions are the ones the step kernels use, so the results are identical.
-constexpr int RX = 32, RY = 8, RZ = 8, RW = RX + 4;
+// One thread per (x, y) column walks RZ z-slices; every stencil operand is a direct
+// read-only load (neighbours' reads hit L1), with no barriers, so all loads of a slice are
+// in flight together.  The stencil functions are the ones the step kernels use, so the
+// results are identical.
+constexpr int RX = 32, RY = 8, RZ = 4;
 
-__global__ void __launch_bounds__(RX *RY) k_recon3d(float *__restrict__ buf, Geom g)
+__global__ void __launch_bounds__(RX *RY) k_recon3d(const float *__restrict__ py,
+                                                     const float *__restrict__ pz,
+                                                     float *__restrict__ cross, Geom g)
 {
-    __shared__ float spy[RY][RW];
-    __shared__ float spz[RY + 4][RW];
-    __shared__ float sdy[RY][RW];
-    const int x0 = blockIdx.x * RX, y0 = blockIdx.y * RY, z0 = blockIdx.z * RZ;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + RX * ty;
+    const int i = blockIdx.x * RX + threadIdx.x, j = blockIdx.y * RY + threadIdx.y;
+    if (i >= g.n0 || j >= g.n1) return;
     const int64_t P = g.plane;
-    const float *py = buf + 2 * P, *pz = buf + 3 * P;
-    const int i = x0 + tx, j = y0 + ty;
-    const int zend = min(z0 + RZ, g.n2);
-    for (int kz = z0; kz < zend; ++kz) {
-        const int64_t zoff = (int64_t)kz * g.n1;
-        // stage psi_y (rows y0..y0+7) and psi_z (rows y0-2..y0+9), columns x0-2..x0+33
-        for (int e = tid; e < (RY + (RY + 4)) * RW; e += RX * RY) {
-            const bool isz = e >= RY * RW;
-            const int ee = isz ? e - RY * RW : e;
-            const int r = ee / RW, c = ee % RW;
-            const int gx = x0 - 2 + c, gy = (isz ? y0 - 2 : y0) + r;
-            float v = 0.f;
-            if (gx >= 0 && gx < g.n0 && gy >= 0 && gy < g.n1)
-                v = (isz ? pz : py)[(zoff + gy) * g.pitch + gx];
-            if (isz) spz[r][c] = v; else spy[r][c] = v;
-        }
-        __syncthreads();
-        // Dy psi_z on rows y0..y0+7 for every staged column
-        for (int e = tid; e < RY * RW; e += RX * RY) {
-            const int r = e / RW, c = e % RW;
-            const int gy = y0 + r, gx = x0 - 2 + c;
-            float v = 0.f;
-            if (gy < g.n1 && gx >= 0 && gx < g.n0)
-                v = dline(gy, g.n1, g.i2h1, [&](int q) { return spz[q - y0 + 2][c]; });
-            sdy[r][c] = v;
-        }
-        __syncthreads();
-        if (i < g.n0 && j < g.n1) {
-            const int64_t o = (zoff + j) * g.pitch + i;
-            buf[4 * P + o] = dline(i, g.n0, g.i2h0, [&](int q) { return spy[ty][q - x0 + 2]; });
-            buf[5 * P + o] = dline(i, g.n0, g.i2h0, [&](int q) { return spz[ty + 2][q - x0 + 2]; });
-            buf[6 * P + o] = sdy[ty][tx + 2];
-            buf[7 * P + o] = dline(i, g.n0, g.i2h0, [&](int q) { return sdy[ty][q - x0 + 2]; });
-        }
-        __syncthreads();
+    const int z0 = blockIdx.z * RZ, zend = min(z0 + RZ, g.n2);
+#pragma unroll
+    for (int dz = 0; dz < RZ; ++dz) {
+        const int kz = z0 + dz;
+        if (kz >= zend) break;
+        const int64_t row = ((int64_t)kz * g.n1) * g.pitch;
+        const float *ly = py + row, *lz = pz + row;
+        auto Y = [&](int xx, int yy) { return __ldg(ly + (int64_t)yy * g.pitch + xx); };
+        auto Z = [&](int xx, int yy) { return __ldg(lz + (int64_t)yy * g.pitch + xx); };
+        const float fxy = dline(i, g.n0, g.i2h0, [&](int q) { return Y(q, j); });
+        const float fxz = dline(i, g.n0, g.i2h0, [&](int q) { return Z(q, j); });
+        const float fyz = dline(j, g.n1, g.i2h1, [&](int r) { return Z(i, r); });
+        const float fxyz = dline(i, g.n0, g.i2h0, [&](int q) {
+            return dline(j, g.n1, g.i2h1, [&](int r) { return Z(q, r); });
+        });
+        const int64_t o = row + (int64_t)j * g.pitch + i;
+        cross[o] = fxy;
+        cross[P + o] = fxz;
+        cross[2 * P + o] = fyz;
+        cross[3 * P + o] = fxyz;
     }
 }
 
@@ -333,7 +372,7 @@ cudaError_t launch_recon3d(const Geom &g, float *buf, cudaStream_t s)
 {
     dim3 block(RX, RY);
     dim3 grid((g.n0 + RX - 1) / RX, (g.n1 + RY - 1) / RY, (g.n2 + RZ - 1) / RZ);
-    k_recon3d<<<grid, block, 0, s>>>(buf, g);
+    k_recon3d<<<grid, block, 0, s>>>(buf + 2 * g.plane, buf + 3 * g.plane, buf + 4 * g.plane, g);
     return cudaGetLastError();
 }
 
