@@ -334,6 +334,7 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
         char msg[200];
         st = surrogate_for_step(v->surrogate, vp, dt, g->h[0], g->h[1], ip, chk, msg, sizeof(msg));
         if (st != GALS_OK) return fail(g, st, "%s", msg);
+        chk.err = g->err_dev;
         sur = v->surrogate;
         for (int k = 0; k < 6; ++k) sur_key[k] = ip.scale[k];
         sur_key[6] = chk.tol_x;

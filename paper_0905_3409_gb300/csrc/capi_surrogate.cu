@@ -36,6 +36,7 @@ struct gals_surrogate {
     float tol_x = 0.05f, tol_J = 0.05f;
     int samples = 4;
     unsigned long long *counters = nullptr;  // tiles, fallbacks
+    int *err_dev = nullptr;                  // device error word of the inference kernel
     int adam_step = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -60,6 +61,17 @@ gals_status scuda(gals_surrogate *s, cudaError_t e, const char *what)
 {
     return sfail(s, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
                  cudaGetErrorString(e));
+}
+
+// After a synchronisation: report (and clear) a timeout recorded by the inference kernel.
+gals_status check_err(gals_surrogate *s)
+{
+    int code = 0;
+    cudaError_t e = cudaMemcpy(&code, s->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return scuda(s, e, "error word");
+    if (code == 0) return GALS_OK;
+    cudaMemset(s->err_dev, 0, sizeof(int));
+    return sfail(s, GALS_ERR_TIMEOUT, "a bounded wait of the inference kernel ran out (code %d)", code);
 }
 
 uint64_t splitmix64_host(uint64_t &state)
@@ -171,11 +183,11 @@ gals_status gals_surrogate_create(const gals_mlp_desc *desc, gals_surrogate **ou
     if ((e = cudaMalloc(&s->params, pb)) != cudaSuccess || (e = cudaMalloc(&s->grad, pb)) != cudaSuccess ||
         (e = cudaMalloc(&s->m, pb)) != cudaSuccess || (e = cudaMalloc(&s->v, pb)) != cudaSuccess ||
         (e = cudaMalloc(&s->ip.w, sizeof(__nv_bfloat16) * W_TOTAL)) != cudaSuccess ||
-        (e = cudaMalloc(&s->ip.b, sizeof(float) * B_TOTAL)) != cudaSuccess ||
         (e = cudaMalloc(&s->scale_dev, sizeof(float) * OUT)) != cudaSuccess ||
         (e = cudaMalloc(&s->one, sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&s->loss_dev, sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&s->counters, 2 * sizeof(unsigned long long))) != cudaSuccess)
+        (e = cudaMalloc(&s->counters, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&s->err_dev, sizeof(int))) != cudaSuccess)
         return bail(e, "cudaMalloc");
     // Weights uniform in [-a, a]: Glorot for the hidden and output layers; the first layer
     // (and its bias) uniform in [-4, 4], so that the SiLU units of the first layer already
@@ -197,7 +209,8 @@ gals_status gals_surrogate_create(const gals_mlp_desc *desc, gals_surrogate **ou
         (e = cudaMemset(s->m, 0, pb)) != cudaSuccess || (e = cudaMemset(s->v, 0, pb)) != cudaSuccess ||
         (e = cudaMemcpy(s->one, &one, sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(s->scale_dev, ones.data(), sizeof(float) * OUT, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(s->counters, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
+        (e = cudaMemset(s->counters, 0, 2 * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(s->err_dev, 0, sizeof(int))) != cudaSuccess)
         return bail(e, "initial upload");
     if ((e = repack(s)) != cudaSuccess || (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
         return bail(e, "pack");
@@ -210,8 +223,8 @@ gals_status gals_surrogate_destroy(gals_surrogate *s)
     if (!s) return GALS_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(s->params); cudaFree(s->grad); cudaFree(s->m); cudaFree(s->v);
-    cudaFree(s->ip.w); cudaFree(s->ip.b); cudaFree(s->scale_dev); cudaFree(s->one);
-    cudaFree(s->loss_dev); cudaFree(s->counters);
+    cudaFree(s->ip.w); cudaFree(s->scale_dev); cudaFree(s->one);
+    cudaFree(s->loss_dev); cudaFree(s->counters); cudaFree(s->err_dev);
     cudaFree(s->Xn); cudaFree(s->T); cudaFree(s->G0); cudaFree(s->G1); cudaFree(s->split);
     for (int l = 0; l < NLAYER; ++l) { cudaFree(s->Z[l]); cudaFree(s->A[l]); }
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -314,7 +327,7 @@ gals_status gals_surrogate_stats(gals_surrogate *s, int64_t *tiles, int64_t *fal
     if (tiles) *tiles = (int64_t)h[0];
     if (fallbacks) *fallbacks = (int64_t)h[1];
     if (reset && (e = cudaMemset(s->counters, 0, sizeof(h))) != cudaSuccess) return scuda(s, e, "reset");
-    return GALS_OK;
+    return check_err(s);
 }
 
 gals_status gals_surrogate_get_params(const gals_surrogate *s, float *params, float *scales)
@@ -368,17 +381,17 @@ gals_status gals_surrogate_forward(gals_surrogate *s, const float *inputs, int n
     cudaError_t e;
     if ((e = ensure_scratch(s, n)) != cudaSuccess) return scuda(s, e, "scratch");
     if ((e = cudaMemcpyAsync(s->Xn, inputs, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
-        (e = infer_points(s->ip, s->Xn, s->T, n, s->stream)) != cudaSuccess ||
+        (e = infer_points(s->ip, s->Xn, s->T, n, s->err_dev, s->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(outputs, s->T, sizeof(float) * OUT * n, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
         return scuda(s, e, "forward");
-    return GALS_OK;
+    return check_err(s);
 }
 
 gals_status gals_surrogate_forward_device(gals_surrogate *s, const float *inputs, int64_t n, float *outputs)
 {
     if (!s || !inputs || !outputs || n < 1 || n > ((int64_t)1 << 26)) return sfail(s, GALS_ERR_ARG, "bad arguments");
-    cudaError_t e = infer_points(s->ip, inputs, outputs, (int)n, s->stream);
+    cudaError_t e = infer_points(s->ip, inputs, outputs, (int)n, s->err_dev, s->stream);
     if (e != cudaSuccess) return scuda(s, e, "forward_device");
     return GALS_OK;
 }

@@ -1,177 +1,324 @@
-// mlp_infer.cu -- tensor-core inference of the flow-map surrogate and the surrogate trace
-// of one GALS step.
+// mlp_infer.cu -- tensor-core (tcgen05 + TMEM) inference of the flow-map surrogate and the
+// surrogate trace of one GALS step.
 //
-// A block of 8 warps keeps all weights (BF16, about 115 KB) in shared memory and runs the
-// network on tiles of 128 points: warp w owns rows 16w..16w+15 of the 128 x 128 activation
-// matrix; every layer is mma.sync.m16n8k16 (BF16 operands, FP32 accumulation) with
-// operands fetched by ldmatrix from padded shared rows, then bias + SiLU in FP32 and a BF16
-// store for the next layer.  Blocks are persistent (one per SM) so the weights are loaded
-// once.  The trace kernel turns the outputs into the foot displacement and the Jacobian of
-// the backward map, checks a few nodes of every tile against the exact RK3 trace
-// (Sec. 5.1) and recomputes the whole tile with RK3 when the check fails.
+// A block holds all BF16 weights (120 KB with the bias slabs) in shared memory and runs
+// NWG = 3 groups of 4 warps, each with its own 128-point tile in flight, so that one tile's
+// epilogue overlaps another tile's matrix products.  Per layer and group, one elected
+// thread issues tcgen05.mma (M = 128 points, N = 128 units (16 for the output layer),
+// K = 16 per instruction, BF16 operands from shared memory, FP32 accumulator in TMEM, 128
+// columns per group) and commits them to the group's mbarrier; after a bounded wait each
+// thread reads its accumulator row back with tcgen05.ld (the bias is one more K-slab of the
+// product), applies SiLU (FP32, tanh on FP16 pairs) and stores the BF16 activations as the
+// next layer's A operand.  Operands use the no-swizzle K-major core-matrix layout: 8 rows
+// x 16 bytes per core matrix, core matrices adjacent in K `lbo` bytes apart and adjacent
+// in M/N 128 bytes apart.  The trace kernel turns the outputs into the foot displacement
+// and the Jacobian of the backward map, checks a few nodes of every tile against the exact
+// RK3 trace (Sec. 5.1) and recomputes the whole tile with RK3 when the check fails.
+#include <cuda_fp16.h>
+
 #include "mlp_internal.h"
+#include "tma.cuh"
 
 namespace gals {
 namespace mlp {
 
 namespace {
 
-constexpr int NT = 256;          // threads per block (8 warps x 16 rows)
+constexpr int NWG = 3;               // tile groups (tiles in flight) per block
+constexpr int GT = 128;              // threads per tile group: one per accumulator row
+                                     // (four warps, one per TMEM lane quarter)
+constexpr int NT = GT * NWG;         // threads per block
+constexpr int ROWS = 128;            // points per tile (= M of the products, = TMEM lanes)
+constexpr uint32_t TMEM_COLS = NWG <= 2 ? 256 : 512;  // power of two >= NWG * 128
+constexpr int kErrMmaTimeout = 2;
 
-__device__ __forceinline__ uint32_t smem_u32_(const void *p)
+// byte offset of element (r, k) of an R-row, K-major operand in the core-matrix layout
+__host__ __device__ constexpr uint32_t cm_off(int R, int r, int k)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
+    return (uint32_t)((k >> 3) * (R >> 3) * 128 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
-constexpr int ROWS = 128;        // points per tile
-constexpr int LDA = 136;         // padded row length (bf16) of activations and weights
-constexpr int LD1 = 24;          // padded row length of the first layer (K = 16)
 
 struct Smem {
-    __nv_bfloat16 w1[128 * LD1];
-    __nv_bfloat16 w[3][128 * LDA];
-    __nv_bfloat16 w5[8 * LDA];
-    float b[B_TOTAL];
-    __nv_bfloat16 in[ROWS * LD1];
-    __nv_bfloat16 act[2][ROWS * LDA];
-    float out[ROWS * 8];
+    __nv_bfloat16 w[W_TOTAL];            // packed operands (weights, bias slabs, ones block)
+    __align__(1024) __nv_bfloat16 act[NWG][ROWS * HID];  // A operand of each group's tile
+    uint64_t bar[NWG];
+    uint32_t tmem;                       // TMEM base address from tcgen05.alloc
+    int fail[NWG];
 };
 
-__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void *p)
+// ---- tcgen05 / TMEM wrappers (PTX ISA, tcgen05 instructions) ----
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void wg_sync(int g)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32_(p)));
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(GT) : "memory");
 }
-__device__ __forceinline__ void ldsm_x2(uint32_t r[2], const void *p)
+// named barrier of the tile group that also ORs a flag over its threads
+__device__ __forceinline__ int wg_sync_or(int g, int flag)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r[0]), "=r"(r[1])
-                 : "r"(smem_u32_(p)));
+    int r;
+    asm volatile(
+        "{\n .reg .pred q, o;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred o, %2, %3, q;\n"
+        " selp.s32 %0, 1, 0, o;\n}\n"
+        : "=r"(r)
+        : "r"(flag), "r"(1 + g), "n"(GT)
+        : "memory");
+    return r;
 }
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets,
+// descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    const uint32_t a = smem_u32(p);
+    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
-// Load the inference weights into shared memory (all threads).
-__device__ void load_weights(Smem &sm, const InferParams &ip)
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
 {
-    for (int e = threadIdx.x; e < 128 * 16; e += NT) sm.w1[(e / 16) * LD1 + e % 16] = ip.w[W1_OFF + e];
-    for (int L = 0; L < 3; ++L) {
-        const __nv_bfloat16 *src = ip.w + W2_OFF + (int64_t)L * 128 * 128;
-        for (int e = threadIdx.x; e < 128 * 128 / 8; e += NT) {  // 16-byte chunks
-            const int r = e / 16, c = (e % 16) * 8;
-            *reinterpret_cast<uint4 *>(&sm.w[L][r * LDA + c]) =
-                *reinterpret_cast<const uint4 *>(src + r * 128 + c);
-        }
-    }
-    for (int e = threadIdx.x; e < 8 * 128; e += NT) sm.w5[(e / 128) * LDA + e % 128] = ip.w[W5_OFF + e];
-    for (int e = threadIdx.x; e < B_TOTAL; e += NT) sm.b[e] = ip.b[e];
-    for (int e = threadIdx.x; e < ROWS * LD1; e += NT) sm.in[e] = __float2bfloat16(0.f);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
 }
 
-// out[128][8] = network(in[128][16]) ; must be called by all threads (warp w: rows 16w..)
-__device__ void run_tile(Smem &sm)
+// 32 columns of this warp's 32 TMEM lanes (one accumulator row per thread), not yet waited
+// for: several loads share one tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32])
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = warp * 16;
-    const int arow = r0 + (lane & 15), acol = (lane >> 4) * 8;          // A (x4) lane address
-    const int brow = (lane & 7) + ((lane >> 4) << 3), bcol = ((lane >> 3) & 1) * 8;  // B (x4)
-    const int crow = r0 + (lane >> 2), ccol = 2 * (lane & 3);            // accumulator
-    float acc[16][4];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-    // layer 1: K = 16
-    {
-        uint32_t a[4];
-        ldsm_x4(a, &sm.in[arow * LD1 + acol]);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-            uint32_t b[4];
-            ldsm_x4(b, &sm.w1[(8 * j + brow) * LD1 + bcol]);
-            mma_bf16(acc[j], a, b[0], b[1]);
-            mma_bf16(acc[j + 1], a, b[2], b[3]);
-        }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// SiLU of two pre-activations given as h = z/2 (FP32): silu(z) = z (1 + tanh(z/2)) / 2
+// = h + h tanh(h).  tanh runs on packed FP16 pairs (one MUFU operation for two values,
+// relative error about 1e-3, below the BF16 rounding of the result); the rest in FP32.
+// Returns the two results as a BF16 pair.
+__device__ __forceinline__ uint32_t silu2_bf16(float2 h)
+{
+    const __half2 hh = __floats2half2_rn(h.x, h.y);
+    uint32_t tr;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(tr) : "r"(*reinterpret_cast<const uint32_t *>(&hh)));
+    const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&tr));
+    const float2 y = __ffma2_rn(h, t, h);
+    return pack_bf16(y.x, y.y);
+}
+
+// ---- block setup / teardown ----
+
+// Weights and biases into shared memory, barriers, TMEM allocation (warp 0).
+__device__ void block_setup(Smem &sm, const InferParams &ip)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(ip.w);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm.w);
+    for (int e = threadIdx.x; e < (int)(W_TOTAL * 2 / 16); e += NT) dst[e] = src[e];
+    if (threadIdx.x < NWG) {
+        mbar_init(&sm.bar[threadIdx.x], 1);
+        sm.fail[threadIdx.x] = 0;
     }
-    int cur = 0;
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm.tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ void block_teardown(Smem &sm)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// Per-thread state of the tile engine.  Tile group g owns TMEM columns 128g..128g+127;
+// warp q of the group reads TMEM lane quarter q (rows 32q..32q+31).
+struct Wg {
+    int g;            // tile group
+    int r;            // thread's row = TMEM lane
+    uint32_t tcol;    // TMEM address of the group's accumulator, lane 0
+    uint32_t tlane;   // this warp's TMEM lane base, in address units
+    uint32_t phase;   // parity of the group's mbarrier
+};
+
+__device__ __forceinline__ Wg make_wg(const Smem &sm)
+{
+    Wg w;
+    w.g = threadIdx.x / GT;
+    w.r = threadIdx.x % GT;
+    w.tcol = sm.tmem + (uint32_t)(128 * w.g);
+    w.tlane = (uint32_t)((w.r & ~31) << 16);
+    w.phase = 0u;
+    return w;
+}
+
+// Row r's network input (x, y, phase in [-1, 1], then 1 for the bias, K padded to 16 with
+// zeros) as the first layer's A operand; then the group barrier that publishes it to the
+// tensor core.
+__device__ __forceinline__ void stage_input(Smem &sm, const Wg &w, float a, float b, float c)
+{
+    char *base = reinterpret_cast<char *>(sm.act[w.g]) + (w.r >> 3) * 128 + (w.r & 7) * 16;
+    *reinterpret_cast<uint4 *>(base) = make_uint4(pack_bf16(a, b), pack_bf16(c, 1.f), 0u, 0u);
+    *reinterpret_cast<uint4 *>(base + 2048) = make_uint4(0u, 0u, 0u, 0u);
+    fence_async_smem();
+    wg_sync(w.g);
+}
+
+// The network on the warpgroup's staged tile: out[0..5] = outputs of row r (+ 2 padding).
+// Returns false (after recording the error) if a product did not complete in time.
+__device__ bool run_tile(Smem &sm, Wg &w, int *err, float out[8])
+{
+    const int g = w.g;
+    const char *act = reinterpret_cast<const char *>(sm.act[g]);
+    const char *wts = reinterpret_cast<const char *>(sm.w);
+    const bool leader = threadIdx.x % GT == 0;
+    for (int L = 0; L < NLAYER; ++L) {
+        if (leader) {
+            tc_fence_after();
+            if (L == 0) {
+                umma(w.tcol, sdesc(act, 2048, 128), sdesc(wts + 2 * W1_OFF, 2048, 128),
+                     idesc_bf16(128, 128), 0u);
+            } else if (L < NLAYER - 1) {
+                const char *W = wts + 2 * (W2_OFF + (int64_t)(L - 1) * 128 * 128);
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+                    umma(w.tcol, sdesc(act + s * 4096, 2048, 128), sdesc(W + s * 4096, 2048, 128),
+                         idesc_bf16(128, 128), s > 0 ? 1u : 0u);
+                umma(w.tcol, sdesc(wts + 2 * ONES_OFF, 2048, 128),
+                     sdesc(wts + 2 * (WB_OFF + (int64_t)(L - 1) * 128 * 16), 2048, 128), idesc_bf16(128, 128), 1u);
+            } else {
+#pragma unroll
+                for (int s = 0; s < 8; ++s)
+                    umma(w.tcol, sdesc(act + s * 4096, 2048, 128), sdesc(wts + 2 * W5_OFF + s * 512, 256, 128),
+                         idesc_bf16(128, 16), s > 0 ? 1u : 0u);
+                umma(w.tcol, sdesc(wts + 2 * ONES_OFF, 2048, 128), sdesc(wts + 2 * W5B_OFF, 256, 128),
+                     idesc_bf16(128, 16), 1u);
+            }
+            umma_commit(&sm.bar[g]);
+        }
+        // one warp polls the barrier; the others sleep in the group barrier below
+        const bool ok = (threadIdx.x % GT) < 32 ? mbar_wait_bounded(&sm.bar[g], w.phase) : true;
+        w.phase ^= 1u;
+        if (wg_sync_or(g, !ok)) {
+            if (leader) atomicExch(err, kErrMmaTimeout);
+            return false;
+        }
+        tc_fence_after();
+        const uint32_t ta = w.tcol + w.tlane;
+        if (L < NLAYER - 1) {
+            // SiLU of h = z/2 (the accumulator), BF16 activations of row r as the next
+            // layer's A operand (K = 128)
+            char *arow = reinterpret_cast<char *>(sm.act[g]) + (w.r >> 3) * 128 + (w.r & 7) * 16;
 #pragma unroll 1
-    for (int L = 0; L < 4; ++L) {
-        // epilogue of the previous layer: bias + SiLU -> BF16 activations (own rows only)
-        const float *bias = sm.b + 128 * L;
-        __nv_bfloat16 *dst = sm.act[cur];
+            for (int c = 0; c < 4; c += 2) {
+                uint32_t v[2][32];
+                tmem_ld32_nowait(ta + 32 * c, v[0]);
+                tmem_ld32_nowait(ta + 32 * c + 32, v[1]);
+                tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int c = 8 * j + ccol;
-            const float b0 = bias[c], b1 = bias[c + 1];
-            *reinterpret_cast<__nv_bfloat162 *>(&dst[crow * LDA + c]) =
-                __floats2bfloat162_rn(silu(acc[j][0] + b0), silu(acc[j][1] + b1));
-            *reinterpret_cast<__nv_bfloat162 *>(&dst[(crow + 8) * LDA + c]) =
-                __floats2bfloat162_rn(silu(acc[j][2] + b0), silu(acc[j][3] + b1));
-        }
-        __syncwarp();
-        const __nv_bfloat16 *A = sm.act[cur];
-        if (L < 3) {
-            const __nv_bfloat16 *W = sm.w[L];
+                for (int u = 0; u < 2; ++u)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t p[4];
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                uint32_t a[4];
-                ldsm_x4(a, &A[arow * LDA + 16 * kk + acol]);
-#pragma unroll
-                for (int j = 0; j < 16; j += 2) {
-                    uint32_t b[4];
-                    ldsm_x4(b, &W[(8 * j + brow) * LDA + 16 * kk + bcol]);
-                    mma_bf16(acc[j], a, b[0], b[1]);
-                    mma_bf16(acc[j + 1], a, b[2], b[3]);
-                }
+                        for (int e = 0; e < 4; ++e) {
+                            const int k = 8 * q + 2 * e;
+                            p[e] = silu2_bf16(make_float2(__uint_as_float(v[u][k]), __uint_as_float(v[u][k + 1])));
+                        }
+                        *reinterpret_cast<uint4 *>(arow + (4 * (c + u) + q) * 2048) =
+                            make_uint4(p[0], p[1], p[2], p[3]);
+                    }
             }
-            cur ^= 1;
+            tc_fence_before();
+            fence_async_smem();
+            wg_sync(g);
         } else {
-            // output layer: N = 8 (6 used)
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t v[8];
+            tmem_ld8(ta, v);
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                uint32_t a[4], b[2];
-                ldsm_x4(a, &A[arow * LDA + 16 * kk + acol]);
-                ldsm_x2(b, &sm.w5[(lane & 7) * LDA + 16 * kk + ((lane >> 3) & 1) * 8]);
-                mma_bf16(o, a, b[0], b[1]);
-            }
-            const float *b5 = sm.b + 512;
-            sm.out[crow * 8 + ccol] = o[0] + b5[ccol];
-            sm.out[crow * 8 + ccol + 1] = o[1] + b5[ccol + 1];
-            sm.out[(crow + 8) * 8 + ccol] = o[2] + b5[ccol];
-            sm.out[(crow + 8) * 8 + ccol + 1] = o[3] + b5[ccol + 1];
+            for (int k = 0; k < 8; ++k) out[k] = __uint_as_float(v[k]);
+            tc_fence_before();
         }
-        __syncwarp();
     }
+    return true;
+}
+
+// After an abort: bounded wait for the products still in flight, before TMEM is freed.
+__device__ void drain(Smem &sm, const Wg &w, bool aborted)
+{
+    if (aborted) mbar_wait_bounded(&sm.bar[w.g], w.phase ^ 1u);
 }
 
 __global__ void __launch_bounds__(NT, 1)
-k_infer_points(InferParams ip, const float *__restrict__ Xn, float *__restrict__ Y, int n)
+k_infer_points(InferParams ip, const float *__restrict__ Xn, float *__restrict__ Y, int n, int *err)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    load_weights(sm, ip);
-    __syncthreads();
-    for (int t0 = blockIdx.x * ROWS; t0 < n; t0 += gridDim.x * ROWS) {
-        if (threadIdx.x < ROWS) {
-            const int p = t0 + threadIdx.x;
-            for (int c = 0; c < 3; ++c)
-                sm.in[threadIdx.x * LD1 + c] = __float2bfloat16(p < n ? Xn[3 * p + c] : 0.f);
-        }
-        __syncthreads();
-        run_tile(sm);
-        __syncthreads();
-        if (threadIdx.x < ROWS && t0 + threadIdx.x < n)
-            for (int c = 0; c < OUT; ++c) Y[6 * (t0 + threadIdx.x) + c] = sm.out[threadIdx.x * 8 + c];
-        __syncthreads();
+    block_setup(sm, ip);
+    Wg w = make_wg(sm);
+    bool aborted = false;
+    const int ntiles = (n + ROWS - 1) / ROWS;
+    for (int tile = blockIdx.x * NWG + w.g; tile < ntiles; tile += gridDim.x * NWG) {
+        const int p = tile * ROWS + w.r;
+        const int64_t pc = min(p, n - 1);
+        stage_input(sm, w, Xn[3 * pc], Xn[3 * pc + 1], Xn[3 * pc + 2]);
+        float o[8];
+        if (!run_tile(sm, w, err, o)) { aborted = true; break; }
+        if (p < n)
+            for (int c = 0; c < OUT; ++c) Y[6 * (int64_t)p + c] = o[c];
+        wg_sync(w.g);  // act[g] is rewritten by the next tile's inputs
     }
+    drain(sm, w, aborted);
+    block_teardown(sm);
 }
 
 __device__ __forceinline__ uint32_t tile_hash(uint32_t a, uint32_t b)
@@ -188,63 +335,61 @@ k_mlp_trace(InferParams ip, Geom g, VelParams vp, const StageCoef *__restrict__ 
             const double *__restrict__ t_dev, int kstep, double dt, float *__restrict__ trace,
             Check chk)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ int fail;
-    load_weights(sm, ip);
+    block_setup(sm, ip);
+    Wg w = make_wg(sm);
+    bool aborted = false;
     const double t = t_dev[0] + (double)kstep * dt;
     const float phase = (float)(t - floor(t));
     const float dtf = (float)dt;
     const int tiles_x = (g.n0 + ROWS - 1) / ROWS;
     const int ntiles = tiles_x * g.n1;
-    __syncthreads();
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // outputs of the tile's rows for the residual check (act[g] is free after the products)
+    float *outs = reinterpret_cast<float *>(sm.act[w.g]);
+    for (int tile = blockIdx.x * NWG + w.g; tile < ntiles; tile += gridDim.x * NWG) {
         const int j = tile / tiles_x, x0 = (tile % tiles_x) * ROWS;
-        const int tid = threadIdx.x;
-        const int i = x0 + tid;
-        if (tid < ROWS) {
+        const int i = x0 + w.r;
+        if (w.r == 0) sm.fail[w.g] = 0;
+        {
             const float x = g.lo0 + (float)min(i, g.n0 - 1) * g.h0, y = g.lo1 + (float)j * g.h1;
-            sm.in[tid * LD1 + 0] = __float2bfloat16(2.f * x - 1.f);
-            sm.in[tid * LD1 + 1] = __float2bfloat16(2.f * y - 1.f);
-            sm.in[tid * LD1 + 2] = __float2bfloat16(2.f * phase - 1.f);
+            stage_input(sm, w, 2.f * x - 1.f, 2.f * y - 1.f, 2.f * phase - 1.f);
         }
-        if (tid == 0) fail = 0;
-        __syncthreads();
-        run_tile(sm);
-        __syncthreads();
-        const int64_t o = (int64_t)j * g.pitch + i;
+        float y[8];
+        if (!run_tile(sm, w, chk.err, y)) { aborted = true; break; }
+        for (int c = 0; c < OUT; ++c) outs[w.r * 8 + c] = y[c];
         float d[2], J[4];
-        if (tid < ROWS) {
-            const float *y = &sm.out[tid * 8];
-            d[0] = y[0] * ip.scale[0] * g.h0;
-            d[1] = y[1] * ip.scale[1] * g.h1;
-            J[0] = 1.f + dtf * y[2] * ip.scale[2];
-            J[1] = dtf * y[3] * ip.scale[3];
-            J[2] = dtf * y[4] * ip.scale[4];
-            J[3] = 1.f + dtf * y[5] * ip.scale[5];
-        }
+        d[0] = y[0] * ip.scale[0] * g.h0;
+        d[1] = y[1] * ip.scale[1] * g.h1;
+        J[0] = 1.f + dtf * y[2] * ip.scale[2];
+        J[1] = dtf * y[3] * ip.scale[3];
+        J[2] = dtf * y[4] * ip.scale[4];
+        J[3] = 1.f + dtf * y[5] * ip.scale[5];
+        wg_sync(w.g);
         // residual check of `samples` nodes of the tile against the exact RK3 trace
         const int width = min(ROWS, g.n0 - x0);
-        if (tid < chk.samples) {
-            const int q = (int)(tile_hash((uint32_t)tile, (uint32_t)kstep + 977u * tid) % (uint32_t)width);
-            const float *y = &sm.out[q * 8];
-            const float xq = g.lo0 + (float)(x0 + q) * g.h0, yq = g.lo1 + (float)j * g.h1;
+        if (w.r < chk.samples) {
+            const int q = (int)(tile_hash((uint32_t)tile, (uint32_t)kstep + 977u * w.r) % (uint32_t)width);
+            const float *yq = &outs[q * 8];
+            const float xq = g.lo0 + (float)(x0 + q) * g.h0, yy = g.lo1 + (float)j * g.h1;
             float dr[2], Jr[4];
-            trace2d<TR_RK3, VK_FOURIER2D>(vp, *coef, xq, yq, dtf, dr[0], dr[1], Jr);
-            const float ex = fmaxf(fabsf(y[0] * ip.scale[0] * g.h0 - dr[0]) * g.ih0,
-                                   fabsf(y[1] * ip.scale[1] * g.h1 - dr[1]) * g.ih1);
-            const float mJ[4] = {1.f + dtf * y[2] * ip.scale[2], dtf * y[3] * ip.scale[3],
-                                 dtf * y[4] * ip.scale[4], 1.f + dtf * y[5] * ip.scale[5]};
+            trace2d<TR_RK3, VK_FOURIER2D>(vp, *coef, xq, yy, dtf, dr[0], dr[1], Jr);
+            const float ex = fmaxf(fabsf(yq[0] * ip.scale[0] * g.h0 - dr[0]) * g.ih0,
+                                   fabsf(yq[1] * ip.scale[1] * g.h1 - dr[1]) * g.ih1);
+            const float mJ[4] = {1.f + dtf * yq[2] * ip.scale[2], dtf * yq[3] * ip.scale[3],
+                                 dtf * yq[4] * ip.scale[4], 1.f + dtf * yq[5] * ip.scale[5]};
             float eJ = 0.f;
             for (int e = 0; e < 4; ++e) eJ = fmaxf(eJ, fabsf(mJ[e] - Jr[e]));
-            if (!(ex <= chk.tol_x) || !(eJ <= chk.tol_J)) atomicOr(&fail, 1);
+            if (!(ex <= chk.tol_x) || !(eJ <= chk.tol_J)) atomicOr(&sm.fail[w.g], 1);
         }
-        __syncthreads();
-        if (fail && tid < ROWS && i < g.n0) {
-            const float x = g.lo0 + (float)i * g.h0, y = g.lo1 + (float)j * g.h1;
-            trace2d<TR_RK3, VK_FOURIER2D>(vp, *coef, x, y, dtf, d[0], d[1], J);
+        wg_sync(w.g);
+        const bool fail = sm.fail[w.g] != 0;
+        if (fail && i < g.n0) {
+            const float x = g.lo0 + (float)i * g.h0, yy = g.lo1 + (float)j * g.h1;
+            trace2d<TR_RK3, VK_FOURIER2D>(vp, *coef, x, yy, dtf, d[0], d[1], J);
         }
-        if (tid < ROWS && i < g.n0) {
+        if (i < g.n0) {
+            const int64_t o = (int64_t)j * g.pitch + i;
             trace[o] = d[0];
             trace[g.plane + o] = d[1];
             trace[2 * g.plane + o] = J[0];
@@ -252,59 +397,88 @@ k_mlp_trace(InferParams ip, Geom g, VelParams vp, const StageCoef *__restrict__ 
             trace[4 * g.plane + o] = J[2];
             trace[5 * g.plane + o] = J[3];
         }
-        if (tid == 0) {
+        if (w.r == 0) {
             atomicAdd(chk.tiles, 1ull);
             if (fail) atomicAdd(chk.fallbacks, 1ull);
         }
-        __syncthreads();
+        wg_sync(w.g);  // outs, fail and act[g] are reused by the next tile
+    }
+    drain(sm, w, aborted);
+    block_teardown(sm);
+}
+
+// FP32 master parameters -> packed BF16 operands in the core-matrix layout (see
+// mlp_internal.h): hidden layers and their biases halved, biases as K-slab columns.
+__global__ void k_pack(const float *__restrict__ p, __nv_bfloat16 *__restrict__ w)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < 128 * 16) {  // W1/2 (inputs 0..2), b1/2 (column 3), zeros
+        const int r = e / 16, c = e % 16;
+        const float v = c < IN ? p[woff(0) + r * IN + c] : (c == IN ? p[boff(0) + r] : 0.f);
+        w[W1_OFF + cm_off(128, r, c) / 2] = __float2bfloat16(0.5f * v);
+    }
+    if (e < 3 * 128 * 128) {  // W2/2..W4/2: 128 x 128
+        const int L = e / (128 * 128), rem = e % (128 * 128), r = rem / 128, c = rem % 128;
+        w[W2_OFF + (int64_t)L * 128 * 128 + cm_off(128, r, c) / 2] = __float2bfloat16(0.5f * p[woff(1 + L) + rem]);
+    }
+    if (e < 16 * 128) {  // W5: 16 x 128, rows 6..15 zero
+        const int r = e / 128, c = e % 128;
+        w[W5_OFF + cm_off(16, r, c) / 2] = __float2bfloat16(r < OUT ? p[woff(4) + r * 128 + c] : 0.f);
+    }
+    if (e < 3 * 128 * 16) {  // hidden bias slabs: b/2 in column 0
+        const int L = e / (128 * 16), rem = e % (128 * 16), r = rem / 16, c = rem % 16;
+        w[WB_OFF + (int64_t)L * 128 * 16 + cm_off(128, r, c) / 2] =
+            __float2bfloat16(c == 0 ? 0.5f * p[boff(1 + L) + r] : 0.f);
+    }
+    if (e < 16 * 16) {  // output bias slab: b5 in column 0
+        const int r = e / 16, c = e % 16;
+        w[W5B_OFF + cm_off(16, r, c) / 2] = __float2bfloat16(c == 0 && r < OUT ? p[boff(4) + r] : 0.f);
+    }
+    if (e < 128 * 16) {  // ones block
+        const int r = e / 16, c = e % 16;
+        w[ONES_OFF + cm_off(128, r, c) / 2] = __float2bfloat16(c == 0 ? 1.f : 0.f);
     }
 }
 
-__global__ void k_pack(const float *__restrict__ p, __nv_bfloat16 *__restrict__ w, float *__restrict__ b)
+int sm_count()
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < 128 * 16) {  // W1 [128][16], K padded with zeros
-        const int r = e / 16, c = e % 16;
-        w[W1_OFF + e] = __float2bfloat16(c < IN ? p[woff(0) + r * IN + c] : 0.f);
-    }
-    if (e < 3 * 128 * 128) {
-        const int L = e / (128 * 128), rem = e % (128 * 128);
-        w[W2_OFF + e] = __float2bfloat16(p[woff(1 + L) + rem]);
-    }
-    if (e < 8 * 128) {  // W5 [8][128], N padded with zeros
-        const int r = e / 128;
-        w[W5_OFF + e] = __float2bfloat16(r < OUT ? p[woff(4) + e] : 0.f);
-    }
-    if (e < 4 * 128) b[e] = p[boff(e / 128) + e % 128];
-    if (e < 8) b[512 + e] = e < OUT ? p[boff(4) + e] : 0.f;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
 }
+
+template <class K>
+cudaError_t set_smem(K fn)
+{
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+}
+
+static_assert(sizeof(Smem) <= 227 * 1024, "shared memory budget");
+static_assert(W_TOTAL * 2 % 16 == 0, "weights are copied in 16-byte chunks");
+static_assert(W2_OFF * 2 % 16 == 0 && W5_OFF * 2 % 16 == 0 && WB_OFF * 2 % 16 == 0 &&
+                  W5B_OFF * 2 % 16 == 0 && ONES_OFF * 2 % 16 == 0,
+              "operands start on 16-byte boundaries");
 
 }  // namespace
 
 cudaError_t pack_infer(const float *params, InferParams &ip, cudaStream_t s)
 {
-    k_pack<<<(3 * 128 * 128 + 255) / 256, 256, 0, s>>>(params, ip.w, ip.b);
+    k_pack<<<(3 * 128 * 128 + 255) / 256, 256, 0, s>>>(params, ip.w);
     return cudaGetLastError();
 }
 
-static cudaError_t set_smem(const void *fn)
-{
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-}
-
-cudaError_t infer_points(const InferParams &ip, const float *Xn, float *Y, int n, cudaStream_t s)
+cudaError_t infer_points(const InferParams &ip, const float *Xn, float *Y, int n, int *err, cudaStream_t s)
 {
     static bool set = false;
     if (!set) {
-        cudaError_t e = set_smem((const void *)k_infer_points);
+        cudaError_t e = set_smem(k_infer_points);
         if (e != cudaSuccess) return e;
         set = true;
     }
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = (n + ROWS - 1) / ROWS;
-    k_infer_points<<<tiles < sms ? tiles : sms, NT, sizeof(Smem), s>>>(ip, Xn, Y, n);
+    const int tiles = (n + ROWS - 1) / ROWS, sms = sm_count();
+    const int blocks = (tiles + NWG - 1) / NWG;
+    k_infer_points<<<blocks < sms ? blocks : sms, NT, sizeof(Smem), s>>>(ip, Xn, Y, n, err);
     return cudaGetLastError();
 }
 
@@ -314,15 +488,13 @@ cudaError_t launch_mlp_trace(const InferParams &ip, const Geom &g, const VelPara
 {
     static bool set = false;
     if (!set) {
-        cudaError_t e = set_smem((const void *)k_mlp_trace);
+        cudaError_t e = set_smem(k_mlp_trace);
         if (e != cudaSuccess) return e;
         set = true;
     }
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int ntiles = ((g.n0 + ROWS - 1) / ROWS) * g.n1;
-    k_mlp_trace<<<ntiles < sms ? ntiles : sms, NT, sizeof(Smem), s>>>(ip, g, vp, coef, t_dev, kstep,
+    const int ntiles = ((g.n0 + ROWS - 1) / ROWS) * g.n1, sms = sm_count();
+    const int blocks = (ntiles + NWG - 1) / NWG;
+    k_mlp_trace<<<blocks < sms ? blocks : sms, NT, sizeof(Smem), s>>>(ip, g, vp, coef, t_dev, kstep,
                                                                      dt, trace, chk);
     return cudaGetLastError();
 }

@@ -9,15 +9,22 @@ namespace mlp {
 
 // Inference weights: BF16 copies laid out for the tensor-core kernel, FP32 biases and
 // the output de-normalisation.
+// Each weight matrix (N units x K inputs) is stored as the tensor core's K-major operand
+// in the no-swizzle core-matrix layout (8 x 8 BF16 blocks of 128 bytes).  Biases enter the
+// products as one more K-slab: bias column k = 0 of a 16-wide slab times a constant block
+// whose column 0 is 1 (layer 1 uses input column 3 = 1 instead).  Hidden layers (weights
+// and biases) are pre-scaled by 1/2, exact in BF16, so their accumulators hold z/2.
 struct InferParams {
-    __nv_bfloat16 *w;   // W1 [128][16] (K padded), W2..W4 [128][128], W5 [8][128] (N padded)
-    float *b;           // b1..b4 [128 each], b5 [8]
+    __nv_bfloat16 *w;   // packed operands, W_TOTAL elements (offsets below)
     float scale[OUT];   // output k of the network times scale[k] is the physical target
 };
-constexpr int64_t W1_OFF = 0, W2_OFF = 128 * 16, W3_OFF = W2_OFF + 128 * 128,
-                  W4_OFF = W3_OFF + 128 * 128, W5_OFF = W4_OFF + 128 * 128,
-                  W_TOTAL = W5_OFF + 8 * 128;
-constexpr int B_TOTAL = 4 * 128 + 8;
+constexpr int64_t W1_OFF = 0,                          // 128 x 16: W1/2 (inputs 0..2), b1/2 (column 3)
+                  W2_OFF = W1_OFF + 128 * 16,          // 3 x (128 x 128): W2/2, W3/2, W4/2
+                  W5_OFF = W2_OFF + 3 * 128 * 128,     // 16 x 128: W5 (rows 6..15 zero)
+                  WB_OFF = W5_OFF + 16 * 128,          // 3 x (128 x 16): b2/2, b3/2, b4/2 in column 0
+                  W5B_OFF = WB_OFF + 3 * 128 * 16,     // 16 x 16: b5 in column 0
+                  ONES_OFF = W5B_OFF + 16 * 16,        // 128 x 16: 1 in column 0
+                  W_TOTAL = ONES_OFF + 128 * 16;
 
 // Residual check of the surrogate trace (per 128-node tile, `samples` nodes against the
 // exact RK3 trace): a tile fails when |delta_mlp - delta_rk3|_inf > tol_x cells or
@@ -26,6 +33,7 @@ struct Check {
     float tol_x, tol_J;
     int samples;
     unsigned long long *tiles, *fallbacks;  // device counters
+    int *err;                               // device error word (bounded waits)
 };
 
 __device__ void flowmap_rk4(const VelParams &vp, float x, float y, float t, float dt, int m,
@@ -45,8 +53,10 @@ cudaError_t adam_step(float *params, const float *grad, float *m, float *v, floa
                       float b2, float eps, int step, cudaStream_t s);
 // FP32 master parameters -> inference layout
 cudaError_t pack_infer(const float *params, InferParams &ip, cudaStream_t s);
-// Network outputs (normalised) for n inputs in [-1,1]^3 with the tensor-core kernel.
-cudaError_t infer_points(const InferParams &ip, const float *Xn, float *Y, int n, cudaStream_t s);
+// Network outputs (normalised) for n inputs in [-1,1]^3 with the tensor-core kernel; a
+// product that does not complete in time sets *err.
+cudaError_t infer_points(const InferParams &ip, const float *Xn, float *Y, int n, int *err,
+                         cudaStream_t s);
 // Surrogate trace of one step over a 2D grid: planes (dx, dy, J00, J01, J10, J11) with the
 // grid's pitch and plane stride, into `trace`; `coef` = this step's stage coefficients.
 cudaError_t launch_mlp_trace(const InferParams &ip, const Geom &g, const VelParams &vp,
