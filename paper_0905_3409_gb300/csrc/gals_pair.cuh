@@ -143,19 +143,22 @@ __device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
     J[3] = fma2(mdt, fma2(fma2(m2, N11, add2(a.d11, M11)), i6, N11), one);
 }
 
-// Paired 1D basis (see basis1): near = xi >= 1/2 evaluates the value part from the
-// nearer end so that xi = 0 or 1 reproduce node data exactly.
-struct Basis2 { F2 Sn, dS, hG0, hG1, dG0, dG1; bool n0, n1; };
+// Paired 1D basis (see basis1).  n0, n1 = (xi >= 1/2) per lane pick each foot's nearest
+// corner, whose phi the Hermite evaluation subtracts from the corner values (the value
+// terms become O(h)).  The value part is then evaluated from the cell's first end,
+// p0 + (p1 - p0) S: exact at xi = 0, where every interior foot on a node lands, and, for
+// phi, at xi = 1 too (there p1 = 0 and p1 - p0 = -p0).  The gradient data at xi = 1 (a
+// foot clamped onto the last node of an axis) come back to rounding.
+struct Basis2 { F2 S, dS, hG0, hG1, dG0, dG1; bool n0, n1; };
 
 __device__ __forceinline__ Basis2 basis_pair(F2 xi, float h, float ih)
 {
     Basis2 b;
     const F2 om = fma2(xi, bc(-1.f), bc(1.f));
     const F2 xx = mul2(xi, xi), xo = mul2(xi, om);
-    const F2 S = mul2(xx, fma2(bc(-2.f), xi, bc(3.f)));
+    b.S = mul2(xx, fma2(bc(-2.f), xi, bc(3.f)));
     b.n0 = xi.x >= 0.5f;
     b.n1 = xi.y >= 0.5f;
-    b.Sn = add2(S, make_float2(b.n0 ? -1.f : 0.f, b.n1 ? -1.f : 0.f));
     b.dS = mul2(xo, bc(6.f * ih));
     b.hG0 = mul2(mul2(xo, om), bc(h));
     b.hG1 = mul2(mul2(om, xx), bc(-h));
@@ -171,7 +174,7 @@ __device__ __forceinline__ F2 pick(const Basis2 &b, F2 p0, F2 p1)
 
 __device__ __forceinline__ F2 hval2(const Basis2 &b, F2 p0, F2 p1, F2 s0, F2 s1)
 {
-    return fma2(sub2(p1, p0), b.Sn, fma2(s0, b.hG0, fma2(s1, b.hG1, pick(b, p0, p1))));
+    return fma2(sub2(p1, p0), b.S, fma2(s0, b.hG0, fma2(s1, b.hG1, p0)));
 }
 __device__ __forceinline__ F2 hder2(const Basis2 &b, F2 p0, F2 p1, F2 s0, F2 s1)
 {
