@@ -51,7 +51,8 @@ struct gals_grid {
     double t = 0.0;
     int64_t steps = 0;
     double *t_dev = nullptr;
-    CUtensorMap maps[2][2];       // TMA maps per buffer: [b][0] COMPACT box, [b][1] FULL box
+    CUtensorMap maps[2][3];       // TMA maps per buffer: [b][0] COMPACT box, [b][1] FULL box,
+                                  // [b][2] 3D reconstruction box
     float *trace_buf = nullptr;   // surrogate trace of the current step: dx, dy, J (6 planes)
     int *err_dev = nullptr;       // device error word written by kernels (bounded waits)
     StageCoef *coef = nullptr;    // per-step stage coefficients of the current call
@@ -124,6 +125,7 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
         }
         a.tmap3 = &g->maps[cur][0];
         a.tmap4 = &g->maps[cur][1];
+        a.tmap_cross = &g->maps[cur ^ 1][2];
         a.err = g->err_dev;
         a.trace = trace == GALS_TRACE_EULER ? TR_EULER : (trace == GALS_TRACE_SURROGATE ? TR_GIVEN : TR_RK3);
         if (g->layout == GALS_LAYOUT_FULL) {
@@ -225,9 +227,9 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
         return st;
     }
     // TMA maps of each buffer with the step kernels' tile boxes:
-    // 2D (x, y, plane), 3D (x, y, z, plane)
+    // 2D (x, y, plane), 3D (x, y, z, plane); 3D also the reconstruction kernel's box
     for (int b = 0; b < 2; ++b)
-        for (int v = 0; v < 2; ++v) {
+        for (int v = 0; v < (g->dim == 2 ? 2 : 3); ++v) {
             if (g->dim == 2) {
                 const int np = v == 0 ? 3 : 4;
                 const uint64_t dims[3] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)np};
@@ -237,8 +239,12 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
                 e = make_tile_map(&g->maps[b][v], g->buf[b], 3, dims, strides, box);
             } else {
                 uint32_t box[4];
-                tile_box3d(v == 0, box);
-                const uint64_t dims[4] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)G.n2, (uint64_t)box[3]};
+                if (v < 2)
+                    tile_box3d(v == 0, box);
+                else
+                    recon_box3d(box);
+                const uint64_t np = v == 2 ? 8 : box[3];  // the reconstruction box starts at plane 2
+                const uint64_t dims[4] = {(uint64_t)G.n0, (uint64_t)G.n1, (uint64_t)G.n2, np};
                 const uint64_t strides[3] = {(uint64_t)G.pitch * 4, (uint64_t)G.pitch * G.n1 * 4,
                                              (uint64_t)G.plane * 4};
                 e = make_tile_map(&g->maps[b][v], g->buf[b], 4, dims, strides, box);

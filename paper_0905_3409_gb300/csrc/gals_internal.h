@@ -21,6 +21,7 @@ struct StepLaunch {
     int write_cross;     // 1: also write the mixed-derivative planes of the new state
     const CUtensorMap *tmap4; // TMA map of `in` for reading stored mixed derivatives
     const CUtensorMap *tmap3; // TMA map of `in` for rebuilding them (COMPACT)
+    const CUtensorMap *tmap_cross; // 3D FULL: TMA map of `out` with the reconstruction box
     int *err;            // device error word (kErrTmaTimeout on a lost tile copy)
 };
 
@@ -28,6 +29,8 @@ struct StepLaunch {
 void tile_box2d(int np, uint32_t box[3]);
 // Box (x, y, z, planes) of the 3D step kernel's staged tile.
 void tile_box3d(int cross_recon, uint32_t box[4]);
+// Box (x, y, z, planes) of the 3D reconstruction kernel's staged psi_y, psi_z.
+void recon_box3d(uint32_t box[4]);
 // Encode a tiled TMA map of FP32 data: rank dims (innermost first), byte strides of
 // dims 1..rank-1, box extents; zero fill outside the tensor.
 cudaError_t make_tile_map(CUtensorMap *map, const float *base, int rank, const uint64_t *dims,

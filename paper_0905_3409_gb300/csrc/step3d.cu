@@ -310,6 +310,51 @@ __global__ void __launch_bounds__(RX *RY) k_recon3d(const float *__restrict__ py
     }
 }
 
+// The same reconstruction after a FULL step, with psi_y and psi_z of a block's nodes
+// (x-halo 4 for 16-byte TMA rows, y-halo 2 for the one-sided ends) staged in shared memory
+// by one TMA copy: a block of 32 x 8 threads covers QZ z-slices.
+constexpr int QX = 32, QY = 8, QZ = 4, QHX = 4, QHY = 2;
+constexpr int QW = QX + 2 * QHX, QH = QY + 2 * QHY;
+
+__global__ void __launch_bounds__(QX *QY)
+k_recon3d_tma(float *__restrict__ buf, Geom g, const __grid_constant__ CUtensorMap map,
+              int *__restrict__ err)
+{
+    __shared__ __align__(128) float t[2][QZ][QH][QW];  // psi_y, psi_z
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x + QX * threadIdx.y;
+    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = blockIdx.z * QZ;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, (uint32_t)sizeof(t));
+        tma_load_4d(&t[0][0][0][0], &map, x0 - QHX, y0 - QHY, z0, 2, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicExch(err, kErrTmaTimeout);
+            mbar_wait_bounded(&bar, 0);
+        }
+        return;
+    }
+    const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+    if (i >= g.n0 || j >= g.n1) return;
+    const int64_t P = g.plane;
+    const int nz = min(QZ, g.n2 - z0);
+    for (int dz = 0; dz < nz; ++dz) {
+        auto Y = [&](int q, int r) { return t[0][dz][r - y0 + QHY][q - x0 + QHX]; };
+        auto Z = [&](int q, int r) { return t[1][dz][r - y0 + QHY][q - x0 + QHX]; };
+        const int64_t o = ((int64_t)(z0 + dz) * g.n1 + j) * g.pitch + i;
+        buf[4 * P + o] = dline(i, g.n0, g.i2h0, [&](int q) { return Y(q, j); });
+        buf[5 * P + o] = dline(i, g.n0, g.i2h0, [&](int q) { return Z(q, j); });
+        buf[6 * P + o] = dline(j, g.n1, g.i2h1, [&](int r) { return Z(i, r); });
+        buf[7 * P + o] = dline(i, g.n0, g.i2h0, [&](int q) {
+            return dline(j, g.n1, g.i2h1, [&](int r) { return Z(q, r); });
+        });
+    }
+}
+
 template <int TR, int VK, int CR>
 cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
 {
@@ -354,7 +399,14 @@ cudaError_t launch_step3d(const StepLaunch &a, cudaStream_t s)
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess || !a.write_cross) return e;
-    return launch_recon(3, a.geom, a.out, s);
+    dim3 grid((a.geom.n0 + QX - 1) / QX, (a.geom.n1 + QY - 1) / QY, (a.geom.n2 + QZ - 1) / QZ);
+    k_recon3d_tma<<<grid, dim3(QX, QY), 0, s>>>(a.out, a.geom, *a.tmap_cross, a.err);
+    return cudaGetLastError();
+}
+
+void recon_box3d(uint32_t box[4])
+{
+    box[0] = QW; box[1] = QH; box[2] = QZ; box[3] = 2;
 }
 
 void tile_box3d(int cross_recon, uint32_t box[4])
