@@ -35,8 +35,78 @@ template <int TY> struct Geo {
 template <int TY, int WC> struct Smem {
     float psy[WC ? TY : 1][TX + 3];   // psi_y+ of columns x0-2 .. x0+TX
     StageCoefPair scp;
+    float fsum[12][TY];               // FOURIER2D stage 1: row sums of the tile's rows
     uint64_t bar;
 };
+
+// FOURIER2D at grid nodes (stage 1, t + dt).  Psi = sum_kl A_kl s_k(x) s_l(y) separates:
+// the sums over l depend on the row only, so the block computes them once per tile row
+// (FRow, in shared memory), and each thread keeps its column's s_k(x), c_k(x) (FCol); a
+// node then costs the four-term sums over k.  The arithmetic (multiple angles by the
+// Chebyshev recurrences, the order of every sum) is that of vel2d_pair, lane by lane.
+struct FCol { float s[5], c[5]; };
+
+__device__ __forceinline__ void multiple_angles(float s1, float c1, float s[5], float c[5])
+{
+    s[1] = s1;
+    c[1] = c1;
+    s[2] = 2.f * __fmul_rn(s1, c1);
+    c[2] = __fmaf_rn(-2.f, __fmul_rn(s1, s1), 1.f);
+    s[3] = __fmaf_rn(s[2], c1, __fmul_rn(c[2], s1));
+    c[3] = __fmaf_rn(c[2], c1, -__fmul_rn(s[2], s1));
+    s[4] = 2.f * __fmul_rn(s[2], c[2]);
+    c[4] = __fmaf_rn(-2.f, __fmul_rn(s[2], s[2]), 1.f);
+}
+
+__device__ __forceinline__ FCol fourier_col(float x)
+{
+    FCol f;
+    float s1, c1;
+    sincospi_f(x, &s1, &c1);
+    multiple_angles(s1, c1, f.s, f.c);
+    return f;
+}
+
+// Row sums of row y for stage-1 tables: Ux_k = sum_l Al_kl c_l(y), Vx_k = sum_l A_kl s_l(y),
+// W_k = sum_l All_kl s_l(y), into out[k-1], out[4+k-1], out[8+k-1] (k = 1..4).
+__device__ __forceinline__ void fourier_row(const StageCoef &sc, float y, int k, float &ux, float &vx,
+                                            float &w)
+{
+    float sy1, cy1, sy[5], cy[5];
+    sincospi_f(y, &sy1, &cy1);
+    multiple_angles(sy1, cy1, sy, cy);
+    ux = 0.f; vx = 0.f; w = 0.f;
+#pragma unroll
+    for (int l = 1; l <= 4; ++l) {
+        const int kl = (k - 1) * 4 + (l - 1);
+        ux = __fmaf_rn(sc.Al[0][kl], cy[l], ux);
+        vx = __fmaf_rn(sc.A[0][kl], sy[l], vx);
+        w = __fmaf_rn(sc.All[0][kl], sy[l], w);
+    }
+}
+
+// v, Dv at the two nodes (rows r, r+1 of the tile) of a thread's column.
+template <int TY>
+__device__ __forceinline__ V2p fourier_stage1_pair(const FCol &f, const float (*fsum)[TY], int r)
+{
+    F2 u = bc(0.f), v = bc(0.f), d00 = bc(0.f), d01 = bc(0.f), d10 = bc(0.f);
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        const F2 Ux = make_float2(fsum[k - 1][r], fsum[k - 1][r + 1]);
+        const F2 Vx = make_float2(fsum[4 + k - 1][r], fsum[4 + k - 1][r + 1]);
+        const F2 W = make_float2(fsum[8 + k - 1][r], fsum[8 + k - 1][r + 1]);
+        const float kp = (float)k * kPi;
+        const F2 sk = bc(f.s[k]), ck = bc(f.c[k]);
+        u = fma2(neg2(sk), Ux, u);
+        v = fma2(mul2(bc(kp), ck), Vx, v);
+        d00 = fma2(mul2(bc(-kp), ck), Ux, d00);
+        d01 = fma2(sk, W, d01);
+        d10 = fma2(mul2(bc(-kp * kp), sk), Vx, d10);
+    }
+    V2p rr;
+    rr.u = u; rr.v = v; rr.d00 = d00; rr.d01 = d01; rr.d10 = d10; rr.d11 = neg2(d00);
+    return rr;
+}
 
 // phi_xy at corner column q (q = k + o, o in {0,1}) from the psi_y row window
 // w[0..3] = psi_y[k-1 .. k+2]: the same stencils as the reconstruction kernel.
@@ -147,7 +217,8 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
                                             const VelParams &vp, const StageCoef &sc,
                                             const StageCoefPair *scp, float dt, int i0, int j0,
                                             int i1, int j1, F2 x, F2 y, const Sep2 &cx,
-                                            const Sep2 &ry, F2 &phi, F2 &px, F2 &py)
+                                            const Sep2 &ry, F2 &phi, F2 &px, F2 &py,
+                                            const V2p *a1 = nullptr)
 {
     F2 dx, dy, J[4];
     if (TR == TR_GIVEN) {
@@ -159,6 +230,8 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
         dy = make_float2(__ldg(tb + P + o0), __ldg(tb + P + o1));
 #pragma unroll
         for (int e = 0; e < 4; ++e) J[e] = make_float2(__ldg(tb + (2 + e) * P + o0), __ldg(tb + (2 + e) * P + o1));
+    } else if (VK == VK_FOURIER2D && a1 != nullptr) {
+        trace2d_pair<TR, VK>(*a1, vp, sc, scp, x, y, dt, dx, dy, J);
     } else {
         trace2d_pair<TR, VK>(stage1_pair<VK>(vp, sc, scp, x, y, cx, ry), vp, sc, scp, x, y, dt, dx,
                              dy, J);
@@ -225,12 +298,26 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
     }
     const StageCoefPair *scp = &scp_s;
     (void)psy;
+    if (VK == VK_FOURIER2D) {
+        // stage-1 row sums of the tile's rows (rows past the grid repeat the last one)
+        for (int e = tid; e < TY * 4; e += TX) {
+            const int r = e >> 2, k = (e & 3) + 1;
+            const float yr = g.lo1 + (float)min(y0 + r, g.n1 - 1) * g.h1;
+            float ux, vx, w;
+            fourier_row(sc, yr, k, ux, vx, w);
+            sm.fsum[k - 1][r] = ux;
+            sm.fsum[4 + k - 1][r] = vx;
+            sm.fsum[8 + k - 1][r] = w;
+        }
+    }
 
     const int i = x0 + tid;
     const int rows = min(TY, g.n1 - y0);
     const float xs = g.lo0 + (float)i * g.h0;
     const F2 x = bc(xs);
     const Sep2 cx = (VK == VK_VORTEX2D) ? sep_factors2(x) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+    FCol fcol;
+    if (VK == VK_FOURIER2D) fcol = fourier_col(xs);
 
     // bounded wait for the tile; a block-uniform verdict so no thread is left at a barrier
     const bool ok = mbar_wait_bounded(&sm.bar, parity);
@@ -248,8 +335,14 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             const F2 y = make_float2(g.lo1 + (float)j0 * g.h1, g.lo1 + (float)j1 * g.h1);
             const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
             F2 phi, px, py;
-            node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y, cx, ry,
-                                    phi, px, py);
+            if (VK == VK_FOURIER2D && TR != TR_GIVEN) {
+                const V2p a1 = fourier_stage1_pair<TY>(fcol, sm.fsum, r);
+                node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
+                                            cx, ry, phi, px, py, &a1);
+            } else {
+                node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
+                                            cx, ry, phi, px, py);
+            }
             const int o = j0 * g.pitch + i;
             out[o] = phi.x;
             out[g.plane + o] = px.x;
