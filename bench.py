@@ -341,22 +341,15 @@ def batch_oracle_leg(probs, states, budget_s=10.0):
 
 def run_batch(args, wl):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     probs, states = batch_inputs(wl["batch"])  # before any CUDA work (spawned pool)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    from paper_0905_3409_gb300 import replicas
+    R = replicas.init("nccl") if int(os.environ.get("WORLD_SIZE", "1")) > 1 else replicas.init()
+    rank, world, local = R.rank, R.world, R.local
+    torch.cuda.set_device(local if world > 1 else 0)
     import __graft_entry__ as ge
     if rank == 0:
         ge.build()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     from paper_0905_3409_gb300 import gals
     stream = torch.cuda.Stream()
     sizes = [(p.n, p.n) for p in probs]
@@ -373,8 +366,7 @@ def run_batch(args, wl):
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -382,15 +374,11 @@ def run_batch(args, wl):
     b.step(vels, dts, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop() if rank == 0 else None
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = nodes * args.steps * world / (ms * 1e-3)
+    ms = replicas.max_over_ranks(R, ms, device="cuda")
+    value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
     bpn = bytes_per_node(2, args.layout)
     achieved = bpn * nodes / (ms * 1e-3 / args.steps) / 1e9
     peak, peak_kind = measured_peaks()
@@ -431,8 +419,7 @@ def run_batch(args, wl):
                                     "sample": sample}
         print(json.dumps(line))
     b.close()
-    if dist:
-        dist.destroy_process_group()
+    replicas.finish(R)
 
 
 def run_reference_batch(args, wl):
@@ -471,21 +458,14 @@ def run_reference_batch(args, wl):
 
 def run_ours(args, wl):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    from paper_0905_3409_gb300 import replicas
+    R = replicas.init("nccl") if int(os.environ.get("WORLD_SIZE", "1")) > 1 else replicas.init()
+    rank, world, local = R.rank, R.world, R.local
+    torch.cuda.set_device(local if world > 1 else 0)
     import __graft_entry__ as ge
     if rank == 0:
         ge.build()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     from paper_0905_3409_gb300 import gals
 
     n = wl["n"]
@@ -507,8 +487,7 @@ def run_ours(args, wl):
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -516,15 +495,11 @@ def run_ours(args, wl):
     g.step(vel, dt, args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop() if rank == 0 else None
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = nodes * args.steps * world / (ms * 1e-3)
+    ms = replicas.max_over_ranks(R, ms, device="cuda")
+    value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
 
     # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels)
     launches_per_step = 2 if (args.layout == "full" and dim == 3) else 1
@@ -544,19 +519,15 @@ def run_ours(args, wl):
     g2.step(vel, dt, 1)
     g2.read_state(pin_out.numpy())
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         g2.set_state(pin_in.numpy(), recon=False)
         g2.step(vel, dt, 1)
         g2.read_state(pin_out.numpy())
     el = time.perf_counter() - t0
-    el_t = torch.tensor([el], device="cuda")
-    if dist:
-        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-    el = float(el_t.item())
-    e2e_value = nodes * e2e_steps * world / el
+    el = replicas.max_over_ranks(R, el, device="cuda")
+    e2e_value = replicas.throughput(nodes * e2e_steps, world, el)
     io_bytes = nplanes * 4 * nodes
 
     if rank == 0:
@@ -584,8 +555,7 @@ def run_ours(args, wl):
         print(json.dumps(line))
     g.close()
     g2.close()
-    if dist:
-        dist.destroy_process_group()
+    replicas.finish(R)
 
 
 # ---------------------------------------------------------------------- learned trace
@@ -600,21 +570,14 @@ def run_surrogate(args, wl):
     in time RK3 run (interface symmetric difference, area, max |phi|/|psi| differences).
     The roofline is that of the tensor-core MLP evaluation over one grid's nodes."""
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    from paper_0905_3409_gb300 import replicas
+    R = replicas.init("nccl") if int(os.environ.get("WORLD_SIZE", "1")) > 1 else replicas.init()
+    rank, world, local = R.rank, R.world, R.local
+    torch.cuda.set_device(local if world > 1 else 0)
     import __graft_entry__ as ge
     if rank == 0:
         ge.build()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     from paper_0905_3409_gb300 import gals
 
     n = wl["n"]
@@ -637,8 +600,7 @@ def run_surrogate(args, wl):
         g.step(vel, dt, K)           # captures the K-step graph
         g.set_state(st_host, t0=0.0, recon=True)
         g.synchronize()
-        if dist:
-            dist.barrier()
+        replicas.barrier(R)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -646,11 +608,7 @@ def run_surrogate(args, wl):
         g.step(vel, dt, K)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        t = torch.tensor([ms], device="cuda")
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(R, e0.elapsed_time(e1), device="cuda")
 
     g_plain = gals.Grid(n, stream=stream)
     ms_plain = timed(plain, g_plain)
@@ -662,8 +620,8 @@ def run_surrogate(args, wl):
     ms_sur = timed(learned, g_sur)
     clocks = sampler.stop() if rank == 0 else None
     tiles, falls = S.stats()
-    value = nodes * K * world / (ms_sur * 1e-3)
-    value_plain = nodes * K * world / (ms_plain * 1e-3)
+    value = replicas.throughput(nodes * K, world, ms_sur * 1e-3)
+    value_plain = replicas.throughput(nodes * K, world, ms_plain * 1e-3)
 
     # accuracy: both runs against RK3 with dt/4 over the same time
     g_fine = gals.Grid(n, stream=stream)
@@ -710,18 +668,15 @@ def run_surrogate(args, wl):
     g2.step(learned, dt, 1)
     g2.read_state(pin_out.numpy())
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(R)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         g2.set_state(pin_in.numpy(), recon=False)
         g2.step(learned, dt, 1)
         g2.read_state(pin_out.numpy())
     el = time.perf_counter() - t0
-    el_t = torch.tensor([el], device="cuda")
-    if dist:
-        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-    e2e_value = nodes * e2e_steps * world / float(el_t.item())
+    e2e_value = replicas.throughput(nodes * e2e_steps, world,
+                                    replicas.max_over_ranks(R, el, device="cuda"))
     io_bytes = 4 * 4 * nodes
 
     if rank == 0:
@@ -761,8 +716,7 @@ def run_surrogate(args, wl):
     for g in (g_plain, g_sur, g_fine, g0, g2):
         g.close()
     S.close()
-    if dist:
-        dist.destroy_process_group()
+    replicas.finish(R)
 
 
 def main():
