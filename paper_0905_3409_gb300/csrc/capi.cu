@@ -173,6 +173,11 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
         if (!std::isfinite(d->lo[i]) || !std::isfinite(d->hi[i]) || !(d->hi[i] > d->lo[i]))
             return fail(nullptr, GALS_ERR_ARG, "axis %d: need finite lo < hi", i);
     }
+    {
+        char msg[160];
+        const int n3[3] = {d->n[0], d->n[1], d->dim == 3 ? d->n[2] : 1};
+        if (!gals::grid_size_ok(d->dim, n3, msg, sizeof(msg))) return fail(nullptr, GALS_ERR_ARG, "%s", msg);
+    }
     gals_grid *g = new (std::nothrow) gals_grid();
     if (!g) return fail(nullptr, GALS_ERR_NOMEM, "host allocation failed");
     g->dim = d->dim;

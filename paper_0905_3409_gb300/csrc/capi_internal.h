@@ -13,6 +13,12 @@ namespace gals {
 // parameters; on error writes a message to msg and returns the status.
 gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char *msg, size_t len);
 
+// Size limits of the kernels' index arithmetic and launch grids: 2D planes of at most
+// 2^31 - 1 elements (row pitch x rows, 32-bit offsets in the tile kernels), at most
+// 65535 tile rows of blocks in 2D (n[1] <= 65535 * rows per tile) and at most 65535
+// blocks along y and z in 3D (n[1], n[2] <= 262140).  Returns false with a message.
+bool grid_size_ok(int dim, const int n[3], char *msg, size_t len);
+
 // Whether surrogate `s` serves a step with these parameters; fills the kernel views.
 gals_status surrogate_for_step(const gals_surrogate *s, const VelParams &vp, double dt, double h0,
                                double h1, mlp::InferParams &ip, mlp::Check &chk, char *msg,

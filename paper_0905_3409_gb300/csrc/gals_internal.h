@@ -25,8 +25,9 @@ struct StepLaunch {
     int *err;            // device error word (kErrTmaTimeout on a lost tile copy)
 };
 
-// Box of the 2D step kernel's staged tile for np planes.
+// Box of the 2D step kernel's staged tile for np planes; its output rows per block.
 void tile_box2d(int np, uint32_t box[3]);
+int tile_rows2d();
 // Box (x, y, z, planes) of the 3D step kernel's staged tile.
 void tile_box3d(int cross_recon, uint32_t box[4]);
 // Box (x, y, z, planes) of the 3D reconstruction kernel's staged psi_y, psi_z.

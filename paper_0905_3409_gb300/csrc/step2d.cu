@@ -94,6 +94,8 @@ cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s)
     }
 }
 
+int tile_rows2d() { return TY; }
+
 void tile_box2d(int np, uint32_t box[3])
 {
     box[0] = TW;

@@ -1,5 +1,6 @@
 // velparams.cu -- validation of a gals_velocity descriptor and its conversion to the
 // kernels' VelParams (shared by the single-grid and batched C ABI).
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -66,6 +67,33 @@ gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char 
         }
     }
     return GALS_OK;
+}
+
+bool grid_size_ok(int dim, const int n[3], char *msg, size_t len)
+{
+    if (dim == 2) {
+        const int64_t pitch = ((int64_t)n[0] + 3) / 4 * 4;
+        if (pitch * n[1] > (int64_t)INT32_MAX) {
+            snprintf(msg, len, "2D grid %d x %d: more than 2^31 - 1 elements per plane", n[0], n[1]);
+            return false;
+        }
+        const int64_t rows = (int64_t)65535 * tile_rows2d();
+        if (n[1] > rows) {
+            snprintf(msg, len, "2D grid: n[1] = %d above %lld", n[1], (long long)rows);
+            return false;
+        }
+        return true;
+    }
+    for (int i = 1; i < 3; ++i)
+        if (n[i] > 65535 * 4) {
+            snprintf(msg, len, "3D grid: n[%d] = %d above %d", i, n[i], 65535 * 4);
+            return false;
+        }
+    if (n[0] > INT32_MAX - 3) {
+        snprintf(msg, len, "3D grid: n[0] = %d too large", n[0]);
+        return false;
+    }
+    return true;
 }
 
 }  // namespace gals

@@ -52,6 +52,18 @@ def test_version_and_argument_errors_without_gpu(built):
     d.hi[0] = d.hi[1] = 1.0
     assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
     assert built.gals_create_grid(None, ctypes.byref(h)) == gals.ERR_ARG
+    # size limits of the kernels' 32-bit plane offsets and launch grids (no allocation)
+    d.n[0], d.n[1] = 46344, 46341            # pitch 46344 x 46341 rows > 2^31 - 1
+    assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
+    assert b"2^31" in built.gals_last_error(None)
+    d.n[0], d.n[1] = 4, 786421               # more than 65535 blocks of 12 rows
+    assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
+    d.dim = 3
+    d.n[0], d.n[1], d.n[2] = 8, 8, 262141    # more than 65535 blocks of 4 z-slices
+    d.hi[2] = 1.0
+    assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
+    assert b"n[2]" in built.gals_last_error(None)
+    d.dim = 2
     assert built.gals_step(None, None, 0.1, 1) == gals.ERR_ARG
     assert built.gals_destroy_grid(None) == gals.OK
 
