@@ -26,14 +26,14 @@ _lib = None
 
 # enums of gals_oracle.h
 VEL_CONST, VEL_ROTATION, VEL_VORTEX2D, VEL_DEFORM3D, VEL_PSEUDO1D, VEL_FOURIER2D = range(6)
-TRACE_EULER, TRACE_RK3 = 0, 1
+TRACE_EULER, TRACE_RK3, TRACE_HEUN_PSI = 0, 1, 2
 CROSS_CENTRAL, CROSS_ZERO = 0, 1
 
 _VEL_NAMES = {
     "const": VEL_CONST, "rotation": VEL_ROTATION, "vortex2d": VEL_VORTEX2D,
     "deform3d": VEL_DEFORM3D, "pseudo1d": VEL_PSEUDO1D, "fourier2d": VEL_FOURIER2D,
 }
-_TRACE_NAMES = {"euler": TRACE_EULER, "rk3": TRACE_RK3}
+_TRACE_NAMES = {"euler": TRACE_EULER, "rk3": TRACE_RK3, "heun_psi": TRACE_HEUN_PSI}
 
 
 def build(force: bool = False) -> str:

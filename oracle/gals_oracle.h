@@ -37,7 +37,13 @@ enum {
     ORC_VEL_FOURIER2D = 5  /* stream fn sum_m a_m sin(k pi x) sin(l pi y) cos(2 pi n t + chi) */
 };
 
-enum { ORC_TRACE_EULER = 0, ORC_TRACE_RK3 = 1 };
+/* EULER, RK3: superconsistent traces (Sec. 5.1 examples); psi+ = J^T grad H(foot).
+ * HEUN_PSI: the CIR form of Sec. 4 with the step-3 choice the paper names for gradients:
+ * the foot by the Shu-Osher RK3 trace, psi(foot) = grad H(foot), then
+ * d psi / d tau = -grad v . psi (eq. cir_evolution_psi; (grad v)_ij = dv_j/dx_i) integrated
+ * forward from (foot, t) to (node, t + dt) by one step of Heun's method (explicit
+ * trapezoidal rule). */
+enum { ORC_TRACE_EULER = 0, ORC_TRACE_RK3 = 1, ORC_TRACE_HEUN_PSI = 2 };
 enum { ORC_CROSS_CENTRAL = 0, ORC_CROSS_ZERO = 1 };
 
 typedef struct {

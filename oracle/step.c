@@ -93,8 +93,30 @@ void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace,
     double H, gradH[3] = {0, 0, 0};
     orc_hermite_cell(dim, data, g->h, xi, &H, gradH);
 
-    /* superconsistent update: phi+ = H(foot), psi+ = J^T grad H(foot) */
     *phi = H;
+    if (trace == ORC_TRACE_HEUN_PSI) {
+        /* CIR step 3 (Sec. 4): psi(tau) along the characteristic from (foot, t) to
+         * (x, t+dt), d psi/d tau = -(grad v) . psi = -Dv^T psi, by Heun's method:
+         * k1 = f(foot, t, psi0), k2 = f(x, t+dt, psi0 + dt k1), psi+ = psi0 + dt (k1+k2)/2.
+         * The characteristic passes through the computed foot (not the clamped point). */
+        double v0[3], D0[9], v1[3], D1[9], k1[3], ps[3], k2[3];
+        orc_vel_eval(vel, dim, foot, t, v0, D0);
+        orc_vel_eval(vel, dim, x, t + dt, v1, D1);
+        for (int a = 0; a < dim; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < dim; ++b) s += D0[3 * b + a] * gradH[b];
+            k1[a] = -s;
+        }
+        for (int a = 0; a < dim; ++a) ps[a] = gradH[a] + dt * k1[a];
+        for (int a = 0; a < dim; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < dim; ++b) s += D1[3 * b + a] * ps[b];
+            k2[a] = -s;
+        }
+        for (int a = 0; a < dim; ++a) psi[a] = gradH[a] + 0.5 * dt * (k1[a] + k2[a]);
+        return;
+    }
+    /* superconsistent update: psi+ = J^T grad H(foot) */
     for (int a = 0; a < dim; ++a) {
         double s = 0.0;
         for (int b = 0; b < dim; ++b) s += J[3 * b + a] * gradH[b];

@@ -47,6 +47,7 @@ void orc_trace(int scheme, const orc_velocity *vel, int dim, const double *x,
     double v1[3], D1[9];
     orc_vel_eval(vel, dim, xv, t + dt, v1, D1);
 
+    /* HEUN_PSI uses the RK3 foot (its J is not used by that scheme) */
     if (scheme == ORC_TRACE_EULER) {
         identity3(J);
         for (int i = 0; i < 3; ++i) foot[i] = xv[i] - dt * v1[i];

@@ -202,12 +202,16 @@ def _pseudo1d_solution(X, Y, t, x0=(0.5, 0.5)):
     return e - math.exp(-0.15 ** 2), px, py
 
 
-def test_local_truncation_order_pseudo1d(golden):
+@pytest.mark.parametrize("trace", ["rk3", "heun_psi"])
+def test_local_truncation_order_pseudo1d(golden, trace):
     """Sec. 6.1.1: 16 steps with dt = h/2 on the pseudo-1D flow; the error away
     from the boundary converges with order 4 in phi and 3 in grad phi.  The
     region [0.4, 0.7]^2 is outside the numerical domain of dependence of the
     inflow edges and away from the one-sided cross stencils at the outflow edges
-    (the paper only says 'a part of the domain not influenced by the boundary')."""
+    (the paper only says 'a part of the domain not influenced by the boundary').
+    Both the superconsistent RK3 scheme and the CIR scheme with Heun's method for the
+    gradients (Sec. 4: RK3 for the characteristic, Heun for eq. cir_evolution_psi) have
+    these orders."""
     vel = oracle.velocity("pseudo1d")
     ephi, epsi = [], []
     for n in (129, 257, 513):
@@ -215,7 +219,7 @@ def test_local_truncation_order_pseudo1d(golden):
         dt = h / 2
         g = oracle.grid((n, n))
         st = oracle.recon_cross(g, inputs.gaussian_bump2d((n, n)))
-        st = oracle.run(g, vel, st, 0.0, dt, 16)
+        st = oracle.run(g, vel, st, 0.0, dt, 16, trace_scheme=trace)
         X, Y = np.meshgrid(*inputs.node_coords((n, n)), indexing="xy")
         ph, px, py = _pseudo1d_solution(X, Y, 16 * dt)
         region = (X >= 0.4) & (Y >= 0.4) & (X <= 0.7) & (Y <= 0.7)
@@ -265,3 +269,41 @@ def test_step_band_equals_full_step(dim):
     for b0, b1 in ((0, 3), (4, outer - 1), (outer - 2, outer)):
         band = oracle.step_band(g, vel, st, 0.2, 0.03, b0, b1)
         assert np.array_equal(band, full[:, b0:b1])
+
+
+def test_heun_psi_constant_velocity_equals_superconsistent():
+    """With constant v, grad v = 0: the Heun gradient update is grad H(foot), the same
+    as J^T grad H(foot) with J = I."""
+    n = (23, 19)
+    g = oracle.grid(n)
+    st = oracle.recon_cross(g, inputs.circle_sdf(n, center=(0.45, 0.55), r=0.3))
+    vel = oracle.velocity("const", c=(0.4, -0.3))
+    a = oracle.step(g, vel, st, 0.0, 0.03, trace_scheme="rk3")
+    b = oracle.step(g, vel, st, 0.0, 0.03, trace_scheme="heun_psi")
+    assert np.array_equal(a, b)
+
+
+def test_heun_psi_rotation_closed_form():
+    """Rigid rotation, grad v constant: Heun's method applied to d psi/d tau = B psi with
+    B = -(Dv)^T gives psi+ = (I + dt B + dt^2 B^2 / 2) psi(foot); for linear phi,
+    psi(foot) is the constant gradient a at every foot inside the box."""
+    n = (33, 33)
+    om, dt = 2 * np.pi, 0.01
+    g = oracle.grid(n)
+    a = np.array([0.3, -0.7])
+    st = inputs.linear2d(n, a=a)
+    vel = oracle.velocity("rotation", omega=om, center=(0.5, 0.5))
+    out = oracle.step(g, vel, st, 0.0, dt, trace_scheme="heun_psi")
+    Dv = np.array([[0.0, -om], [om, 0.0]])
+    B = -Dv.T
+    M = np.eye(2) + dt * B + 0.5 * dt * dt * B @ B
+    want = M @ a
+    X, Y = np.meshgrid(*inputs.node_coords(n), indexing="xy")
+    r = np.hypot(X - 0.5, Y - 0.5)
+    inside = r < 0.45   # feet stay inside the box
+    assert np.max(np.abs(out[1][inside] - want[0])) < 1e-13
+    assert np.max(np.abs(out[2][inside] - want[1])) < 1e-13
+    # the superconsistent RK3 update differs from it by O(dt^3) here
+    sc = oracle.step(g, vel, st, 0.0, dt, trace_scheme="rk3")
+    d = np.max(np.abs(sc[1:3][:, inside] - out[1:3][:, inside]))
+    assert 0 < d < 10 * (om * dt) ** 3
