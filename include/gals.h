@@ -83,7 +83,10 @@ enum {
 enum {
     GALS_TRACE_EULER = 0,     /* superconsistent forward Euler (Sec. 5.1, first order) */
     GALS_TRACE_RK3 = 1,       /* superconsistent Shu-Osher RK3 (Sec. 5.1), the default of Sec. 6 */
-    GALS_TRACE_SURROGATE = 2  /* learned flow map (gals_surrogate_*), RK3 fallback; 2D FOURIER2D */
+    GALS_TRACE_SURROGATE = 2, /* learned flow map (gals_surrogate_*), RK3 fallback; 2D FOURIER2D */
+    GALS_TRACE_HEUN_PSI = 3   /* CIR form of Sec. 4: foot by Shu-Osher RK3, psi(foot) = grad H,
+                                 then d psi/d tau = -(grad v) . psi along the characteristic
+                                 by one step of Heun's method (not superconsistent) */
 };
 
 typedef struct gals_surrogate gals_surrogate;   /* opaque, owned by the library */

@@ -127,7 +127,10 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
         a.tmap4 = &g->maps[cur][1];
         a.tmap_cross = &g->maps[cur ^ 1][2];
         a.err = g->err_dev;
-        a.trace = trace == GALS_TRACE_EULER ? TR_EULER : (trace == GALS_TRACE_SURROGATE ? TR_GIVEN : TR_RK3);
+        a.trace = trace == GALS_TRACE_EULER      ? TR_EULER
+                  : trace == GALS_TRACE_SURROGATE ? TR_GIVEN
+                  : trace == GALS_TRACE_HEUN_PSI  ? TR_HEUN
+                                                  : TR_RK3;
         if (g->layout == GALS_LAYOUT_FULL) {
             a.cross_in = CROSS_PLANE;
             a.write_cross = 1;

@@ -31,7 +31,9 @@ constexpr float kPi = 3.14159265358979323846f;
 
 enum VelKind { VK_CONST = 0, VK_ROTATION = 1, VK_VORTEX2D = 2, VK_DEFORM3D = 3,
                VK_PSEUDO1D = 4, VK_FOURIER2D = 5 };
-enum TraceKind { TR_EULER = 0, TR_RK3 = 1, TR_GIVEN = 2 };  // GIVEN: precomputed (surrogate)
+// GIVEN: precomputed (surrogate); HEUN: RK3 foot, gradients by Heun's method along the
+// characteristic (Sec. 4, CIR form)
+enum TraceKind { TR_EULER = 0, TR_RK3 = 1, TR_GIVEN = 2, TR_HEUN = 3 };
 enum CrossSrc { CROSS_PLANE = 0, CROSS_RECON = 1 };
 
 // Velocity descriptor as passed to kernels (by value).

@@ -105,6 +105,21 @@ __device__ __forceinline__ V2p vel2d_pair(const VelParams &vp, const StageCoef &
     return r;
 }
 
+// Gradient update of the CIR form (Sec. 4, step 3) by Heun's method: from psi0 = grad H at
+// the foot (time t) to the node (time t + dt) along the characteristic,
+// d psi / d tau = -Dv^T psi; Df = Dv at the foot and time t, Dn = Dv at the node, t + dt.
+__device__ __forceinline__ void heun_psi2(const V2p &Df, const V2p &Dn, float dt, F2 gx, F2 gy,
+                                          F2 &px, F2 &py)
+{
+    const F2 k1x = neg2(fma2(Df.d00, gx, mul2(Df.d10, gy)));
+    const F2 k1y = neg2(fma2(Df.d01, gx, mul2(Df.d11, gy)));
+    const F2 sx = fma2(bc(dt), k1x, gx), sy = fma2(bc(dt), k1y, gy);
+    const F2 k2x = neg2(fma2(Dn.d00, sx, mul2(Dn.d10, sy)));
+    const F2 k2y = neg2(fma2(Dn.d01, sx, mul2(Dn.d11, sy)));
+    px = fma2(bc(0.5f * dt), add2(k1x, k2x), gx);
+    py = fma2(bc(0.5f * dt), add2(k1y, k2y), gy);
+}
+
 // Superconsistent trace of Sec. 5.1 for two nodes; a = v(x, t+dt) supplied by the caller.
 template <int TR, int VK>
 __device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
@@ -259,6 +274,23 @@ __device__ __forceinline__ void matmul3_pair(const F2 *A, const F2 *B, F2 *C)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             C[3 * i + j] = fma2(A[3 * i], B[j], fma2(A[3 * i + 1], B[3 + j], mul2(A[3 * i + 2], B[6 + j])));
+}
+
+// 3D gradient update of the CIR form by Heun's method (see heun_psi2); Df, Dn as there.
+__device__ __forceinline__ void heun_psi3(const V3p &Df, const V3p &Dn, float dt, const F2 g[3],
+                                          F2 psi[3])
+{
+    F2 k1[3], s[3], k2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        k1[a] = neg2(fma2(Df.d[a], g[0], fma2(Df.d[3 + a], g[1], mul2(Df.d[6 + a], g[2]))));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s[a] = fma2(bc(dt), k1[a], g[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        k2[a] = neg2(fma2(Dn.d[a], s[0], fma2(Dn.d[3 + a], s[1], mul2(Dn.d[6 + a], s[2]))));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) psi[a] = fma2(bc(0.5f * dt), add2(k1[a], k2[a]), g[a]);
 }
 
 // Superconsistent RK3 trace of Sec. 5.1 for two nodes (a = v(x, t+dt) from the caller):

@@ -76,6 +76,7 @@ cudaError_t launch_cr(const StepLaunch &a, cudaStream_t s)
 template <int VK>
 cudaError_t launch_tr(const StepLaunch &a, cudaStream_t s)
 {
+    if (a.trace == TR_HEUN) return launch_cr<TR_HEUN, VK>(a, s);
     return a.trace == TR_EULER ? launch_cr<TR_EULER, VK>(a, s) : launch_cr<TR_RK3, VK>(a, s);
 }
 

@@ -236,6 +236,7 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
         trace2d_pair<TR, VK>(stage1_pair<VK>(vp, sc, scp, x, y, cx, ry), vp, sc, scp, x, y, dt, dx,
                              dy, J);
     }
+    (void)J;
     int k0, l0, k1, l1;
     F2 xi, eta;
     locate(i0, dx.x * g.ih0, g.n0, k0, xi.x);
@@ -257,6 +258,14 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
     F2 H, Hx, Hy;
     hermite2d_pair(c, bx, by, H, Hx, Hy);
     phi = H;
+    if (TR == TR_HEUN) {
+        // CIR gradient update (Sec. 4): Dv at the foot at time t (stage coefficients 1),
+        // Dv at the node at t + dt (the trace's first stage, evaluated again)
+        const V2p Df = vel2d_pair<VK>(vp, sc, scp, 1, add2(x, dx), add2(y, dy));
+        const V2p Dn = (VK == VK_FOURIER2D && a1 != nullptr) ? *a1 : stage1_pair<VK>(vp, sc, scp, x, y, cx, ry);
+        heun_psi2(Df, Dn, dt, Hx, Hy, px, py);
+        return;
+    }
     px = fma2(J[0], Hx, mul2(J[2], Hy));  // (J^T grad H)_x
     py = fma2(J[1], Hx, mul2(J[3], Hy));  // (J^T grad H)_y
 }

@@ -256,9 +256,16 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
             }, H, gr);
         }
         F2 psi[3];
+        if (TR == TR_HEUN) {
+            // CIR gradient update (Sec. 4): Dv at the foot at time t, Dv at the node at t + dt
+            const V3p Df = vel3d_pair<VK>(vp, sc, 1, add2(X, d[0]), add2(Y, d[1]), add2(Z, d[2]));
+            const V3p Dn = stage1_pair<VK>(vp, sc, pre, X, Y, Z);
+            heun_psi3(Df, Dn, dt, gr, psi);
+        } else {
 #pragma unroll
-        for (int a = 0; a < 3; ++a)  // (J^T grad H)_a = sum_b J[b][a] dH/dx_b
-            psi[a] = fma2(J[a], gr[0], fma2(J[3 + a], gr[1], mul2(J[6 + a], gr[2])));
+            for (int a = 0; a < 3; ++a)  // (J^T grad H)_a = sum_b J[b][a] dH/dx_b
+                psi[a] = fma2(J[a], gr[0], fma2(J[3 + a], gr[1], mul2(J[6 + a], gr[2])));
+        }
         if (!valid) continue;
         const int64_t o = (int64_t)kz * zstride + (int64_t)j * g.pitch + i;
         out[o] = H.x;
@@ -384,6 +391,7 @@ cudaError_t launch_cr(const StepLaunch &a, cudaStream_t s)
 template <int VK>
 cudaError_t launch_tr(const StepLaunch &a, cudaStream_t s)
 {
+    if (a.trace == TR_HEUN) return launch_cr<TR_HEUN, VK>(a, s);
     return a.trace == TR_EULER ? launch_cr<TR_EULER, VK>(a, s) : launch_cr<TR_RK3, VK>(a, s);
 }
 

@@ -32,7 +32,8 @@ gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char 
 {
     std::memset(&vp, 0, sizeof(vp));
     if (!v) return vfail(msg, len, GALS_ERR_ARG, "velocity descriptor is NULL");
-    if (v->trace != GALS_TRACE_EULER && v->trace != GALS_TRACE_RK3 && v->trace != GALS_TRACE_SURROGATE)
+    if (v->trace != GALS_TRACE_EULER && v->trace != GALS_TRACE_RK3 && v->trace != GALS_TRACE_SURROGATE &&
+        v->trace != GALS_TRACE_HEUN_PSI)
         return vfail(msg, len, GALS_ERR_ARG, "unknown trace scheme %d", v->trace);
     if (!vel_supported(dim, v->kind))
         return vfail(msg, len, GALS_ERR_UNSUPPORTED, "velocity kind %d not available in %dD", v->kind, dim);

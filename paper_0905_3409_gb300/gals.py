@@ -22,7 +22,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE, ERR_UNS
 MEM_HOST, MEM_DEVICE = 0, 1
 LAYOUT_FULL, LAYOUT_COMPACT = 0, 1
 VEL = {"const": 0, "rotation": 1, "vortex2d": 2, "deform3d": 3, "pseudo1d": 4, "fourier2d": 5}
-TRACE = {"euler": 0, "rk3": 1, "surrogate": 2}
+TRACE = {"euler": 0, "rk3": 1, "surrogate": 2, "heun_psi": 3}
 SET_RECON_CROSS = 1
 MAX_MODES = 64
 

@@ -93,7 +93,7 @@ def test_ragged_sizes_vortex(gals, n, layout):
                recon=True, T=8.0)
 
 
-@pytest.mark.parametrize("trace", ["rk3", "euler"])
+@pytest.mark.parametrize("trace", ["rk3", "euler", "heun_psi"])
 def test_rotation_slotted_disk(gals, trace):
     n = (96, 96)
     st = inputs.slotted_disk_sdf(n)
@@ -108,12 +108,24 @@ def test_pseudo1d_gaussian_rectangular_cells(gals):
     check_step(gals, n, st, "pseudo1d", 0.01, steps=2, lo=lo, hi=hi)
 
 
-def test_fourier_time_periodic(gals):
+@pytest.mark.parametrize("trace", ["rk3", "heun_psi"])
+def test_fourier_time_periodic(gals, trace):
     n = (80, 80)
     modes = inputs.fourier_modes(16, seed=5, periodic=True)
     st = inputs.ellipse_sdf(n, (0.5, 0.5), 0.2, 0.1, 0.4)
     vmax = inputs.fourier_speed_bound(modes)
-    check_step(gals, n, st, "fourier2d", (1.0 / 79) / vmax, t0=0.3, steps=2, recon=True, modes=modes)
+    check_step(gals, n, st, "fourier2d", (1.0 / 79) / vmax, t0=0.3, steps=2, recon=True, modes=modes,
+               trace=trace)
+
+
+@pytest.mark.parametrize("layout", ["full", "compact"])
+def test_vortex_heun_psi(gals, layout):
+    """The CIR form with Heun's method for the gradients (time-dependent field: the foot's
+    velocity gradient is taken at time t, the node's at t + dt)."""
+    n = (67, 45)
+    st = inputs.circle_sdf(n, center=(0.45, 0.55), r=0.3)
+    check_step(gals, n, st, "vortex2d", 0.8 / 66, t0=0.9, steps=2, layout=layout, trace="heun_psi",
+               recon=True, T=8.0)
 
 
 def test_random_state_high_cfl(gals):
@@ -133,6 +145,14 @@ def test_random_state_high_cfl(gals):
 def test_3d_deform(gals, n, layout):
     st = inputs.sphere_sdf(n, center=(0.4, 0.45, 0.5), r=0.25)
     check_step(gals, n, st, "deform3d", 0.5 / (max(n) - 1), t0=0.2, steps=2, layout=layout,
+               recon=True, T=3.0)
+
+
+@pytest.mark.parametrize("layout", ["full", "compact"])
+def test_3d_deform_heun_psi(gals, layout):
+    n = (19, 17, 16)
+    st = inputs.sphere_sdf(n, center=(0.45, 0.5, 0.5), r=0.25)
+    check_step(gals, n, st, "deform3d", 0.5 / 18, t0=0.4, steps=2, layout=layout, trace="heun_psi",
                recon=True, T=3.0)
 
 
