@@ -27,7 +27,8 @@ _lib = None
 # enums of gals_oracle.h
 VEL_CONST, VEL_ROTATION, VEL_VORTEX2D, VEL_DEFORM3D, VEL_PSEUDO1D, VEL_FOURIER2D = range(6)
 TRACE_EULER, TRACE_RK3, TRACE_HEUN_PSI = 0, 1, 2
-CROSS_CENTRAL, CROSS_ZERO = 0, 1
+CROSS_CENTRAL, CROSS_ZERO, CROSS_CELL = 0, 1, 2
+_CROSS_NAMES = {"central": CROSS_CENTRAL, "zero": CROSS_ZERO, "cell": CROSS_CELL}
 
 _VEL_NAMES = {
     "const": VEL_CONST, "rotation": VEL_ROTATION, "vortex2d": VEL_VORTEX2D,
@@ -81,8 +82,9 @@ def lib():
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp]
             L.orc_recon_cross.argtypes = [ctypes.POINTER(_Grid), pp]
             L.orc_node_update.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Velocity),
-                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, pp,
-                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, pp, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, dp, dp]
             L.orc_step.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Velocity), ctypes.c_int,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, pp, pp,
                                    ctypes.c_int]
@@ -248,7 +250,7 @@ def step(g, vel, state, t, dt, trace_scheme="rk3", cross="central", nthreads=Non
     ins = _state_list(state, g)
     outs = [np.empty_like(p) for p in ins]
     lib().orc_step(ctypes.byref(g), ctypes.byref(vel), _TRACE_NAMES[trace_scheme],
-                   CROSS_CENTRAL if cross == "central" else CROSS_ZERO, float(t), float(dt),
+                   _CROSS_NAMES[cross], float(t), float(dt),
                    _planes_ptr(ins), _planes_ptr(outs),
                    default_threads() if nthreads is None else int(nthreads))
     return np.stack(outs).reshape(shape)
@@ -261,7 +263,7 @@ def step_nodes(g, vel, state, t, dt, nodes, trace_scheme="rk3", cross="central",
     sel = np.ascontiguousarray(nodes, dtype=np.int64)
     out = np.zeros((sel.size, nplanes(g.dim)))
     lib().orc_step_nodes(ctypes.byref(g), ctypes.byref(vel), _TRACE_NAMES[trace_scheme],
-                         CROSS_CENTRAL if cross == "central" else CROSS_ZERO, float(t),
+                         _CROSS_NAMES[cross], float(t),
                          float(dt), _planes_ptr(ins), sel.size,
                          sel.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out),
                          default_threads() if nthreads is None else int(nthreads))
@@ -277,7 +279,7 @@ def step_band(g, vel, state, t, dt, b0, b1, trace_scheme="rk3", cross="central",
     inner = (g.n[0],) if g.dim == 2 else (g.n[1], g.n[0])
     outs = [np.empty((b1 - b0) * int(np.prod(inner))) for _ in ins]
     lib().orc_step_band(ctypes.byref(g), ctypes.byref(vel), _TRACE_NAMES[trace_scheme],
-                        CROSS_CENTRAL if cross == "central" else CROSS_ZERO, float(t), float(dt),
+                        _CROSS_NAMES[cross], float(t), float(dt),
                         _planes_ptr(ins), int(b0), int(b1), _planes_ptr(outs),
                         default_threads() if nthreads is None else int(nthreads))
     return np.stack(outs).reshape((len(ins), b1 - b0) + inner)
@@ -293,7 +295,7 @@ def run(g, vel, state, t0, dt, nsteps, trace_scheme="rk3", cross="central", nthr
     st = [p.copy() for p in _state_list(state, g)]  # never write into the caller's array
     scratch = [np.empty_like(p) for p in st]
     lib().orc_run(ctypes.byref(g), ctypes.byref(vel), _TRACE_NAMES[trace_scheme],
-                  CROSS_CENTRAL if cross == "central" else CROSS_ZERO, float(t0), float(dt),
+                  _CROSS_NAMES[cross], float(t0), float(dt),
                   int(nsteps), _planes_ptr(st), _planes_ptr(scratch),
                   default_threads() if nthreads is None else int(nthreads))
     return np.stack(st).reshape(shape)

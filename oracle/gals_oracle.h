@@ -44,7 +44,15 @@ enum {
  * forward from (foot, t) to (node, t + dt) by one step of Heun's method (explicit
  * trapezoidal rule). */
 enum { ORC_TRACE_EULER = 0, ORC_TRACE_RK3 = 1, ORC_TRACE_HEUN_PSI = 2 };
-enum { ORC_CROSS_CENTRAL = 0, ORC_CROSS_ZERO = 1 };
+/* Cross derivatives of the interpolation data (Sec. 2.3):
+ * CENTRAL: approach (A), node values rebuilt from the new gradients after every step;
+ * ZERO: zero cross planes after the step (tests only);
+ * CELL: approach (B), computed per cell from the gradients at the cell's own vertices
+ *   (edge-centre differences extrapolated to each vertex with weights 3/4, 3/4, -1/4,
+ *   -1/4; in 3D within the vertex's facet of the cell; phi_xyz from the double difference
+ *   of psi_z over the vertex's x-y facet).  No node value exists, so the state's cross
+ *   planes are zero after a step. */
+enum { ORC_CROSS_CENTRAL = 0, ORC_CROSS_ZERO = 1, ORC_CROSS_CELL = 2 };
 
 typedef struct {
     int kind;
@@ -92,9 +100,14 @@ void orc_recon_cross(const orc_grid *g, double *const *planes);
 
 /* one node of the step: new phi and psi at node (i,j,k) from the old state
  * (steps 1-2 of Sec. 4 with the superconsistent update, eq. superconsistency) */
-void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace,
+void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
                      double t, double dt, const double *const *in,
                      int i, int j, int k, double *phi, double psi[3]);
+
+/* approach (B): replace the cross entries of a cell's gathered data (data[v * 2^p + a],
+ * vertex v = vx + 2 vy + 4 vz, derivative multi-index a, bit i = d/dx_i) by the
+ * cell-based approximations from the same data's gradient entries */
+void orc_cross_cell(int dim, const double *h, double *data);
 
 /* full step t -> t+dt over all nodes, then cross reconstruction (M = P A, Sec. 5.2) */
 void orc_step(const orc_grid *g, const orc_velocity *vel, int trace, int cross,

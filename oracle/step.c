@@ -53,7 +53,57 @@ static long total_nodes(const orc_grid *g)
     return N;
 }
 
-void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace,
+/* phi_xy-type value at vertex (u, w) of a 2D facet from its four edge-centre differences:
+ * eu[0], eu[1] along the second axis at first-axis index 0, 1 and ew[0], ew[1] along the
+ * first axis at second-axis index 0, 1 (Sec. 2.3 (B), weights 3/4 near, -1/4 opposite) */
+static double cell_vertex(const double eu[2], const double ew[2], int u, int w)
+{
+    return 0.75 * (eu[u] + ew[w]) - 0.25 * (eu[1 - u] + ew[1 - w]);
+}
+
+void orc_cross_cell(int dim, const double *h, double *data)
+{
+    if (dim == 2) {
+        /* psi_x differenced along y at x-index u; psi_y differenced along x at y-index w */
+        double eu[2], ew[2];
+        for (int u = 0; u < 2; ++u) eu[u] = (data[(u + 2) * 4 + 1] - data[u * 4 + 1]) / h[1];
+        for (int w = 0; w < 2; ++w) ew[w] = (data[(1 + 2 * w) * 4 + 2] - data[(2 * w) * 4 + 2]) / h[0];
+        for (int v = 0; v < 4; ++v) data[v * 4 + 3] = cell_vertex(eu, ew, v & 1, (v >> 1) & 1);
+        return;
+    }
+    /* 3D: entry of corner (a, b, c) and derivative index d */
+#define D3(a, b, c, d) data[((a) + 2 * (b) + 4 * (c)) * 8 + (d)]
+    double xy[8], xz[8], yz[8], xyz[8];
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a) {
+                double eu[2], ew[2];
+                /* x-y facet at z-index c: psi_x along y at x = u, psi_y along x at y = w */
+                for (int u = 0; u < 2; ++u) eu[u] = (D3(u, 1, c, 1) - D3(u, 0, c, 1)) / h[1];
+                for (int w = 0; w < 2; ++w) ew[w] = (D3(1, w, c, 2) - D3(0, w, c, 2)) / h[0];
+                xy[a + 2 * b + 4 * c] = cell_vertex(eu, ew, a, b);
+                /* x-z facet at y-index b: psi_x along z at x = u, psi_z along x at z = w */
+                for (int u = 0; u < 2; ++u) eu[u] = (D3(u, b, 1, 1) - D3(u, b, 0, 1)) / h[2];
+                for (int w = 0; w < 2; ++w) ew[w] = (D3(1, b, w, 4) - D3(0, b, w, 4)) / h[0];
+                xz[a + 2 * b + 4 * c] = cell_vertex(eu, ew, a, c);
+                /* y-z facet at x-index a: psi_y along z at y = u, psi_z along y at z = w */
+                for (int u = 0; u < 2; ++u) eu[u] = (D3(a, u, 1, 2) - D3(a, u, 0, 2)) / h[2];
+                for (int w = 0; w < 2; ++w) ew[w] = (D3(a, 1, w, 4) - D3(a, 0, w, 4)) / h[1];
+                yz[a + 2 * b + 4 * c] = cell_vertex(eu, ew, b, c);
+                /* psi_z double difference over the x-y facet at z-index c */
+                xyz[a + 2 * b + 4 * c] = (D3(1, 1, c, 4) - D3(0, 1, c, 4) - D3(1, 0, c, 4) + D3(0, 0, c, 4)) /
+                                         (h[0] * h[1]);
+            }
+    for (int v = 0; v < 8; ++v) {
+        data[v * 8 + 3] = xy[v];
+        data[v * 8 + 5] = xz[v];
+        data[v * 8 + 6] = yz[v];
+        data[v * 8 + 7] = xyz[v];
+    }
+#undef D3
+}
+
+void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
                      double t, double dt, const double *const *in,
                      int i, int j, int k, double *phi, double psi[3])
 {
@@ -90,6 +140,7 @@ void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace,
         long nid = node_index(g, ci, cj, ck);
         for (int a = 0; a < np; ++a) data[v * np + a] = in[plane_of(dim, a)][nid];
     }
+    if (cross == ORC_CROSS_CELL && dim >= 2) orc_cross_cell(dim, g->h, data);
     double H, gradH[3] = {0, 0, 0};
     orc_hermite_cell(dim, data, g->h, xi, &H, gradH);
 
@@ -212,14 +263,14 @@ void orc_step(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
         int k = (int)(r / ny), j = (int)(r % ny);
         for (int i = 0; i < g->n[0]; ++i) {
             double phi, psi[3];
-            orc_node_update(g, vel, trace, t, dt, in, i, j, k, &phi, psi);
+            orc_node_update(g, vel, trace, cross, t, dt, in, i, j, k, &phi, psi);
             long id = node_index(g, i, j, k);
             out[0][id] = phi;
             for (int a = 0; a < dim; ++a) out[1 + a][id] = psi[a];
         }
     }
     if (dim == 1) return;
-    if (cross == ORC_CROSS_ZERO) {
+    if (cross == ORC_CROSS_ZERO || cross == ORC_CROSS_CELL) {
         long N = total_nodes(g);
         int first = dim == 2 ? 3 : 4, nc = dim == 2 ? 1 : 4;
         for (int c = 0; c < nc; ++c) memset(out[first + c], 0, N * sizeof(double));
@@ -238,7 +289,7 @@ static double get_updated(void *vctx, int plane, int i, int j, int k)
 {
     upd_ctx *c = (upd_ctx *)vctx;
     double phi, psi[3];
-    orc_node_update(c->g, c->vel, c->trace, c->t, c->dt, c->in, i, j, k, &phi, psi);
+    orc_node_update(c->g, c->vel, c->trace, ORC_CROSS_CENTRAL, c->t, c->dt, c->in, i, j, k, &phi, psi);
     return plane == 0 ? phi : psi[plane - 1];
 }
 
@@ -258,14 +309,14 @@ void orc_step_nodes(const orc_grid *g, const orc_velocity *vel, int trace, int c
         int j = dim >= 2 ? (int)((id / g->n[0]) % g->n[1]) : 0;
         int k = dim == 3 ? (int)(id / ((long)g->n[0] * g->n[1])) : 0;
         double phi, psi[3];
-        orc_node_update(g, vel, trace, t, dt, in, i, j, k, &phi, psi);
+        orc_node_update(g, vel, trace, cross, t, dt, in, i, j, k, &phi, psi);
         double *o = outv + s * np;
         o[0] = phi;
         for (int a = 0; a < dim; ++a) o[1 + a] = psi[a];
         if (dim == 1) continue;
         int first = dim == 2 ? 3 : 4, nc = dim == 2 ? 1 : 4;
         double cr[4] = {0, 0, 0, 0};
-        if (cross != ORC_CROSS_ZERO) {
+        if (cross == ORC_CROSS_CENTRAL) {
             upd_ctx ctx = {g, vel, trace, t, dt, in};
             cross_at(g, get_updated, &ctx, i, j, k, cr);
         }
@@ -321,7 +372,7 @@ void orc_step_band(const orc_grid *g, const orc_velocity *vel, int trace, int cr
         int j = dim == 2 ? outer : jj, k = dim == 2 ? 0 : outer;
         for (int i = 0; i < g->n[0]; ++i) {
             double phi, psi[3];
-            orc_node_update(g, vel, trace, t, dt, in, i, j, k, &phi, psi);
+            orc_node_update(g, vel, trace, cross, t, dt, in, i, j, k, &phi, psi);
             long id = r * g->n[0] + i;
             out[0][id] = phi;
             for (int a = 0; a < dim; ++a) out[1 + a][id] = psi[a];
@@ -334,7 +385,7 @@ void orc_step_band(const orc_grid *g, const orc_velocity *vel, int trace, int cr
         int j = dim == 2 ? outer : jj, k = dim == 2 ? 0 : outer;
         for (int i = 0; i < g->n[0]; ++i) {
             double cr[4] = {0, 0, 0, 0};
-            if (cross != ORC_CROSS_ZERO) cross_at(g, get_band, &ctx, i, j, k, cr);
+            if (cross == ORC_CROSS_CENTRAL) cross_at(g, get_band, &ctx, i, j, k, cr);
             long id = r * g->n[0] + i;
             for (int c = 0; c < nc; ++c) out[first + c][id] = cr[c];
         }
