@@ -61,7 +61,7 @@ class _Velocity(ctypes.Structure):
 
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
-                ("h", ctypes.c_double * 3)]
+                ("h", ctypes.c_double * 3), ("cross", ctypes.c_int)]
 
 
 def lib():
@@ -162,13 +162,16 @@ def velocity(kind: str, T: float = 1.0, omega: float = 0.0, center=(0.5, 0.5, 0.
     return v
 
 
-def grid(n, lo=None, hi=None):
-    """Grid of ``n`` nodes per axis on [lo, hi] (both ends are nodes)."""
+def grid(n, lo=None, hi=None, cross="central"):
+    """Grid of ``n`` nodes per axis on [lo, hi] (both ends are nodes).  ``cross``: the
+    cross derivatives the diagnostics' interpolant uses ("central": the stored planes,
+    "cell": approach (B) per cell)."""
     dim = len(n)
     lo = [0.0] * dim if lo is None else list(lo)
     hi = [1.0] * dim if hi is None else list(hi)
     g = _Grid()
     g.dim = dim
+    g.cross = _CROSS_NAMES[cross]
     for i in range(3):
         g.n[i] = int(n[i]) if i < dim else 1
         g.lo[i] = float(lo[i]) if i < dim else 0.0

@@ -50,6 +50,7 @@ static void gather_cell(const orc_grid *g, const double *const *planes, const in
         long nid = node_index(g, ci, cj, ck);
         for (int a = 0; a < np; ++a) data[v * np + a] = planes[plane_of(dim, a)][nid];
     }
+    if (g->cross == ORC_CROSS_CELL && dim >= 2) orc_cross_cell(dim, g->h, data);
 }
 
 /* loop over the cells; for each, the q^p samples; accumulate per sample:

@@ -69,6 +69,8 @@ typedef struct {
     int n[3];
     double lo[3];
     double h[3];
+    int cross;         /* cross derivatives the diagnostics' interpolant uses: ORC_CROSS_CENTRAL
+                          (the stored planes) or ORC_CROSS_CELL (approach B, per cell) */
 } orc_grid;
 
 /* 1-cubic basis (eq. 1-cubic_basis_functions): w[v*2+a](xi) and d/dxi */

@@ -374,3 +374,29 @@ def test_cross_cell_converges_to_central():
         inner = (slice(4, -4), slice(4, -4))
         diffs.append(np.max(np.abs(a[0][inner] - b[0][inner])))
     assert diffs[0] / diffs[1] >= 8.0, diffs
+
+
+def test_cross_cell_diagnostics():
+    """The diagnostics of a grid using approach (B) sample the cell-based interpolant: for
+    a p-cubic with linear mixed derivatives it is exact, so the sampled area of {phi < c}
+    matches that of the exact data with approach (A); with zero cross planes and
+    approach (A) it does not."""
+    n = (33, 33)
+    st, f = _poly_state(n, 2)
+    st = st.copy()
+    st[0] -= 0.3
+    ga = oracle.grid(n)
+    gb = oracle.grid(n, cross="cell")
+    exact = oracle.recon_cross(ga, st)      # exact cross planes of the polynomial (A is exact here)
+    area_a = oracle.measure_negative(ga, exact, 4)
+    area_b = oracle.measure_negative(gb, st, 4)  # cross planes zero, rebuilt per cell
+    assert area_b == area_a
+    # pointwise: the cell-based interpolant equals the exact one; zero cross planes do not
+    pts = np.random.default_rng(3).uniform(0.0, 1.0, (200, 2))
+    ha, _ = oracle.eval_points(ga, exact, pts)
+    hb, _ = oracle.eval_points(gb, st, pts)
+    hz, _ = oracle.eval_points(ga, st, pts)
+    x, y = pts[:, 0], pts[:, 1]
+    want = f(x, y)[0] - 0.3
+    assert np.max(np.abs(hb - want)) < 1e-13 and np.max(np.abs(ha - want)) < 1e-13
+    assert np.max(np.abs(hz - want)) > 1e-6
