@@ -64,8 +64,19 @@ typedef struct {
     double lo[3];       /* domain [lo, hi] per axis; node spacing h = (hi - lo)/(n - 1) */
     double hi[3];
     int layout;         /* GALS_LAYOUT_FULL (default 0) or GALS_LAYOUT_COMPACT */
+    int cross_scheme;   /* GALS_CROSS_CENTRAL (default 0) or GALS_CROSS_CELL */
     void *cuda_stream;  /* cudaStream_t to order work on, or NULL for a library-owned stream */
 } gals_grid_desc;
+
+/* Mixed derivatives of the interpolation data (Sec. 2.3).  CENTRAL, approach (A): node
+ * values by central differences of the gradients (one-sided at the box edges), rebuilt
+ * after every step.  CELL, approach (B): computed inside each cell from the gradients at
+ * its vertices (edge-centre differences, vertex weights 3/4, 3/4, -1/4, -1/4; in 3D
+ * within each vertex's facet, phi_xyz from the double difference of psi_z over the
+ * vertex's x-y facet); a node has no single value, so the state's mixed-derivative planes
+ * are zero (set_state ignores given ones) and the step reads and writes phi and psi only.
+ * The diagnostics sample the interpolant of the grid's scheme. */
+enum { GALS_CROSS_CENTRAL = 0, GALS_CROSS_CELL = 1 };
 
 /* Analytic velocity fields v(x, t) with exactly known Jacobian (Sec. 4 assumes both
  * "exactly accessible everywhere").  Coordinates are physical (not index) units. */

@@ -42,6 +42,7 @@ struct gals_grid {
     int n[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
     int layout = GALS_LAYOUT_FULL;
+    int cross = GALS_CROSS_CENTRAL;   // mixed derivatives: approach A (planes) or B (per cell)
     int nplanes = 0;
     Geom geom{};
     float *buf[2] = {nullptr, nullptr};
@@ -131,7 +132,10 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
                   : trace == GALS_TRACE_SURROGATE ? TR_GIVEN
                   : trace == GALS_TRACE_HEUN_PSI  ? TR_HEUN
                                                   : TR_RK3;
-        if (g->layout == GALS_LAYOUT_FULL) {
+        if (g->cross == GALS_CROSS_CELL) {
+            a.cross_in = CROSS_CELL;  // approach B: mixed derivatives per cell, none stored
+            a.write_cross = 0;
+        } else if (g->layout == GALS_LAYOUT_FULL) {
             a.cross_in = CROSS_PLANE;
             a.write_cross = 1;
         } else {
@@ -171,6 +175,8 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
     if (d->dim != 2 && d->dim != 3) return fail(nullptr, GALS_ERR_ARG, "dim must be 2 or 3");
     if (d->layout != GALS_LAYOUT_FULL && d->layout != GALS_LAYOUT_COMPACT)
         return fail(nullptr, GALS_ERR_ARG, "unknown layout %d", d->layout);
+    if (d->cross_scheme != GALS_CROSS_CENTRAL && d->cross_scheme != GALS_CROSS_CELL)
+        return fail(nullptr, GALS_ERR_ARG, "unknown cross scheme %d", d->cross_scheme);
     for (int i = 0; i < d->dim; ++i) {
         if (d->n[i] < 4) return fail(nullptr, GALS_ERR_ARG, "n[%d] = %d < 4", i, d->n[i]);
         if (!std::isfinite(d->lo[i]) || !std::isfinite(d->hi[i]) || !(d->hi[i] > d->lo[i]))
@@ -185,6 +191,7 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
     if (!g) return fail(nullptr, GALS_ERR_NOMEM, "host allocation failed");
     g->dim = d->dim;
     g->layout = d->layout;
+    g->cross = d->cross_scheme;
     g->nplanes = full_planes(d->dim);
     for (int i = 0; i < 3; ++i) {
         g->n[i] = i < d->dim ? d->n[i] : 1;
@@ -316,10 +323,15 @@ gals_status gals_set_state(gals_grid *g, const float *const *fields, int nfields
         if (e != cudaSuccess) return cuda_fail(g, e, "set_state copy");
     }
     const bool recon = nfields == core || (flags & GALS_SET_RECON_CROSS);
-    if (recon) {
+    if (g->cross == GALS_CROSS_CELL) {
+        // approach B keeps no node values of the mixed derivatives
+        for (int p = core; p < g->nplanes; ++p)
+            if ((e = cudaMemsetAsync(dst + p * G.plane, 0, sizeof(float) * (size_t)G.plane, g->stream)) != cudaSuccess)
+                return cuda_fail(g, e, "set_state zero");
+    } else if (recon) {
         if ((e = launch_recon(g->dim, G, dst, g->stream)) != cudaSuccess) return cuda_fail(g, e, "recon");
     }
-    g->cross_explicit = (g->layout == GALS_LAYOUT_COMPACT) && !recon;
+    g->cross_explicit = (g->layout == GALS_LAYOUT_COMPACT) && !recon && g->cross != GALS_CROSS_CELL;
     g->t = t0;
     g->steps = 0;
     if ((e = cudaMemcpyAsync(g->t_dev, &g->t, sizeof(double), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
@@ -440,7 +452,7 @@ static gals_status ensure_cross(gals_grid *g)
 {
     // COMPACT layout: the mixed derivatives of the current state are not stored by the
     // step; rebuild them (unless set_state just provided them explicitly).
-    if (g->layout == GALS_LAYOUT_COMPACT && !g->cross_explicit) {
+    if (g->layout == GALS_LAYOUT_COMPACT && !g->cross_explicit && g->cross != GALS_CROSS_CELL) {
         cudaError_t e = launch_recon(g->dim, g->geom, g->buf[g->cur], g->stream);
         if (e != cudaSuccess) return cuda_fail(g, e, "recon");
     }
@@ -503,13 +515,14 @@ gals_status gals_diagnostics(gals_grid *g, const gals_diag_request *req, gals_di
     if (r) {
         // the reference is read on this grid's stream: order after its own work
         if ((e = cudaStreamSynchronize(r->stream)) != cudaSuccess) return cuda_fail(g, e, "reference sync");
-        if (r->layout == GALS_LAYOUT_COMPACT && !r->cross_explicit) {
+        if (r->layout == GALS_LAYOUT_COMPACT && !r->cross_explicit && r->cross != GALS_CROSS_CELL) {
             if ((e = launch_recon(r->dim, r->geom, r->buf[r->cur], g->stream)) != cudaSuccess)
                 return cuda_fail(g, e, "reference recon");
         }
     }
     e = launch_diag(g->dim, g->geom, g->buf[g->cur], r ? r->buf[r->cur] : nullptr, req->q, g->diag_dev,
-                    g->diag_partials, g->stream);
+                    g->diag_partials, g->stream, g->cross == GALS_CROSS_CELL,
+                    r && r->cross == GALS_CROSS_CELL);
     if (e != cudaSuccess) return cuda_fail(g, e, "diagnostics launch");
     DiagOut h;
     if ((e = cudaMemcpyAsync(&h, g->diag_dev, sizeof(h), cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess)

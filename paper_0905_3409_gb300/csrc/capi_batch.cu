@@ -205,6 +205,8 @@ gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch
             if (!std::isfinite(d.lo[i]) || !std::isfinite(d.hi[i]) || !(d.hi[i] > d.lo[i]))
                 return bfail(nullptr, GALS_ERR_ARG, "problem %d: need finite lo < hi", p);
         }
+        if (d.cross_scheme != GALS_CROSS_CENTRAL)
+            return bfail(nullptr, GALS_ERR_ARG, "problem %d: the batched mode uses approach (A)", p);
         char msg[160];
         const int n3[3] = {d.n[0], d.n[1], 1};
         if (!grid_size_ok(2, n3, msg, sizeof(msg)))

@@ -65,11 +65,23 @@ __device__ __forceinline__ unsigned block_max(unsigned v, unsigned *red)
     return s;
 }
 
-// One thread per cell: q^p cell-centred samples of H (state a) and of the reference b.
+// approach B for a gathered 3D cell (planes 0 phi, 1-3 psi, 4-7 mixed derivatives)
+__device__ __forceinline__ void cell3d_planes(float c[8][8], const Geom &g)
+{
+    float cr[8][4];
+    cross_cell3d([&](int v, int a) { return c[v][a]; }, g.ih0, g.ih1, g.ih2, cr);
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[v][4 + i] = cr[v][i];
+}
+
+// One thread per cell: q^p cell-centred samples of H (state a) and of the reference b;
+// cell_a / cell_b: that state's interpolant takes its mixed derivatives by approach B.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads)
 k_diag_cells(Geom g, const float *__restrict__ a, const float *__restrict__ b, int q,
-             DiagOut *out)
+             DiagOut *out, int cell_a, int cell_b)
 {
     __shared__ unsigned long long red[kThreads / 32];
     const int64_t nc0 = g.n0 - 1, nc1 = g.n1 - 1, nc2 = DIM == 3 ? g.n2 - 1 : 1;
@@ -85,6 +97,9 @@ k_diag_cells(Geom g, const float *__restrict__ a, const float *__restrict__ b, i
             float ca[4][4], cb[4][4];
             gather2d(a, g, k, l, ca);
             if (b) gather2d(b, g, k, l, cb);
+            // approach B: the cell's mixed derivatives from its vertices' gradients
+            if (cell_a) cross_cell2d(ca, g.ih0, g.ih1);
+            if (b && cell_b) cross_cell2d(cb, g.ih0, g.ih1);
             for (int sy = 0; sy < q; ++sy) {
                 const Basis1 by = basis1(((float)sy + 0.5f) * invq, g.h1, g.ih1);
                 for (int sx = 0; sx < q; ++sx) {
@@ -103,6 +118,8 @@ k_diag_cells(Geom g, const float *__restrict__ a, const float *__restrict__ b, i
             float ca[8][8], cb[8][8];
             gather3d(a, g, k, l, m, ca);
             if (b) gather3d(b, g, k, l, m, cb);
+            if (cell_a) cell3d_planes(ca, g);
+            if (b && cell_b) cell3d_planes(cb, g);
             for (int sz = 0; sz < q; ++sz) {
                 const Basis1 bz = basis1(((float)sz + 0.5f) * invq, g.h2, g.ih2);
                 for (int sy = 0; sy < q; ++sy) {
@@ -184,15 +201,15 @@ __global__ void k_diag_finish(const double *partials, int nparts, DiagOut *out)
 int diag_partials_needed() { return kNodeBlocks; }
 
 cudaError_t launch_diag(int dim, const Geom &g, const float *a, const float *b, int q,
-                        DiagOut *counters, double *partials, cudaStream_t s)
+                        DiagOut *counters, double *partials, cudaStream_t s, bool cell_a, bool cell_b)
 {
     cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(DiagOut), s);
     if (e != cudaSuccess) return e;
     if (q > 0) {
         const int64_t ncell = (int64_t)(g.n0 - 1) * (g.n1 - 1) * (dim == 3 ? g.n2 - 1 : 1);
         int blocks = (int)std::min<int64_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
-        if (dim == 2) k_diag_cells<2><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters);
-        else k_diag_cells<3><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters);
+        if (dim == 2) k_diag_cells<2><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters, cell_a, cell_b);
+        else k_diag_cells<3><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters, cell_a, cell_b);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_diag_nodes<<<kNodeBlocks, kThreads, 0, s>>>(g, dim, a, b, counters, partials);
@@ -209,8 +226,8 @@ cudaError_t launch_diag_with(int dim, const Geom &g, const float *a, const float
     if (q > 0) {
         const int64_t ncell = (int64_t)(g.n0 - 1) * (g.n1 - 1) * (dim == 3 ? g.n2 - 1 : 1);
         int blocks = (int)std::min<int64_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
-        if (dim == 2) k_diag_cells<2><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters);
-        else k_diag_cells<3><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters);
+        if (dim == 2) k_diag_cells<2><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters, 0, 0);
+        else k_diag_cells<3><<<blocks, kThreads, 0, s>>>(g, a, b, q, counters, 0, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     k_diag_nodes<<<nparts, kThreads, 0, s>>>(g, dim, a, b, counters, partials);

@@ -34,7 +34,10 @@ enum VelKind { VK_CONST = 0, VK_ROTATION = 1, VK_VORTEX2D = 2, VK_DEFORM3D = 3,
 // GIVEN: precomputed (surrogate); HEUN: RK3 foot, gradients by Heun's method along the
 // characteristic (Sec. 4, CIR form)
 enum TraceKind { TR_EULER = 0, TR_RK3 = 1, TR_GIVEN = 2, TR_HEUN = 3 };
-enum CrossSrc { CROSS_PLANE = 0, CROSS_RECON = 1 };
+// Where a cell's mixed derivatives come from: the stored planes (approach A, FULL), the
+// psi windows around the cell (approach A, COMPACT), or the cell's own gradients
+// (approach B of Sec. 2.3).
+enum CrossSrc { CROSS_PLANE = 0, CROSS_RECON = 1, CROSS_CELL = 2 };
 
 // Velocity descriptor as passed to kernels (by value).
 struct VelParams {
@@ -445,6 +448,49 @@ __device__ __forceinline__ void hermite3d(const float c[8][8], const Basis1 &bx,
     g[2] = hder(bz, R[0], R[1], Rz[0], Rz[1]);
     g[0] = hval(bz, Rx[0], Rx[1], Rzx[0], Rzx[1]);
     g[1] = hval(bz, Ry[0], Ry[1], Rzy[0], Rzy[1]);
+}
+
+// ---------------------------------------------------------------- approach B (cell-based)
+
+// Vertex (u, w) of a facet from its edge-centre differences e (along the facet's second
+// axis, at first-axis index 0, 1) and f (along the first axis, at second-axis index 0, 1):
+// 3/4 of the two edges through the vertex, -1/4 of the two opposite ones (Sec. 2.3 (B)).
+__device__ __forceinline__ float cell_vertex(float e0, float e1, float f0, float f1, int u, int w)
+{
+    const float ne = u ? e1 : e0, fe = u ? e0 : e1, nf = w ? f1 : f0, ff = w ? f0 : f1;
+    return 0.75f * (ne + nf) - 0.25f * (fe + ff);
+}
+
+// 2D cell, c[v][a] (v = vx + 2 vy; a = 0 phi, 1 phi_x, 2 phi_y, 3 phi_xy): phi_xy at the
+// four vertices from psi_x differenced along y and psi_y differenced along x.
+__device__ __forceinline__ void cross_cell2d(float c[4][4], float ih0, float ih1)
+{
+    const float e0 = (c[2][1] - c[0][1]) * ih1, e1 = (c[3][1] - c[1][1]) * ih1;
+    const float f0 = (c[1][2] - c[0][2]) * ih0, f1 = (c[3][2] - c[2][2]) * ih0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) c[v][3] = cell_vertex(e0, e1, f0, f1, v & 1, v >> 1);
+}
+
+// 3D cell: q(v, a) gives phi (a = 0) and psi_x, psi_y, psi_z (a = 1..3) at vertex
+// v = vx + 2 vy + 4 vz; cr[v] = (phi_xy, phi_xz, phi_yz, phi_xyz), each pair derivative
+// in the vertex's facet spanning its two axes, phi_xyz from the double difference of
+// psi_z over the vertex's x-y facet.
+template <class Q>
+__device__ __forceinline__ void cross_cell3d(const Q &q, float ih0, float ih1, float ih2,
+                                             float cr[8][4])
+{
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const int a = v & 1, b = (v >> 1) & 1, c = v >> 2;
+        auto P = [&](int x, int y, int z, int comp) { return q(x + 2 * y + 4 * z, comp); };
+        cr[v][0] = cell_vertex((P(0, 1, c, 1) - P(0, 0, c, 1)) * ih1, (P(1, 1, c, 1) - P(1, 0, c, 1)) * ih1,
+                               (P(1, 0, c, 2) - P(0, 0, c, 2)) * ih0, (P(1, 1, c, 2) - P(0, 1, c, 2)) * ih0, a, b);
+        cr[v][1] = cell_vertex((P(0, b, 1, 1) - P(0, b, 0, 1)) * ih2, (P(1, b, 1, 1) - P(1, b, 0, 1)) * ih2,
+                               (P(1, b, 0, 3) - P(0, b, 0, 3)) * ih0, (P(1, b, 1, 3) - P(0, b, 1, 3)) * ih0, a, c);
+        cr[v][2] = cell_vertex((P(a, 0, 1, 2) - P(a, 0, 0, 2)) * ih2, (P(a, 1, 1, 2) - P(a, 1, 0, 2)) * ih2,
+                               (P(a, 1, 0, 3) - P(a, 0, 0, 3)) * ih1, (P(a, 1, 1, 3) - P(a, 0, 1, 3)) * ih1, b, c);
+        cr[v][3] = (P(1, 1, c, 3) - P(0, 1, c, 3) - P(1, 0, c, 3) + P(0, 0, c, 3)) * ih0 * ih1;
+    }
 }
 
 // ---------------------------------------------------------------- approach A stencils

@@ -58,8 +58,10 @@ struct DiagOut {
 };
 // Scratch: `partials` holds at least diag_partials_needed() doubles; `counters` a DiagOut.
 int diag_partials_needed();
+// cell_a / cell_b: the interpolant of a / b takes its mixed derivatives by approach B.
 cudaError_t launch_diag(int dim, const Geom &g, const float *a, const float *b, int q,
-                        DiagOut *counters, double *partials, cudaStream_t s);
+                        DiagOut *counters, double *partials, cudaStream_t s, bool cell_a = false,
+                        bool cell_b = false);
 // Same kernels with `nparts` node blocks (one FP64 partial each) instead of the default.
 cudaError_t launch_diag_with(int dim, const Geom &g, const float *a, const float *b, int q,
                              DiagOut *counters, double *partials, int nparts, cudaStream_t s);

@@ -66,6 +66,7 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
 template <int TR, int VK>
 cudaError_t launch_cr(const StepLaunch &a, cudaStream_t s)
 {
+    if (a.cross_in == CROSS_CELL) return launch_t<TR, VK, CROSS_CELL, 0>(a, s);  // approach B
     if (a.write_cross)
         return a.cross_in == CROSS_PLANE ? launch_t<TR, VK, CROSS_PLANE, 1>(a, s)
                                          : launch_t<TR, VK, CROSS_RECON, 1>(a, s);

@@ -187,6 +187,7 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
                 c[2 * B + 1][3] = cross_from_window<1>(w, k + 1, g.n0, g.i2h0);
             }
         }
+        if (CR == CROSS_CELL) cross_cell2d(c, g.ih0, g.ih1);
         return;
     }
     const float *Pphi = in, *Ppx = in + g.plane, *Ppy = in + 2 * g.plane;
@@ -208,6 +209,7 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
             c[2 * B + 1][3] = cross_from_window<1>(w, k + 1, g.n0, g.i2h0);
         }
     }
+    if (CR == CROSS_CELL) cross_cell2d(c, g.ih0, g.ih1);
 }
 
 // Update of two nodes (i0, j0) and (i1, j1): phi+, psi_x+, psi_y+ per lane.

@@ -31,8 +31,9 @@ __device__ __forceinline__ float dwin(const float w[4], int q, int n, float i2h)
 constexpr int TX = 32, TY = 4, TZ = 4;
 constexpr int HX = 4, HZ = 1;          // halo (x rounded to 16 bytes for TMA)
 template <int CR> struct Tile3 {
-    static constexpr int HY = CR == CROSS_RECON ? 2 : 1;  // psi_z y-window needs one more
-    static constexpr int NP = CR == CROSS_RECON ? 4 : 8;
+    // psi_z y-window needs one more row (CROSS_RECON); CROSS_CELL shares that tile's map
+    static constexpr int HY = CR == CROSS_PLANE ? 1 : 2;
+    static constexpr int NP = CR == CROSS_PLANE ? 8 : 4;
     static constexpr int W = TX + 2 * HX, H = TY + 2 * HY, D = TZ + 2 * HZ;
     static constexpr int PS = W * H * D;
     static constexpr int BYTES = NP * PS * 4;
@@ -213,7 +214,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
         // a cell is served from the tile if every value its line reads is staged
         auto in_tile = [&](int k, int l, int m) {
             const int tx = k - x0 + HX, ty = l - y0 + T::HY, tz = m - z0 + HZ;
-            return CR == CROSS_PLANE
+            return CR != CROSS_RECON
                 ? (tx >= 0 && tx <= T::W - 2 && ty >= 0 && ty <= T::H - 2 && tz >= 0 && tz <= T::D - 2)
                 : (tx >= 1 && tx <= T::W - 3 && ty >= 1 && ty <= T::H - 3 && tz >= 0 && tz <= T::D - 2);
         };
@@ -228,7 +229,39 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
         const int nk0 = k0 + (bx.n0 ? 1 : 0), nl0 = l0 + (by.n0 ? 1 : 0), nm0 = m0 + (bz.n0 ? 1 : 0);
         const int nk1 = k1 + (bx.n1 ? 1 : 0), nl1 = l1 + (by.n1 ? 1 : 0), nm1 = m1 + (bz.n1 ? 1 : 0);
         F2 H, gr[3];
-        if (in0 && in1) {
+        if (CR == CROSS_CELL) {
+            // approach B: the cell's 8 vertices x (phi, psi) per foot, mixed derivatives from them
+            auto ld0 = [&](int a, int zz, int yy, int xx) { return in0 ? lds(a, zz, yy, xx) : ldg(a, zz, yy, xx); };
+            auto ld1 = [&](int a, int zz, int yy, int xx) { return in1 ? lds(a, zz, yy, xx) : ldg(a, zz, yy, xx); };
+            float q0[8][4], q1[8][4], c0[8][4], c1[8][4];
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    q0[v][a] = ld0(a, m0 + (v >> 2), l0 + ((v >> 1) & 1), k0 + (v & 1));
+                    q1[v][a] = ld1(a, m1 + (v >> 2), l1 + ((v >> 1) & 1), k1 + (v & 1));
+                }
+            cross_cell3d([&](int v, int a) { return q0[v][a]; }, g.ih0, g.ih1, g.ih2, c0);
+            cross_cell3d([&](int v, int a) { return q1[v][a]; }, g.ih0, g.ih1, g.ih2, c1);
+            const int vn0 = (bx.n0 ? 1 : 0) + (by.n0 ? 2 : 0) + (bz.n0 ? 4 : 0);
+            const int vn1 = (bx.n1 ? 1 : 0) + (by.n1 ? 2 : 0) + (bz.n1 ? 4 : 0);
+            float b0 = q0[0][0], b1 = q1[0][0];
+#pragma unroll
+            for (int v = 1; v < 8; ++v) {
+                b0 = v == vn0 ? q0[v][0] : b0;
+                b1 = v == vn1 ? q1[v][0] : b1;
+            }
+            hermite3d_pair(bx, by, bz, make_float2(b0, b1), [&](int B, int C, F2 lo[8], F2 hi[8]) {
+                const int v = 2 * B + 4 * C;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    lo[a] = make_float2(q0[v][a], q1[v][a]);
+                    hi[a] = make_float2(q0[v + 1][a], q1[v + 1][a]);
+                    lo[4 + a] = make_float2(c0[v][a], c1[v][a]);
+                    hi[4 + a] = make_float2(c0[v + 1][a], c1[v + 1][a]);
+                }
+            }, H, gr);
+        } else if (in0 && in1) {
             const F2 base = make_float2(lds(0, nm0, nl0, nk0), lds(0, nm1, nl1, nk1));
             hermite3d_pair(bx, by, bz, base, [&](int B, int C, F2 lo[8], F2 hi[8]) {
                 float a0[8], b0[8], a1[8], b1[8];
@@ -384,6 +417,7 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
 template <int TR, int VK>
 cudaError_t launch_cr(const StepLaunch &a, cudaStream_t s)
 {
+    if (a.cross_in == CROSS_CELL) return launch_t<TR, VK, CROSS_CELL>(a, s);
     return a.cross_in == CROSS_PLANE ? launch_t<TR, VK, CROSS_PLANE>(a, s)
                                      : launch_t<TR, VK, CROSS_RECON>(a, s);
 }

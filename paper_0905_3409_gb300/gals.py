@@ -55,7 +55,8 @@ class GalsError(RuntimeError):
 
 class GridDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3), ("layout", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("hi", ctypes.c_double * 3), ("layout", ctypes.c_int), ("cross_scheme", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class VelocityDesc(ctypes.Structure):
@@ -222,7 +223,7 @@ class Grid:
     ``n``: nodes per axis (x first); the state arrays have shape
     (nplanes, [nz,] ny, nx) with x fastest."""
 
-    def __init__(self, n, lo=None, hi=None, layout: str = "full", stream=None):
+    def __init__(self, n, lo=None, hi=None, layout: str = "full", stream=None, cross: str = "central"):
         dim = len(n)
         d = GridDesc()
         d.dim = dim
@@ -233,6 +234,7 @@ class Grid:
             d.lo[i] = float(lo[i]) if i < dim else 0.0
             d.hi[i] = float(hi[i]) if i < dim else 1.0
         d.layout = LAYOUT_FULL if layout == "full" else LAYOUT_COMPACT
+        d.cross_scheme = {"central": 0, "cell": 1}[cross]
         if stream is not None:
             d.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
         h = ctypes.c_void_p()

@@ -70,5 +70,6 @@ def test_version_and_argument_errors_without_gpu(built):
 
 def test_struct_layouts_match_header():
     # sizes of the public structs as laid out by the C compiler (x86-64 / aarch64 LP64)
-    assert ctypes.sizeof(gals.GridDesc) == 4 + 12 + 24 + 24 + 4 + 4 + 8  # padded to 80
+    assert ctypes.sizeof(gals.GridDesc) == 4 + 12 + 24 + 24 + 4 + 4 + 8  # layout, cross_scheme: 80
+    assert gals.GridDesc.cross_scheme.offset == 68 and gals.GridDesc.cuda_stream.offset == 72
     assert ctypes.sizeof(gals.DiagOut) == 11 * 8

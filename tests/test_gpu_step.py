@@ -39,11 +39,11 @@ def _gvel(G, kind, trace="rk3", **kw):
 
 
 def check_step(G, n, state, kind, dt, t0=0.0, steps=1, layout="full", trace="rk3",
-               lo=None, hi=None, recon=False, **vkw):
+               lo=None, hi=None, recon=False, cross="central", **vkw):
     """Advance `steps` steps on the GPU and check each against one oracle step."""
-    g = G.Grid(n, lo=lo, hi=hi, layout=layout)
+    g = G.Grid(n, lo=lo, hi=hi, layout=layout, cross=cross)
     g.set_state(state.astype(np.float32), t0=t0, recon=recon)
-    og = oracle.grid(n, lo=lo, hi=hi)
+    og = oracle.grid(n, lo=lo, hi=hi, cross=cross)
     ov = _ovel(kind, **vkw)
     gv = _gvel(G, kind, trace=trace, **vkw)
     worst = [0.0, 0.0, 0.0]
@@ -54,11 +54,16 @@ def check_step(G, n, state, kind, dt, t0=0.0, steps=1, layout="full", trace="rk3
         t = g.time
         g.step(gv, dt, 1)
         after = g.read_state().astype(np.float64)
-        ref = oracle.step(og, ov, before, t, dt, trace_scheme=trace)
+        ref = oracle.step(og, ov, before, t, dt, trace_scheme=trace, cross=cross)
         dphi = np.max(np.abs(after[0] - ref[0]))
         dpsi = np.max(np.abs(after[1:core] - ref[1:core]))
         assert dphi <= TOL_PHI, dphi
         assert dpsi <= TOL_PSI, dpsi
+        if cross == "cell":
+            # approach B keeps no node values of the mixed derivatives
+            assert not np.any(after[core:]) and not np.any(ref[core:])
+            worst = [max(worst[0], dphi), max(worst[1], dpsi), 0.0]
+            continue
         # mixed derivatives: exact stencil arithmetic on the GPU's own gradients
         rec = oracle.recon_cross(og, after)
         scale = np.max(np.abs(rec[core:])) + 1.0
@@ -167,3 +172,46 @@ def test_3d_gaussian_explicit_cross(gals):
     n = (16, 17, 18)
     st = inputs.gaussian_bump3d(n)
     check_step(gals, n, st, "const", 0.02, steps=1, c=(0.3, -0.5, 0.7))
+
+
+@pytest.mark.parametrize("layout", ["full", "compact"])
+def test_vortex_cross_cell(gals, layout):
+    """Mixed derivatives by approach (B) (Sec. 2.3), per cell from the vertices' gradients."""
+    n = (61, 47)
+    st = inputs.circle_sdf(n, center=(0.45, 0.55), r=0.3)
+    check_step(gals, n, st, "vortex2d", 0.9 / 60, t0=0.5, steps=3, layout=layout, cross="cell",
+               T=8.0)
+
+
+@pytest.mark.parametrize("layout", ["full", "compact"])
+def test_3d_deform_cross_cell(gals, layout):
+    n = (19, 18, 17)
+    st = inputs.sphere_sdf(n, center=(0.45, 0.5, 0.5), r=0.25)
+    check_step(gals, n, st, "deform3d", 0.5 / 18, t0=0.3, steps=2, layout=layout, cross="cell", T=3.0)
+
+
+def test_random_state_cross_cell_high_cfl(gals):
+    """Approach (B) with feet two cells away (global-memory gathers) and random data."""
+    n = (40, 33)
+    h = 1.0 / 39
+    st = inputs.random_state((4,) + n[::-1], seed=12)
+    st[0] *= h
+    check_step(gals, n, st, "const", 0.05, steps=1, cross="cell", c=(1.7, -1.2, 0))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_diagnostics_cross_cell(gals, dim):
+    """The diagnostics sample the approach-(B) interpolant, like the oracle's."""
+    n = (48, 40) if dim == 2 else (20, 18, 16)
+    st = inputs.circle_sdf(n, r=0.3, center=(0.5, 0.5)) if dim == 2 else inputs.sphere_sdf(
+        n, center=(0.5, 0.5, 0.5), r=0.3)
+    g = gals.Grid(n, cross="cell")
+    g.set_state(st.astype(np.float32))
+    d = g.diagnostics(q=4)
+    gs = g.read_state().astype(np.float64)
+    og = oracle.grid(n, cross="cell")
+    area = oracle.measure_negative(og, gs, 4)
+    cell = np.prod([1.0 / (v - 1) for v in n]) / 4 ** dim
+    assert abs(d["measure_negative"] - area) <= 16 * cell, (d["measure_negative"], area)
+    # the state keeps no mixed-derivative planes under approach (B)
+    assert not np.any(gs[1 + dim:])
