@@ -305,6 +305,17 @@ gals_status gals_surrogate_stats(gals_surrogate *s, int64_t *tiles, int64_t *fal
 gals_status gals_surrogate_get_params(const gals_surrogate *s, float *params, float *scales);
 gals_status gals_surrogate_set_params(gals_surrogate *s, const float *params, const float *scales);
 gals_status gals_surrogate_bind(gals_surrogate *s, const gals_velocity *vel, double dt, double h);
+/* Write / read a trained surrogate to / from a file: the FP32 parameters, the output
+ * scales, the residual-check settings and, if bound, the field (FOURIER2D modes as the
+ * library holds them), dt and h, so that a loaded surrogate serves gals_step at once.
+ * Format (host byte order): "GALSMLP" 0x01, int32 version 1, int32 GALS_MLP_PARAMS,
+ * int32 6, float params[], float scales[6], float tol_x, float tol_J, int32 samples,
+ * int32 bound, then if bound: double dt, double h, int32 kind, int32 nmodes,
+ * float a[nmodes], int32 k | l << 8 [nmodes], double n[nmodes], double chi / (2 pi) [nmodes].
+ * Errors: GALS_ERR_ARG (NULL, unreadable / unwritable file, wrong magic, version or sizes,
+ * truncated), GALS_ERR_CUDA.  save synchronises the surrogate's stream. */
+gals_status gals_surrogate_save(const gals_surrogate *s, const char *path);
+gals_status gals_surrogate_load(gals_surrogate *s, const char *path);
 /* Network outputs (normalised, n x 6, host) for inputs in [-1,1] (n x 3, host), evaluated by
  * the tensor-core inference kernel; synchronises. */
 gals_status gals_surrogate_forward(gals_surrogate *s, const float *inputs, int n, float *outputs);

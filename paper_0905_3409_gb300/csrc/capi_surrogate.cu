@@ -435,3 +435,91 @@ gals_status gals_surrogate_targets(gals_surrogate *s, const gals_velocity *vel, 
 }
 
 }  // extern "C"
+
+namespace {
+const char kMagic[8] = {'G', 'A', 'L', 'S', 'M', 'L', 'P', 1};
+constexpr int32_t kVersion = 1;
+
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() { if (f) fclose(f); }
+};
+
+template <class T>
+bool put(FILE *f, const T *v, size_t n) { return fwrite(v, sizeof(T), n, f) == n; }
+template <class T>
+bool get(FILE *f, T *v, size_t n) { return fread(v, sizeof(T), n, f) == n; }
+}  // namespace
+
+gals_status gals_surrogate_save(const gals_surrogate *s, const char *path)
+{
+    if (!s || !path) return sfail(const_cast<gals_surrogate *>(s), GALS_ERR_ARG, "NULL argument");
+    gals_surrogate *ms = const_cast<gals_surrogate *>(s);
+    std::vector<float> p(NPARAM);
+    float sc[OUT];
+    gals_status st = gals_surrogate_get_params(s, p.data(), sc);
+    if (st != GALS_OK) return st;
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) return sfail(ms, GALS_ERR_ARG, "cannot write %s", path);
+    const int32_t hdr[3] = {kVersion, (int32_t)NPARAM, (int32_t)OUT};
+    const float tols[2] = {s->tol_x, s->tol_J};
+    const int32_t samples = s->samples, bound = s->bound ? 1 : 0;
+    bool ok = put(fc.f, kMagic, 8) && put(fc.f, hdr, 3) && put(fc.f, p.data(), NPARAM) && put(fc.f, sc, OUT) &&
+              put(fc.f, tols, 2) && put(fc.f, &samples, 1) && put(fc.f, &bound, 1);
+    if (ok && bound) {
+        const double dh[2] = {s->dt, s->h};
+        const int32_t kn[2] = {s->vp.kind, s->vp.nmodes};
+        const size_t m = (size_t)s->vp.nmodes;
+        ok = put(fc.f, dh, 2) && put(fc.f, kn, 2) && put(fc.f, s->vp.mode_a, m) &&
+             put(fc.f, s->vp.mode_kl, m) && put(fc.f, s->vp.mode_n, m) && put(fc.f, s->vp.mode_chi, m);
+    }
+    if (!ok) return sfail(ms, GALS_ERR_ARG, "write to %s failed", path);
+    return GALS_OK;
+}
+
+gals_status gals_surrogate_load(gals_surrogate *s, const char *path)
+{
+    if (!s || !path) return sfail(s, GALS_ERR_ARG, "NULL argument");
+    FileCloser fc{fopen(path, "rb")};
+    if (!fc.f) return sfail(s, GALS_ERR_ARG, "cannot read %s", path);
+    char magic[8];
+    int32_t hdr[3];
+    if (!get(fc.f, magic, 8) || std::memcmp(magic, kMagic, 8) != 0)
+        return sfail(s, GALS_ERR_ARG, "%s is not a surrogate file", path);
+    if (!get(fc.f, hdr, 3) || hdr[0] != kVersion || hdr[1] != (int32_t)NPARAM || hdr[2] != (int32_t)OUT)
+        return sfail(s, GALS_ERR_ARG, "%s: unsupported version or network shape", path);
+    std::vector<float> p(NPARAM);
+    float sc[OUT], tols[2];
+    int32_t samples = 0, bound = 0;
+    if (!get(fc.f, p.data(), NPARAM) || !get(fc.f, sc, OUT) || !get(fc.f, tols, 2) || !get(fc.f, &samples, 1) ||
+        !get(fc.f, &bound, 1))
+        return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
+    VelParams vp{};
+    double dh[2] = {0.0, 0.0};
+    if (bound) {
+        int32_t kn[2];
+        if (!get(fc.f, dh, 2) || !get(fc.f, kn, 2)) return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
+        if (kn[0] != VK_FOURIER2D || kn[1] < 1 || kn[1] > kMaxModes || !(dh[0] > 0.0) || !(dh[1] > 0.0))
+            return sfail(s, GALS_ERR_ARG, "%s: invalid bound field", path);
+        vp.kind = kn[0];
+        vp.nmodes = kn[1];
+        const size_t m = (size_t)kn[1];
+        if (!get(fc.f, vp.mode_a, m) || !get(fc.f, vp.mode_kl, m) || !get(fc.f, vp.mode_n, m) ||
+            !get(fc.f, vp.mode_chi, m))
+            return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
+    }
+    if (!(tols[0] >= 0.f) || !(tols[1] >= 0.f) || samples < 0)
+        return sfail(s, GALS_ERR_ARG, "%s: invalid residual-check settings", path);
+    gals_status st = gals_surrogate_set_params(s, p.data(), sc);
+    if (st != GALS_OK) return st;
+    s->tol_x = tols[0];
+    s->tol_J = tols[1];
+    s->samples = samples;
+    if (bound) {
+        s->vp = vp;
+        s->dt = dh[0];
+        s->h = dh[1];
+        s->bound = true;
+    }
+    return GALS_OK;
+}

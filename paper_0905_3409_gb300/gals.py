@@ -39,7 +39,7 @@ EXPORTS = [
     "gals_surrogate_set_check", "gals_surrogate_stats", "gals_surrogate_get_params",
     "gals_surrogate_set_params", "gals_surrogate_bind", "gals_surrogate_forward",
     "gals_surrogate_gradient", "gals_surrogate_targets", "gals_surrogate_last_error",
-    "gals_surrogate_forward_device",
+    "gals_surrogate_forward_device", "gals_surrogate_save", "gals_surrogate_load",
 ]
 
 
@@ -162,6 +162,8 @@ def lib() -> ctypes.CDLL:
                                           ctypes.c_double]
         L.gals_surrogate_forward.argtypes = [vp, fp, ctypes.c_int, fp]
         L.gals_surrogate_forward_device.argtypes = [vp, vp, ctypes.c_int64, vp]
+        L.gals_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        L.gals_surrogate_load.argtypes = [vp, ctypes.c_char_p]
         L.gals_surrogate_gradient.argtypes = [vp, fp, fp, ctypes.c_int, fp,
                                               ctypes.POINTER(ctypes.c_double)]
         L.gals_surrogate_targets.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
@@ -495,6 +497,12 @@ class Surrogate:
         Y = np.empty((X.shape[0], 6), dtype=np.float32)
         _scheck(lib().gals_surrogate_forward(self._h, _fp(X), X.shape[0], _fp(Y)), self._h)
         return Y
+
+    def save(self, path):
+        _scheck(lib().gals_surrogate_save(self._h, os.fsencode(path)), self._h)
+
+    def load(self, path):
+        _scheck(lib().gals_surrogate_load(self._h, os.fsencode(path)), self._h)
 
     def forward_device(self, inputs_ptr: int, n: int, outputs_ptr: int):
         """Device-memory forward pass (n x 3 floats in, n x 6 out), enqueued on the

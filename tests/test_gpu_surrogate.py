@@ -171,3 +171,36 @@ def test_surrogate_against_plain_trace(G, field):
           f"surrogate: {n * n * steps / t_sur:.3e} nu/s, interface err {e_sur:.3e}, "
           f"fallback tiles {falls}/{tiles}")
     assert math.isfinite(e_sur) and tiles > 0
+
+
+def test_save_load_roundtrip(G, field, tmp_path):
+    """A saved surrogate loads into a fresh handle with the same parameters, scales,
+    residual check and bound field: its forward pass and a learned step are bit-identical;
+    a file that is not a surrogate is refused."""
+    modes, n, h, dt = field
+    vel = G.Velocity("fourier2d", modes=modes)
+    S = G.Surrogate(seed=13)
+    S.train(vel, dt, h, steps=40, batch=4096, lr=2e-3, lr_min=1e-4)
+    S.set_check(tol_x=0.07, tol_J=0.06, samples=3)
+    path = tmp_path / "mlp.bin"
+    S.save(path)
+    T = G.Surrogate(seed=99)
+    T.load(path)
+    p1, s1 = S.get_params()
+    p2, s2 = T.get_params()
+    assert np.array_equal(p1, p2) and np.array_equal(s1, s2)
+    X = np.random.default_rng(6).uniform(-1, 1, (500, 3)).astype(np.float32)
+    assert np.array_equal(S.forward(X), T.forward(X))
+    st = inputs.ellipse_sdf((n, n), (0.5, 0.5), 0.2, 0.1, 0.3, iters=60).astype(np.float32)
+    outs = []
+    for sur in (S, T):
+        g = G.Grid((n, n))
+        g.set_state(st, t0=0.2, recon=True)
+        sur.stats(reset=True)
+        g.step(G.Velocity("fourier2d", modes=modes, trace="surrogate", surrogate=sur), dt, 2)
+        outs.append((g.read_state(), sur.stats()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a surrogate")
+    with pytest.raises(G.GalsError):
+        T.load(bad)
