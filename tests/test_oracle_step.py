@@ -208,7 +208,7 @@ def test_local_truncation_order_pseudo1d(golden, trace):
     from the boundary converges with order 4 in phi and 3 in grad phi.  The
     region [0.4, 0.7]^2 is outside the numerical domain of dependence of the
     inflow edges and away from the one-sided cross stencils at the outflow edges
-    (the paper only says 'a part of the domain not influenced by the boundary').
+    (the paper asks only for a region the boundary does not influence).
     Both the superconsistent RK3 scheme and the CIR scheme with Heun's method for the
     gradients (Sec. 4: RK3 for the characteristic, Heun for eq. cir_evolution_psi) have
     these orders."""
