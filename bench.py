@@ -177,13 +177,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
-def kernel_source_hash():
+# the sources that define each benchmarked kernel: a recorded DRAM traffic figure is
+# reported only while these files are unchanged
+KERNEL_SOURCES = {
+    2: ["step2d.cu", "step2d_tile.cuh", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
+    3: ["step3d.cu", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
+}
+
+
+def kernel_source_hash(dim=None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0905_3409_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(f.read())
+    names = KERNEL_SOURCES[dim] if dim in KERNEL_SOURCES else sorted(
+        fn for fn in os.listdir(csrc) if fn.endswith((".cu", ".cuh", ".h")))
+    for fn in names:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -196,7 +205,7 @@ def recorded_traffic(workload, layout):
     with open(p) as f:
         d = json.load(f)
     e = d.get(f"{workload}/{layout}")
-    if not e or e.get("kernel_sources") != kernel_source_hash():
+    if not e or e.get("kernel_sources") != kernel_source_hash(WORKLOADS[workload]["dim"]):
         return None
     return e.get("dram_bytes_per_launch")
 
