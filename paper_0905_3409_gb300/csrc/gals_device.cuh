@@ -114,11 +114,19 @@ __device__ inline void stage_coef_one(const VelParams &vp, double t, double dt, 
 // ---------------------------------------------------------------- velocity fields
 
 struct V2 { float u, v, d00, d01, d10, d11; };          // Dv[i][j] = dv_i/dx_j
-struct V3 { float v[3]; float d[9]; };
 
 __device__ __forceinline__ void sincospi_f(float x, float *s, float *c)
 {
     __sincosf(x * kPi, s, c);
+}
+
+// sin a and cos a for a = 2 pi (s - 1/2) = 2 pi s - pi, one rounding: for s in [0, 1] the
+// angle stays in [-pi, pi], where the hardware approximation is most accurate.  Then
+// sin a = -sin(2 pi s), cos a = -cos(2 pi s) and sin^2(pi s) = (1 + cos a) / 2; the
+// separable fields (single vortex, deformation) are written in these factors.
+__device__ __forceinline__ void sincos_turn(float s, float *sn, float *cs)
+{
+    __sincosf(__fmaf_rn(s, 2.f * kPi, -kPi), sn, cs);
 }
 
 template <int VK>
@@ -133,20 +141,19 @@ __device__ __forceinline__ V2 vel2d(const VelParams &vp, const StageCoef &sc, in
         r.v = vp.omega * (x - vp.cx);
         r.d00 = 0.f; r.d01 = -vp.omega; r.d10 = vp.omega; r.d11 = 0.f;
     } else if (VK == VK_VORTEX2D) {
-        float sx, cxx, sy, cyy;
-        sincospi_f(x, &sx, &cxx);
-        sincospi_f(y, &sy, &cyy);
-        float c = sc.mod[stage];
-        float s2x = 2.f * sx * cxx, s2y = 2.f * sy * cyy;
-        float c2x = 1.f - 2.f * sx * sx, c2y = 1.f - 2.f * sy * sy;
-        float sx2 = sx * sx, sy2 = sy * sy;
-        r.u = -c * sx2 * s2y;
-        r.v = c * s2x * sy2;
-        float cp = c * kPi;
-        r.d00 = -cp * s2x * s2y;
-        r.d01 = -2.f * cp * sx2 * c2y;
-        r.d10 = 2.f * cp * c2x * sy2;
-        r.d11 = cp * s2x * s2y;
+        // u = -c sin^2(pi x) sin(2 pi y), v = c sin(2 pi x) sin^2(pi y), in the factors
+        // A = sin a, B = cos a of sincos_turn
+        float Ax, Bx, Ay, By;
+        sincos_turn(x, &Ax, &Bx);
+        sincos_turn(y, &Ay, &By);
+        const float c = sc.mod[stage], h = 0.5f * c;
+        const float cSx = __fmaf_rn(Bx, h, h), mcSy = __fmaf_rn(By, -h, -h);
+        r.u = cSx * Ay;
+        r.v = Ax * mcSy;
+        r.d00 = -(c * kPi) * (Ax * Ay);
+        r.d01 = (2.f * kPi) * (cSx * By);
+        r.d10 = (2.f * kPi) * (Bx * mcSy);
+        r.d11 = -r.d00;
     } else if (VK == VK_PSEUDO1D) {
         float e = __expf(vp.d0 * x + vp.d1 * y);
         r.u = e * vp.d0; r.v = e * vp.d1;
@@ -187,47 +194,6 @@ __device__ __forceinline__ V2 vel2d(const VelParams &vp, const StageCoef &sc, in
     return r;
 }
 
-template <int VK>
-__device__ __forceinline__ V3 vel3d(const VelParams &vp, const StageCoef &sc, int stage,
-                                    float x, float y, float z)
-{
-    V3 r;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) r.d[a] = 0.f;
-    if (VK == VK_CONST) {
-        r.v[0] = vp.c0; r.v[1] = vp.c1; r.v[2] = vp.c2;
-    } else if (VK == VK_ROTATION) {
-        r.v[0] = -vp.omega * (y - vp.cy);
-        r.v[1] = vp.omega * (x - vp.cx);
-        r.v[2] = 0.f;
-        r.d[1] = -vp.omega; r.d[3] = vp.omega;
-    } else {  // VK_DEFORM3D
-        float sx, cxx, sy, cyy, sz, czz;
-        sincospi_f(x, &sx, &cxx);
-        sincospi_f(y, &sy, &cyy);
-        sincospi_f(z, &sz, &czz);
-        float c = sc.mod[stage];
-        float s2x = 2.f * sx * cxx, s2y = 2.f * sy * cyy, s2z = 2.f * sz * czz;
-        float c2x = 1.f - 2.f * sx * sx, c2y = 1.f - 2.f * sy * sy, c2z = 1.f - 2.f * sz * sz;
-        float sx2 = sx * sx, sy2 = sy * sy, sz2 = sz * sz;
-        float cp = c * kPi;
-        r.v[0] = 2.f * c * sx2 * s2y * s2z;
-        r.v[1] = -c * s2x * sy2 * s2z;
-        r.v[2] = -c * s2x * s2y * sz2;
-        float sss = s2x * s2y * s2z;
-        r.d[0] = 2.f * cp * sss;
-        r.d[1] = 4.f * cp * sx2 * c2y * s2z;
-        r.d[2] = 4.f * cp * sx2 * s2y * c2z;
-        r.d[3] = -2.f * cp * c2x * sy2 * s2z;
-        r.d[4] = -cp * sss;
-        r.d[5] = -2.f * cp * s2x * sy2 * c2z;
-        r.d[6] = -2.f * cp * c2x * s2y * sz2;
-        r.d[7] = -2.f * cp * s2x * c2y * sz2;
-        r.d[8] = -cp * sss;
-    }
-    return r;
-}
-
 // ---------------------------------------------------------------- backward traces
 
 // 2D trace from node position (x, y) at t+dt back to t: displacement (dx, dy) of the
@@ -258,15 +224,15 @@ __device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, c
     V2 c = vel2d<VK>(vp, sc, 2, x - q * (a.u + b.u), y - q * (a.v + b.v));  // v(x2, t+dt/2)
     float N00 = c.d00 * J2_00 + c.d01 * J2_10, N01 = c.d00 * J2_01 + c.d01 * J2_11;
     float N10 = c.d10 * J2_00 + c.d11 * J2_10, N11 = c.d10 * J2_01 + c.d11 * J2_11;
-    // stage 3: foot = x - dt (v1/6 + v2/6 + 2 v3/3), J = I - dt (Dv1/6 + Dv2 J1/6 + 2 Dv3 J2/3)
-    // written as w3 + (w1 + w2 - 2 w3)/6 (= w1/6 + w2/6 + 2 w3/3), exact for constant v
-    const float i6 = 1.f / 6.f;
+    // stage 3: foot = x - dt (v1/6 + v2/6 + 2 v3/3), written as w3 + (w1 + w2 - 2 w3)/6,
+    // exact for constant v; J = I - dt (Dv1 + Dv2 J1)/6 - 2 dt Dv3 J2 / 3 (= I when Dv = 0)
+    const float i6 = 1.f / 6.f, m6 = -dt / 6.f, m23 = -2.f * dt / 3.f;
     dx = -dt * fmaf(a.u + b.u - 2.f * c.u, i6, c.u);
     dy = -dt * fmaf(a.v + b.v - 2.f * c.v, i6, c.v);
-    J[0] = 1.f - dt * fmaf(a.d00 + M00 - 2.f * N00, i6, N00);
-    J[1] = -dt * fmaf(a.d01 + M01 - 2.f * N01, i6, N01);
-    J[2] = -dt * fmaf(a.d10 + M10 - 2.f * N10, i6, N10);
-    J[3] = 1.f - dt * fmaf(a.d11 + M11 - 2.f * N11, i6, N11);
+    J[0] = fmaf(m6, a.d00 + M00, fmaf(m23, N00, 1.f));
+    J[1] = fmaf(m6, a.d01 + M01, m23 * N01);
+    J[2] = fmaf(m6, a.d10 + M10, m23 * N10);
+    J[3] = fmaf(m6, a.d11 + M11, fmaf(m23, N11, 1.f));
 }
 
 template <int TR, int VK>
@@ -274,64 +240,6 @@ __device__ __forceinline__ void trace2d(const VelParams &vp, const StageCoef &sc
                                         float y, float dt, float &dx, float &dy, float J[4])
 {
     trace2d_from<TR, VK>(vel2d<VK>(vp, sc, 0, x, y), vp, sc, x, y, dt, dx, dy, J);
-}
-
-__device__ __forceinline__ void matmul3(const float *A, const float *B, float *C)
-{
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
-}
-
-template <int VK>
-__device__ __forceinline__ void trace3d_rk3(const V3 &a, const VelParams &vp, const StageCoef &sc,
-                                            float x, float y, float z, float dt, float d[3],
-                                            float J[9]);
-
-// 3D trace from node position (x, y, z); a = v(x, t+dt) and its Jacobian supplied by the
-// caller.  d = foot - x, J[3i+j] = d foot_i / d x_j.
-template <int TR, int VK>
-__device__ __forceinline__ void trace3d_from(const V3 &a, const VelParams &vp,
-                                             const StageCoef &sc, float x, float y, float z,
-                                             float dt, float d[3], float J[9])
-{
-    if (TR == TR_EULER) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d[i] = -dt * a.v[i];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) J[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * a.d[e];
-    } else {
-        trace3d_rk3<VK>(a, vp, sc, x, y, z, dt, d, J);
-    }
-}
-
-template <int VK>
-__device__ __forceinline__ void trace3d_rk3(const V3 &a, const VelParams &vp, const StageCoef &sc,
-                                            float x, float y, float z, float dt, float d[3],
-                                            float J[9])
-{
-    float J1[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) J1[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * a.d[e];
-    V3 b = vel3d<VK>(vp, sc, 1, x - dt * a.v[0], y - dt * a.v[1], z - dt * a.v[2]);
-    float M[9];
-    matmul3(b.d, J1, M);
-    float q = 0.25f * dt;
-    float J2[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) J2[e] = ((e % 4) == 0 ? 1.f : 0.f) - q * (a.d[e] + M[e]);
-    V3 c = vel3d<VK>(vp, sc, 2, x - q * (a.v[0] + b.v[0]), y - q * (a.v[1] + b.v[1]),
-                     z - q * (a.v[2] + b.v[2]));
-    float N[9];
-    matmul3(c.d, J2, N);
-    const float i6 = 1.f / 6.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) d[i] = -dt * fmaf(a.v[i] + b.v[i] - 2.f * c.v[i], i6, c.v[i]);
-#pragma unroll
-    for (int e = 0; e < 9; ++e)
-        J[e] = ((e % 4) == 0 ? 1.f : 0.f) - dt * fmaf(a.d[e] + M[e] - 2.f * N[e], i6, N[e]);
 }
 
 // ---------------------------------------------------------------- cell location

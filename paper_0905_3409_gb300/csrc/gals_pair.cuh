@@ -33,6 +33,22 @@ __device__ __forceinline__ void sincospi2(F2 s, F2 &sn, F2 &cs)
     sincospi_f(s.y, &sn.y, &cs.y);
 }
 
+// per-lane sin a, cos a with a = 2 pi (s - 1/2) (see sincos_turn)
+__device__ __forceinline__ void sincos_turn2(F2 s, F2 &A, F2 &B)
+{
+    const F2 a = fma2(s, bc(2.f * kPi), bc(-kPi));
+    __sincosf(a.x, &A.x, &B.x);
+    __sincosf(a.y, &A.y, &B.y);
+}
+
+// the same with the angle negated: An = -sin a, B = cos a
+__device__ __forceinline__ void sincos_turn2n(F2 s, F2 &An, F2 &B)
+{
+    const F2 a = fma2(s, bc(-2.f * kPi), bc(kPi));
+    __sincosf(a.x, &An.x, &B.x);
+    __sincosf(a.y, &An.y, &B.y);
+}
+
 // Fourier tables duplicated into float2 pairs (both lanes use the same coefficient).
 struct StageCoefPair {
     F2 A[3][16], Al[3][16], All[3][16];
@@ -52,18 +68,18 @@ __device__ __forceinline__ V2p vel2d_pair(const VelParams &vp, const StageCoef &
         r.v = mul2(w, sub2(x, bc(vp.cx)));
         r.d00 = bc(0.f); r.d01 = bc(-vp.omega); r.d10 = w; r.d11 = bc(0.f);
     } else if (VK == VK_VORTEX2D) {
-        F2 sx, cxx, sy, cyy;
-        sincospi2(x, sx, cxx);
-        sincospi2(y, sy, cyy);
-        const float c = sc.mod[stage], cp = c * kPi;
-        const F2 s2x = mul2(bc(2.f), mul2(sx, cxx)), s2y = mul2(bc(2.f), mul2(sy, cyy));
-        const F2 sx2 = mul2(sx, sx), sy2 = mul2(sy, sy);
-        const F2 c2x = fma2(bc(-2.f), sx2, bc(1.f)), c2y = fma2(bc(-2.f), sy2, bc(1.f));
-        r.u = mul2(bc(-c), mul2(sx2, s2y));
-        r.v = mul2(bc(c), mul2(s2x, sy2));
-        r.d00 = mul2(bc(-cp), mul2(s2x, s2y));
-        r.d01 = mul2(bc(-2.f * cp), mul2(sx2, c2y));
-        r.d10 = mul2(bc(2.f * cp), mul2(c2x, sy2));
+        // u = -c sin^2(pi x) sin(2 pi y), v = c sin(2 pi x) sin^2(pi y) in the factors
+        // A = sin a = -sin(2 pi s), B = cos a = -cos(2 pi s), sin^2(pi s) = (1 + B)/2
+        F2 Ax, Bx, Ay, By;
+        sincos_turn2(x, Ax, Bx);
+        sincos_turn2(y, Ay, By);
+        const float c = sc.mod[stage], h = 0.5f * c;
+        const F2 cSx = fma2(Bx, bc(h), bc(h)), mcSy = fma2(By, bc(-h), bc(-h));
+        r.u = mul2(cSx, Ay);
+        r.v = mul2(Ax, mcSy);
+        r.d00 = mul2(bc(-c * kPi), mul2(Ax, Ay));
+        r.d01 = mul2(bc(2.f * kPi), mul2(cSx, By));
+        r.d10 = mul2(bc(2.f * kPi), mul2(Bx, mcSy));
         r.d11 = neg2(r.d00);
     } else if (VK == VK_PSEUDO1D) {
         const F2 arg = fma2(bc(vp.d0), x, mul2(bc(vp.d1), y));
@@ -148,14 +164,15 @@ __device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
                                  fma2(mq, add2(a.v, b.v), y));
     const F2 N00 = fma2(c.d00, J2_00, mul2(c.d01, J2_10)), N01 = fma2(c.d00, J2_01, mul2(c.d01, J2_11));
     const F2 N10 = fma2(c.d10, J2_00, mul2(c.d11, J2_10)), N11 = fma2(c.d10, J2_01, mul2(c.d11, J2_11));
-    // foot = x - dt (w3 + (w1 + w2 - 2 w3)/6), J = I - dt (N + (Dv1 + M - 2 N)/6): exact for constant v
-    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f);
+    // foot = x - dt (w3 + (w1 + w2 - 2 w3)/6): exact for constant v;
+    // J = I - dt (Dv1 + M)/6 - 2 dt N / 3 (= I when Dv = 0)
+    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f), m6 = bc(-dt / 6.f), m23 = bc(-2.f * dt / 3.f);
     dx = mul2(mdt, fma2(fma2(m2, c.u, add2(a.u, b.u)), i6, c.u));
     dy = mul2(mdt, fma2(fma2(m2, c.v, add2(a.v, b.v)), i6, c.v));
-    J[0] = fma2(mdt, fma2(fma2(m2, N00, add2(a.d00, M00)), i6, N00), one);
-    J[1] = mul2(mdt, fma2(fma2(m2, N01, add2(a.d01, M01)), i6, N01));
-    J[2] = mul2(mdt, fma2(fma2(m2, N10, add2(a.d10, M10)), i6, N10));
-    J[3] = fma2(mdt, fma2(fma2(m2, N11, add2(a.d11, M11)), i6, N11), one);
+    J[0] = fma2(m6, add2(a.d00, M00), fma2(m23, N00, one));
+    J[1] = fma2(m6, add2(a.d01, M01), mul2(m23, N01));
+    J[2] = fma2(m6, add2(a.d10, M10), mul2(m23, N10));
+    J[3] = fma2(m6, add2(a.d11, M11), fma2(m23, N11, one));
 }
 
 // Paired 1D basis (see basis1).  n0, n1 = (xi >= 1/2) per lane pick each foot's nearest
@@ -223,6 +240,27 @@ __device__ __forceinline__ void hermite2d_pair(const F2 c[4][4], const Basis2 &b
 
 struct V3p { F2 v[3]; F2 d[9]; };
 
+// The deformation field from its folded xy products P1 = 2 Sx Ay, P2 = -Ax Sy,
+// P3 = -Ax Ay, P4 = 4 pi Sx By, P5 = -2 pi Bx Sy, P6 = -2 pi Bx Ay, P7 = -2 pi Ax By and
+// z factors Azc = c Az, Szc = c Sz, Bzc = 2 pi c Bz (see vel3d_pair).
+__device__ __forceinline__ void deform_terms(F2 P1, F2 P2, F2 P3, F2 P4, F2 P5, F2 P6, F2 P7,
+                                             F2 Azc, F2 Szc, F2 Bzc, V3p &r)
+{
+    const F2 T = mul2(P3, Azc);                  // -c Ax Ay Az
+    r.v[0] = mul2(P1, Azc);
+    r.v[1] = mul2(P2, Azc);
+    r.v[2] = mul2(P3, Szc);
+    r.d[0] = mul2(bc(2.f * kPi), T);
+    r.d[1] = mul2(P4, Azc);
+    r.d[2] = mul2(P1, Bzc);
+    r.d[3] = mul2(P5, Azc);
+    r.d[4] = mul2(bc(-kPi), T);
+    r.d[5] = mul2(P2, Bzc);
+    r.d[6] = mul2(P6, Szc);
+    r.d[7] = mul2(P7, Szc);
+    r.d[8] = r.d[4];
+}
+
 // v and Dv (Dv[3i+j] = dv_i/dx_j) at two points; DEFORM3D is LeVeque's field
 // u = 2 sin^2(pi x) sin(2 pi y) sin(2 pi z) c, v = -sin(2 pi x) sin^2(pi y) sin(2 pi z) c,
 // w = -sin(2 pi x) sin(2 pi y) sin^2(pi z) c with c = cos(pi t / T).
@@ -241,28 +279,20 @@ __device__ __forceinline__ V3p vel3d_pair(const VelParams &vp, const StageCoef &
         r.v[2] = bc(0.f);
         r.d[1] = bc(-vp.omega); r.d[3] = bc(vp.omega);
     } else {  // VK_DEFORM3D
-        F2 sx, cx, sy, cy, sz, cz;
-        sincospi2(x, sx, cx);
-        sincospi2(y, sy, cy);
-        sincospi2(z, sz, cz);
-        const float c = sc.mod[stage], cp = c * kPi;
-        const F2 two = bc(2.f), one = bc(1.f), mtwo = bc(-2.f);
-        const F2 s2x = mul2(two, mul2(sx, cx)), s2y = mul2(two, mul2(sy, cy)), s2z = mul2(two, mul2(sz, cz));
-        const F2 sx2 = mul2(sx, sx), sy2 = mul2(sy, sy), sz2 = mul2(sz, sz);
-        const F2 c2x = fma2(mtwo, sx2, one), c2y = fma2(mtwo, sy2, one), c2z = fma2(mtwo, sz2, one);
-        const F2 sxy = mul2(s2x, s2y), sss = mul2(sxy, s2z);
-        r.v[0] = mul2(bc(2.f * c), mul2(sx2, mul2(s2y, s2z)));
-        r.v[1] = mul2(bc(-c), mul2(mul2(s2x, sy2), s2z));
-        r.v[2] = mul2(bc(-c), mul2(sxy, sz2));
-        r.d[0] = mul2(bc(2.f * cp), sss);
-        r.d[1] = mul2(bc(4.f * cp), mul2(sx2, mul2(c2y, s2z)));
-        r.d[2] = mul2(bc(4.f * cp), mul2(sx2, mul2(s2y, c2z)));
-        r.d[3] = mul2(bc(-2.f * cp), mul2(c2x, mul2(sy2, s2z)));
-        r.d[4] = mul2(bc(-cp), sss);
-        r.d[5] = mul2(bc(-2.f * cp), mul2(s2x, mul2(sy2, c2z)));
-        r.d[6] = mul2(bc(-2.f * cp), mul2(c2x, mul2(s2y, sz2)));
-        r.d[7] = mul2(bc(-2.f * cp), mul2(s2x, mul2(c2y, sz2)));
-        r.d[8] = r.d[4];
+        // In the factors A = sin a, B = cos a of a = 2 pi (s - 1/2) and S = sin^2(pi s) =
+        // (1 + B)/2 every term is (constant) x (x factor)(y factor)(z factor); the constants
+        // are folded into the factors: x with the angle negated (A -> -A), 2S and -2 pi B;
+        // y: S and 2 pi B; z: c A, c S and 2 pi c B.
+        F2 Axn, Bx, Ay, By, Az, Bz;
+        sincos_turn2n(x, Axn, Bx);
+        sincos_turn2(y, Ay, By);
+        sincos_turn2(z, Az, Bz);
+        const float c = sc.mod[stage], h = 0.5f * c;
+        const F2 Sx2 = add2(Bx, bc(1.f)), Bxm = mul2(bc(-2.f * kPi), Bx);
+        const F2 Sy = fma2(By, bc(0.5f), bc(0.5f)), By2 = mul2(bc(2.f * kPi), By);
+        const F2 Azc = mul2(bc(c), Az), Szc = fma2(Bz, bc(h), bc(h)), Bzc = mul2(bc(2.f * kPi * c), Bz);
+        deform_terms(mul2(Sx2, Ay), mul2(Axn, Sy), mul2(Axn, Ay), mul2(Sx2, By2), mul2(Bxm, Sy),
+                     mul2(Bxm, Ay), mul2(Axn, By2), Azc, Szc, Bzc, r);
     }
     return r;
 }
@@ -325,15 +355,14 @@ __device__ __forceinline__ void trace3d_pair(const V3p &a, const VelParams &vp, 
     const V3p c = vel3d_pair<VK>(vp, sc, 2, fma2(mq, s1[0], x), fma2(mq, s1[1], y), fma2(mq, s1[2], z));
     F2 N[9];
     matmul3_pair(c.d, J2, N);
-    // w3 + (w1 + w2 - 2 w3)/6: exact for constant v
-    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f);
+    // d = -dt (w3 + (w1 + w2 - 2 w3)/6): exact for constant v;
+    // J = I - dt (Dv1 + M)/6 - 2 dt N / 3 (= I when Dv = 0)
+    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f), m6 = bc(-dt / 6.f), m23 = bc(-2.f * dt / 3.f);
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = mul2(mdt, fma2(fma2(m2, c.v[i], s1[i]), i6, c.v[i]));
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-        const F2 w = fma2(fma2(m2, N[e], add2(a.d[e], M[e])), i6, N[e]);
-        J[e] = (e % 4) == 0 ? fma2(mdt, w, one) : mul2(mdt, w);
-    }
+    for (int e = 0; e < 9; ++e)
+        J[e] = fma2(m6, add2(a.d[e], M[e]), (e % 4) == 0 ? fma2(m23, N[e], one) : mul2(m23, N[e]));
 }
 
 // Tricubic Hermite value and gradient for two feet, streamed over the four x-lines of

@@ -122,36 +122,44 @@ __device__ __forceinline__ float cross_from_window(const float w[4], int q, int 
     return dcentral(w[c + 1], w[c - 1], i2h);
 }
 
-// Separable factors of the single-vortex field on a grid line: sin^2(pi s),
-// sin(2 pi s), cos(2 pi s) (one float2 lane per node).
-struct Sep2 { F2 s2, s2x, c2x; };
+// Separable factors of the single-vortex field on a grid line, per lane: A = sin a,
+// B = cos a for a = 2 pi (s - 1/2), and S = sin^2(pi s) = (1 + B)/2 (see sincos_turn).
+struct Sep2 { F2 S, A, B; };
 
 __device__ __forceinline__ Sep2 sep_factors2(F2 s)
 {
-    F2 sn, cs;
-    sincospi2(s, sn, cs);
     Sep2 f;
-    f.s2 = mul2(sn, sn);
-    f.s2x = mul2(bc(2.f), mul2(sn, cs));
-    f.c2x = fma2(bc(-2.f), f.s2, bc(1.f));
+    sincos_turn2(s, f.A, f.B);
+    f.S = fma2(f.B, bc(0.5f), bc(0.5f));
     return f;
 }
 
-// v(x, t+dt) at two nodes of one column; the single vortex uses the separable
-// column factors cx (shared) and row factors ry.
+// A column's factors of the single vortex at t + dt (stage coefficient c), constants
+// folded in: u = ku Ay, v = kv Sy, du/dx = k00 Ay, du/dy = k01 By, dv/dx = k10 Sy.
+struct VCol { float ku, kv, k00, k01, k10; };
+
+__device__ __forceinline__ VCol vortex_col(float x, float c)
+{
+    float A, B;
+    sincos_turn(x, &A, &B);
+    const float S = __fmaf_rn(B, 0.5f, 0.5f), cp = c * kPi;
+    return VCol{c * S, -c * A, -cp * A, (2.f * cp) * S, (-2.f * cp) * B};
+}
+
+// v(x, t+dt) at two nodes of one column; the single vortex uses the column factors cx
+// (fixed per thread) and the row factors ry.
 template <int VK>
 __device__ __forceinline__ V2p stage1_pair(const VelParams &vp, const StageCoef &sc,
-                                           const StageCoefPair *scp, F2 x, F2 y, const Sep2 &cx,
+                                           const StageCoefPair *scp, F2 x, F2 y, const VCol &cx,
                                            const Sep2 &ry)
 {
     if (VK == VK_VORTEX2D) {
         V2p r;
-        const float c = sc.mod[0], cp = c * kPi;
-        r.u = mul2(bc(-c), mul2(cx.s2, ry.s2x));
-        r.v = mul2(bc(c), mul2(cx.s2x, ry.s2));
-        r.d00 = mul2(bc(-cp), mul2(cx.s2x, ry.s2x));
-        r.d01 = mul2(bc(-2.f * cp), mul2(cx.s2, ry.c2x));
-        r.d10 = mul2(bc(2.f * cp), mul2(cx.c2x, ry.s2));
+        r.u = mul2(bc(cx.ku), ry.A);
+        r.v = mul2(bc(cx.kv), ry.S);
+        r.d00 = mul2(bc(cx.k00), ry.A);
+        r.d01 = mul2(bc(cx.k01), ry.B);
+        r.d10 = mul2(bc(cx.k10), ry.S);
         r.d11 = neg2(r.d00);
         return r;
     }
@@ -218,7 +226,7 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
                                             const float *__restrict__ tile, int x0, int y0,
                                             const VelParams &vp, const StageCoef &sc,
                                             const StageCoefPair *scp, float dt, int i0, int j0,
-                                            int i1, int j1, F2 x, F2 y, const Sep2 &cx,
+                                            int i1, int j1, F2 x, F2 y, const VCol &cx,
                                             const Sep2 &ry, F2 &phi, F2 &px, F2 &py,
                                             const V2p *a1 = nullptr)
 {
@@ -326,7 +334,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
     const int rows = min(TY, g.n1 - y0);
     const float xs = g.lo0 + (float)i * g.h0;
     const F2 x = bc(xs);
-    const Sep2 cx = (VK == VK_VORTEX2D) ? sep_factors2(x) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+    const VCol cx = (VK == VK_VORTEX2D) ? vortex_col(xs, sc.mod[0]) : VCol{0.f, 0.f, 0.f, 0.f, 0.f};
     FCol fcol;
     if (VK == VK_FOURIER2D) fcol = fourier_col(xs);
 
@@ -381,7 +389,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             const int r = 2 * rp, j0 = y0 + r, j1 = min(j0 + 1, g.n1 - 1);
             const F2 xh = bc(g.lo0 + (float)ih * g.h0);
             const F2 y = make_float2(g.lo1 + (float)j0 * g.h1, g.lo1 + (float)j1 * g.h1);
-            const Sep2 cxh = (VK == VK_VORTEX2D) ? sep_factors2(xh) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
+            const VCol cxh = (VK == VK_VORTEX2D) ? vortex_col(xh.x, sc.mod[0]) : VCol{0.f, 0.f, 0.f, 0.f, 0.f};
             const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
             F2 phi, px, py;
             node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,

@@ -40,32 +40,22 @@ template <int CR> struct Tile3 {
 };
 
 // v(x, t+dt) and Dv at the two nodes (x, y, z0) and (x, y, z1) of a thread.  For
-// DEFORM3D the x- and y-factors of every term are products fixed per thread (Pre3),
-// so only the z-factors are evaluated per node.
-struct Pre3 { float v0, v1, v2, sxy, d1, d2, d3, d5, d6, d7; };
+// DEFORM3D the xy products of every term (P1..P7 of deform_terms) are fixed per thread
+// (Pre3), so only the z-factors are evaluated per node.
+struct Pre3 { float P1, P2, P3, P4, P5, P6, P7; };
 
 template <int VK>
-__device__ __forceinline__ Pre3 pre3(const StageCoef &sc, float x, float y)
+__device__ __forceinline__ Pre3 pre3(float x, float y)
 {
     Pre3 p{};
     if (VK == VK_DEFORM3D) {
-        float sx, cx, sy, cy;
-        sincospi_f(x, &sx, &cx);
-        sincospi_f(y, &sy, &cy);
-        const float c = sc.mod[0], cp = c * kPi;
-        const float s2x = 2.f * sx * cx, s2y = 2.f * sy * cy;
-        const float sx2 = sx * sx, sy2 = sy * sy;
-        const float c2x = 1.f - 2.f * sx2, c2y = 1.f - 2.f * sy2;
-        p.v0 = 2.f * c * sx2 * s2y;
-        p.v1 = -c * s2x * sy2;
-        p.v2 = -c * s2x * s2y;
-        p.sxy = cp * s2x * s2y;
-        p.d1 = 4.f * cp * sx2 * c2y;
-        p.d2 = 4.f * cp * sx2 * s2y;
-        p.d3 = -2.f * cp * c2x * sy2;
-        p.d5 = -2.f * cp * s2x * sy2;
-        p.d6 = -2.f * cp * c2x * s2y;
-        p.d7 = -2.f * cp * s2x * c2y;
+        float Axn, Bx, Ay, By;
+        __sincosf(__fmaf_rn(x, -2.f * kPi, kPi), &Axn, &Bx);  // -A(x), B(x)
+        sincos_turn(y, &Ay, &By);
+        const float Sx2 = Bx + 1.f, Bxm = (-2.f * kPi) * Bx;
+        const float Sy = __fmaf_rn(By, 0.5f, 0.5f), By2 = (2.f * kPi) * By;
+        p.P1 = Sx2 * Ay; p.P2 = Axn * Sy; p.P3 = Axn * Ay; p.P4 = Sx2 * By2;
+        p.P5 = Bxm * Sy; p.P6 = Bxm * Ay; p.P7 = Axn * By2;
     }
     return p;
 }
@@ -75,24 +65,12 @@ __device__ __forceinline__ V3p stage1_pair(const VelParams &vp, const StageCoef 
                                            F2 x, F2 y, F2 z)
 {
     if (VK != VK_DEFORM3D) return vel3d_pair<VK>(vp, sc, 0, x, y, z);
-    F2 sz, cz;
-    sincospi2(z, sz, cz);
-    const F2 s2z = mul2(bc(2.f), mul2(sz, cz)), sz2 = mul2(sz, sz);
-    const F2 c2z = fma2(bc(-2.f), sz2, bc(1.f));
+    F2 Az, Bz;
+    sincos_turn2(z, Az, Bz);
+    const float c = sc.mod[0], h = 0.5f * c;
     V3p r;
-    const F2 sss = mul2(bc(p.sxy), s2z);
-    r.v[0] = mul2(bc(p.v0), s2z);
-    r.v[1] = mul2(bc(p.v1), s2z);
-    r.v[2] = mul2(bc(p.v2), sz2);
-    r.d[0] = mul2(bc(2.f), sss);
-    r.d[1] = mul2(bc(p.d1), s2z);
-    r.d[2] = mul2(bc(p.d2), c2z);
-    r.d[3] = mul2(bc(p.d3), s2z);
-    r.d[4] = neg2(sss);
-    r.d[5] = mul2(bc(p.d5), c2z);
-    r.d[6] = mul2(bc(p.d6), sz2);
-    r.d[7] = mul2(bc(p.d7), sz2);
-    r.d[8] = r.d[4];
+    deform_terms(bc(p.P1), bc(p.P2), bc(p.P3), bc(p.P4), bc(p.P5), bc(p.P6), bc(p.P7),
+                 mul2(bc(c), Az), fma2(Bz, bc(h), bc(h)), mul2(bc(2.f * kPi * c), Bz), r);
     return r;
 }
 
@@ -177,7 +155,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
     const int i = min(x0 + (int)threadIdx.x, g.n0 - 1), j = min(y0 + (int)threadIdx.y, g.n1 - 1);
     const float x = g.lo0 + (float)i * g.h0;
     const float y = g.lo1 + (float)j * g.h1;
-    const Pre3 pre = pre3<VK>(sc, x, y);
+    const Pre3 pre = pre3<VK>(x, y);
     const int64_t P = g.plane;
     const int64_t zstride = (int64_t)g.n1 * g.pitch;
     const int zend = min(z0 + TZ, g.n2);
@@ -363,7 +341,9 @@ k_recon3d_tma(float *__restrict__ buf, Geom g, const __grid_constant__ CUtensorM
     __shared__ __align__(128) float t[2][QZ][QH][QW];  // psi_y, psi_z
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x + QX * threadIdx.y;
-    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = blockIdx.z * QZ;
+    // z-slabs in reverse: the step kernel wrote the last slabs last, so their psi_y, psi_z
+    // are the ones still in L2
+    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = (gridDim.z - 1 - blockIdx.z) * QZ;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (tid == 0) {
@@ -382,6 +362,23 @@ k_recon3d_tma(float *__restrict__ buf, Geom g, const __grid_constant__ CUtensorM
     if (i >= g.n0 || j >= g.n1) return;
     const int64_t P = g.plane;
     const int nz = min(QZ, g.n2 - z0);
+    if (x0 >= 1 && x0 + QX <= g.n0 - 1 && y0 >= 1 && y0 + QY <= g.n1 - 1) {
+        // every node of the block is interior in x and y: central differences only (the
+        // same operations dline performs there)
+        const int tx = threadIdx.x + QHX, ty = threadIdx.y + QHY;
+        int64_t o = ((int64_t)z0 * g.n1 + j) * g.pitch + i;
+        const int64_t zs = (int64_t)g.n1 * g.pitch;
+        for (int dz = 0; dz < nz; ++dz, o += zs) {
+            const float(*Y)[QW] = t[0][dz];
+            const float(*Z)[QW] = t[1][dz];
+            buf[4 * P + o] = dcentral(Y[ty][tx + 1], Y[ty][tx - 1], g.i2h0);
+            buf[5 * P + o] = dcentral(Z[ty][tx + 1], Z[ty][tx - 1], g.i2h0);
+            buf[6 * P + o] = dcentral(Z[ty + 1][tx], Z[ty - 1][tx], g.i2h1);
+            buf[7 * P + o] = dcentral(dcentral(Z[ty + 1][tx + 1], Z[ty - 1][tx + 1], g.i2h1),
+                                      dcentral(Z[ty + 1][tx - 1], Z[ty - 1][tx - 1], g.i2h1), g.i2h0);
+        }
+        return;
+    }
     for (int dz = 0; dz < nz; ++dz) {
         auto Y = [&](int q, int r) { return t[0][dz][r - y0 + QHY][q - x0 + QHX]; };
         auto Z = [&](int q, int r) { return t[1][dz][r - y0 + QHY][q - x0 + QHX]; };
