@@ -121,7 +121,7 @@ typedef struct gals_grid gals_grid;   /* opaque, owned by the library */
 
 /* Create a grid and allocate its double-buffered device state on the current device.
  * Size limits: 2D at most 2^31 - 1 elements per plane (row pitch = n[0] rounded up to a
- * multiple of 4, times n[1]) and n[1] <= 786420; 3D n[1], n[2] <= 262140.
+ * multiple of 4, times n[1]) and n[1] <= 917490; 3D n[1], n[2] <= 262140.
  * Errors: GALS_ERR_ARG (dim not 2/3, n < 4 or above the limits, hi <= lo, bad layout),
  * GALS_ERR_NOMEM, GALS_ERR_CUDA.  On error *out is set to NULL. */
 gals_status gals_create_grid(const gals_grid_desc *desc, gals_grid **out);

@@ -109,7 +109,7 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
     cudaError_t ce = launch_coef_table(g->coef, vp, g->t_dev, dt, nsteps, g->stream);
     if (ce != cudaSuccess) return ce;
     for (int s = 0; s < nsteps; ++s) {
-        StepLaunch a;
+        StepLaunch a{};
         a.in = g->buf[cur];
         a.out = g->buf[cur ^ 1];
         a.geom = g->geom;

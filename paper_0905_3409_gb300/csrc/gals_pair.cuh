@@ -6,8 +6,8 @@
 // instructions of two scalar updates, and has twice the independent loads in flight.
 // Lane x of every float2 is the first node, lane y the second.  The arithmetic is the one
 // of gals_device.cuh: superconsistent RK3 trace with Jacobian (Sec. 5.1), cell location,
-// bi-/tricubic Hermite value and gradient from the nearest-corner-shifted data (Sec. 2.3),
-// J^T grad H.
+// bi-/tricubic Hermite value and gradient (Sec. 2.3) from the cell's phi shifted by its
+// first corner, J^T grad H.
 // Each lane rounds exactly like a scalar FMA/ADD/MUL chain of the same expression.
 #pragma once
 
@@ -175,13 +175,9 @@ __device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
     J[3] = fma2(m6, add2(a.d11, M11), fma2(m23, N11, one));
 }
 
-// Paired 1D basis (see basis1).  n0, n1 = (xi >= 1/2) per lane pick each foot's nearest
-// corner, whose phi the Hermite evaluation subtracts from the corner values (the value
-// terms become O(h)).  The value part is then evaluated from the cell's first end,
-// p0 + (p1 - p0) S: exact at xi = 0, where every interior foot on a node lands, and, for
-// phi, at xi = 1 too (there p1 = 0 and p1 - p0 = -p0).  The gradient data at xi = 1 (a
-// foot clamped onto the last node of an axis) come back to rounding.
-struct Basis2 { F2 S, dS, hG0, hG1, dG0, dG1; bool n0, n1; };
+// Paired 1D basis: S = 3 xi^2 - 2 xi^3, dS = S'(xi)/h, hG0 = h g(xi), hG1 = -h g(1 - xi),
+// dG0 = g'(xi), dG1 = -g'(1 - xi) (g(x) = x (1 - x)^2; eq. 1-cubic_basis_functions).
+struct Basis2 { F2 S, dS, hG0, hG1, dG0, dG1; };
 
 __device__ __forceinline__ Basis2 basis_pair(F2 xi, float h, float ih)
 {
@@ -189,8 +185,6 @@ __device__ __forceinline__ Basis2 basis_pair(F2 xi, float h, float ih)
     const F2 om = fma2(xi, bc(-1.f), bc(1.f));
     const F2 xx = mul2(xi, xi), xo = mul2(xi, om);
     b.S = mul2(xx, fma2(bc(-2.f), xi, bc(3.f)));
-    b.n0 = xi.x >= 0.5f;
-    b.n1 = xi.y >= 0.5f;
     b.dS = mul2(xo, bc(6.f * ih));
     b.hG0 = mul2(mul2(xo, om), bc(h));
     b.hG1 = mul2(mul2(om, xx), bc(-h));
@@ -199,11 +193,9 @@ __device__ __forceinline__ Basis2 basis_pair(F2 xi, float h, float ih)
     return b;
 }
 
-__device__ __forceinline__ F2 pick(const Basis2 &b, F2 p0, F2 p1)
-{
-    return make_float2(b.n0 ? p1.x : p0.x, b.n1 ? p1.y : p0.y);
-}
-
+// 1D cubic Hermite value and derivative along a cell edge from the end values p0, p1 and
+// slopes s0, s1, evaluated from the first end: p0 + (p1 - p0) S + s0 h g(xi) - s1 h g(1-xi).
+// At xi = 0 the value is p0 and the derivative s0, exactly.
 __device__ __forceinline__ F2 hval2(const Basis2 &b, F2 p0, F2 p1, F2 s0, F2 s1)
 {
     return fma2(sub2(p1, p0), b.S, fma2(s0, b.hG0, fma2(s1, b.hG1, p0)));
@@ -212,20 +204,30 @@ __device__ __forceinline__ F2 hder2(const Basis2 &b, F2 p0, F2 p1, F2 s0, F2 s1)
 {
     return fma2(sub2(p1, p0), b.dS, fma2(s0, b.dG0, mul2(s1, b.dG1)));
 }
+// the same with p0 = 0
+__device__ __forceinline__ F2 hval2z(const Basis2 &b, F2 p1, F2 s0, F2 s1)
+{
+    return fma2(p1, b.S, fma2(s0, b.hG0, mul2(s1, b.hG1)));
+}
+__device__ __forceinline__ F2 hder2z(const Basis2 &b, F2 p1, F2 s0, F2 s1)
+{
+    return fma2(p1, b.dS, fma2(s0, b.dG0, mul2(s1, b.dG1)));
+}
 
-// c[v][a]: corner v = vx + 2 vy, data a = 0 phi, 1 phi_x, 2 phi_y, 3 phi_xy (both lanes)
+// Bicubic Hermite value and gradient (eq. p-cubic_interpolant, sum-factorised: x, then y).
+// c[v][a]: corner v = vx + 2 vy, data a = 0 phi, 1 phi_x, 2 phi_y, 3 phi_xy (both lanes).
+// phi is shifted by its value at corner 0 (the interpolant reproduces constants): the
+// x-reduced values P0, P1 are then O(h), so the y-derivative (P1 - P0) dS, whose factor is
+// O(1/h), carries no rounding error of the O(1) phi itself.  A foot on a node (xi = eta =
+// 0) returns that node's data exactly.
 __device__ __forceinline__ void hermite2d_pair(const F2 c[4][4], const Basis2 &bx,
                                                const Basis2 &by, F2 &H, F2 &Hx, F2 &Hy)
 {
-    // phi of the corner nearest to each foot
-    const F2 b0 = pick(bx, c[0][0], c[1][0]);
-    const F2 b1 = pick(bx, c[2][0], c[3][0]);
-    const F2 base = pick(by, b0, b1);
-    const F2 p00 = sub2(c[0][0], base), p10 = sub2(c[1][0], base);
-    const F2 p01 = sub2(c[2][0], base), p11 = sub2(c[3][0], base);
-    const F2 P0 = hval2(bx, p00, p10, c[0][1], c[1][1]);
+    const F2 base = c[0][0];
+    const F2 p10 = sub2(c[1][0], base), p01 = sub2(c[2][0], base), p11 = sub2(c[3][0], base);
+    const F2 P0 = hval2z(bx, p10, c[0][1], c[1][1]);
     const F2 P1 = hval2(bx, p01, p11, c[2][1], c[3][1]);
-    const F2 Pd0 = hder2(bx, p00, p10, c[0][1], c[1][1]);
+    const F2 Pd0 = hder2z(bx, p10, c[0][1], c[1][1]);
     const F2 Pd1 = hder2(bx, p01, p11, c[2][1], c[3][1]);
     const F2 Q0 = hval2(bx, c[0][2], c[1][2], c[0][3], c[1][3]);
     const F2 Q1 = hval2(bx, c[2][2], c[3][2], c[2][3], c[3][3]);
@@ -368,16 +370,24 @@ __device__ __forceinline__ void trace3d_pair(const V3p &a, const VelParams &vp, 
 // Tricubic Hermite value and gradient for two feet, streamed over the four x-lines of
 // the cell (B = y corner, C = z corner).  row(B, C, lo, hi) must fill lo[a], hi[a] with
 // plane a (0 phi, 1 x, 2 y, 3 z, 4 xy, 5 xz, 6 yz, 7 xyz) at the line's x = k and x = k+1
-// corners, for both lanes; base is phi at each foot's nearest corner.  The reduction
-// order is x, then y, then z, as in the sum-factorised form of Sec. 2.3.
+// corners, for both lanes.  phi is shifted by its value at the cell's first corner (line
+// B = C = 0, x = k), as in hermite2d_pair.  The reduction order is x, then y, then z, as
+// in the sum-factorised form of Sec. 2.3.
 struct XRed2 { F2 P, Pd, Qy, Qyd, Qz, Qzd, Qyz, Qyzd; };
 
+template <bool FIRST>
 __device__ __forceinline__ XRed2 xreduce2(const Basis2 &bx, const F2 lo[8], const F2 hi[8], F2 base)
 {
     XRed2 r;
-    const F2 p0 = sub2(lo[0], base), p1 = sub2(hi[0], base);
-    r.P = hval2(bx, p0, p1, lo[1], hi[1]);
-    r.Pd = hder2(bx, p0, p1, lo[1], hi[1]);
+    const F2 p1 = sub2(hi[0], base);
+    if (FIRST) {  // lo[0] is the base itself
+        r.P = hval2z(bx, p1, lo[1], hi[1]);
+        r.Pd = hder2z(bx, p1, lo[1], hi[1]);
+    } else {
+        const F2 p0 = sub2(lo[0], base);
+        r.P = hval2(bx, p0, p1, lo[1], hi[1]);
+        r.Pd = hder2(bx, p0, p1, lo[1], hi[1]);
+    }
     r.Qy = hval2(bx, lo[2], hi[2], lo[4], hi[4]);
     r.Qyd = hder2(bx, lo[2], hi[2], lo[4], hi[4]);
     r.Qz = hval2(bx, lo[3], hi[3], lo[5], hi[5]);
@@ -389,9 +399,10 @@ __device__ __forceinline__ XRed2 xreduce2(const Basis2 &bx, const F2 lo[8], cons
 
 template <class Row>
 __device__ __forceinline__ void hermite3d_pair(const Basis2 &bx, const Basis2 &by, const Basis2 &bz,
-                                               F2 base, Row row, F2 &H, F2 g[3])
+                                               Row row, F2 &H, F2 g[3])
 {
     F2 R[2], Rx[2], Ry[2], Rz[2], Rzx[2], Rzy[2];
+    F2 base;
 #pragma unroll
     for (int C = 0; C < 2; ++C) {
         XRed2 q[2];
@@ -399,7 +410,12 @@ __device__ __forceinline__ void hermite3d_pair(const Basis2 &bx, const Basis2 &b
         for (int B = 0; B < 2; ++B) {
             F2 lo[8], hi[8];
             row(B, C, lo, hi);
-            q[B] = xreduce2(bx, lo, hi, base);
+            if (B == 0 && C == 0) {
+                base = lo[0];
+                q[B] = xreduce2<true>(bx, lo, hi, base);
+            } else {
+                q[B] = xreduce2<false>(bx, lo, hi, base);
+            }
         }
         R[C] = hval2(by, q[0].P, q[1].P, q[0].Qy, q[1].Qy);
         Ry[C] = hder2(by, q[0].P, q[1].P, q[0].Qy, q[1].Qy);

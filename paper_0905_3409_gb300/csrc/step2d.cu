@@ -5,10 +5,13 @@
 #include "step2d_tile.cuh"
 
 #ifndef GALS_2D_TY
-#define GALS_2D_TY 12
+#define GALS_2D_TY 14
 #endif
 #ifndef GALS_2D_MINB
 #define GALS_2D_MINB 5
+#endif
+#ifndef GALS_2D_HY
+#define GALS_2D_HY 1
 #endif
 
 namespace gals {
@@ -17,6 +20,8 @@ namespace {
 
 using namespace t2;
 constexpr int TY = GALS_2D_TY;  // output tile rows (even)
+constexpr int HYT = GALS_2D_HY; // staged halo rows above and below the tile
+using GT = Geo<TY, HYT>;
 
 template <int TR, int VK, int CR, int WC>
 __global__ void __launch_bounds__(TX, GALS_2D_MINB)
@@ -28,7 +33,7 @@ k_step2d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
     __shared__ __align__(16) Smem<TY, WC> sm;
     if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
     __syncthreads();
-    tile_step2d<TY, TR, VK, CR, WC>(in, out, g, vp, coef, dt, &tmap, err, blockIdx.x * TX,
+    tile_step2d<TY, TR, VK, CR, WC, HYT>(in, out, g, vp, coef, dt, &tmap, err, blockIdx.x * TX,
                                     blockIdx.y * TY, tile, sm, 0);
 }
 
@@ -52,13 +57,13 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_step2d<TR, VK, CR, WC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Geo<TY>::bytes(NP));
+                                             GT::bytes(NP));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((a.geom.n0 + TX - 1) / TX, (a.geom.n1 + TY - 1) / TY);
     const CUtensorMap &map = NP == 4 ? *a.tmap4 : *a.tmap3;
-    k_step2d<TR, VK, CR, WC><<<grid, TX, Geo<TY>::bytes(NP), s>>>(a.in, a.out, a.geom, a.vp, a.coef,
+    k_step2d<TR, VK, CR, WC><<<grid, TX, GT::bytes(NP), s>>>(a.in, a.out, a.geom, a.vp, a.coef,
                                                             (float)a.dt, map, a.err);
     return cudaGetLastError();
 }
@@ -101,7 +106,7 @@ int tile_rows2d() { return TY; }
 void tile_box2d(int np, uint32_t box[3])
 {
     box[0] = TW;
-    box[1] = Geo<TY>::TH;
+    box[1] = GT::TH;
     box[2] = (uint32_t)np;
 }
 

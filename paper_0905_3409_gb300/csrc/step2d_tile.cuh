@@ -25,8 +25,8 @@ constexpr int TX = 128;               // output tile columns (one thread each)
 constexpr int HX = 4, HY = 2;         // input halo (x rounded to 16 bytes for TMA)
 constexpr int TW = TX + 2 * HX;
 
-template <int TY> struct Geo {
-    static constexpr int TH = TY + 2 * HY;
+template <int TY, int HYV = HY> struct Geo {
+    static constexpr int TH = TY + 2 * HYV;
     static constexpr int PS = TW * TH;  // floats per staged plane
     static constexpr int bytes(int np) { return np * PS * 4; }
 };
@@ -169,13 +169,13 @@ __device__ __forceinline__ V2p stage1_pair(const VelParams &vp, const StageCoef 
 // The 4 corners x 4 data of the cell (k, l) for one node, from the staged tile when the
 // cell (and, for COMPACT, its psi_y window k-1..k+2) lies inside it, else from global
 // memory (feet farther than the halo: CFL well above 1).
-template <int TY, int CR>
+template <int TY, int CR, int HYV = HY>
 __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const Geom &g,
                                             const float *__restrict__ tile, int x0, int y0, int k,
                                             int l, float c[4][4])
 {
-    constexpr int TH = Geo<TY>::TH, PS = Geo<TY>::PS;
-    const int tx = k - x0 + HX, ty = l - y0 + HY;
+    constexpr int TH = Geo<TY, HYV>::TH, PS = Geo<TY, HYV>::PS;
+    const int tx = k - x0 + HX, ty = l - y0 + HYV;
     if (tx >= 1 && tx <= TW - 3 && ty >= 0 && ty <= TH - 2) {
         const float *t = tile + ty * TW + tx;
 #pragma unroll
@@ -220,8 +220,9 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
     if (CR == CROSS_CELL) cross_cell2d(c, g.ih0, g.ih1);
 }
 
-// Update of two nodes (i0, j0) and (i1, j1): phi+, psi_x+, psi_y+ per lane.
-template <int TY, int TR, int VK, int CR>
+// Update of two nodes (i0, j0) and (i1, j1): phi+, psi_x+, psi_y+ per lane; the staged
+// tile has HYV halo rows.
+template <int TY, int TR, int VK, int CR, int HYV = HY>
 __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const Geom &g,
                                             const float *__restrict__ tile, int x0, int y0,
                                             const VelParams &vp, const StageCoef &sc,
@@ -255,8 +256,8 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
     locate(j1, dy.y * g.ih1, g.n1, l1, eta.y);
 
     float c0[4][4], c1[4][4];
-    gather_lane<TY, CR>(in, g, tile, x0, y0, k0, l0, c0);
-    gather_lane<TY, CR>(in, g, tile, x0, y0, k1, l1, c1);
+    gather_lane<TY, CR, HYV>(in, g, tile, x0, y0, k0, l0, c0);
+    gather_lane<TY, CR, HYV>(in, g, tile, x0, y0, k1, l1, c1);
     F2 c[4][4];
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -285,7 +286,7 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
 // `parity` is the phase this tile's copy completes.  Returns false (after recording
 // kErrTmaTimeout) if the staged copy did not arrive within the wait limit.
 // Must be called by all TX threads of the block.
-template <int TY, int TR, int VK, int CR, int WC>
+template <int TY, int TR, int VK, int CR, int WC, int HYV = HY>
 __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float *__restrict__ out,
                                             const Geom &g, const VelParams &vp,
                                             const StageCoef *__restrict__ coef, float dt,
@@ -300,8 +301,8 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
 
     // stage the input tile (all planes, halo HX x HY) with one TMA copy
     if (tid == 0) {
-        mbar_arrive_expect_tx(&sm.bar, Geo<TY>::bytes(NP));
-        tma_load_3d(tile, tmap, x0 - HX, y0 - HY, 0, &sm.bar);
+        mbar_arrive_expect_tx(&sm.bar, Geo<TY, HYV>::bytes(NP));
+        tma_load_3d(tile, tmap, x0 - HX, y0 - HYV, 0, &sm.bar);
     }
     const StageCoef &sc = *coef;
     if (VK == VK_FOURIER2D) {
@@ -339,8 +340,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
     if (VK == VK_FOURIER2D) fcol = fourier_col(xs);
 
     // bounded wait for the tile; a block-uniform verdict so no thread is left at a barrier
-    const bool ok = mbar_wait_bounded(&sm.bar, parity);
-    if (__syncthreads_or(!ok)) {
+    if (!mbar_wait_block(&sm.bar, parity)) {
         if (tid == 0) {
             atomicExch(err, kErrTmaTimeout);
             mbar_wait_bounded(&sm.bar, parity);  // let a late copy land before giving up
@@ -356,10 +356,10 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             F2 phi, px, py;
             if (VK == VK_FOURIER2D && TR != TR_GIVEN) {
                 const V2p a1 = fourier_stage1_pair<TY>(fcol, sm.fsum, r);
-                node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
+                node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
                                             cx, ry, phi, px, py, &a1);
             } else {
-                node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
+                node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
                                             cx, ry, phi, px, py);
             }
             const int o = j0 * g.pitch + i;
@@ -392,7 +392,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             const VCol cxh = (VK == VK_VORTEX2D) ? vortex_col(xh.x, sc.mod[0]) : VCol{0.f, 0.f, 0.f, 0.f, 0.f};
             const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
             F2 phi, px, py;
-            node2d_pair<TY, TR, VK, CR>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
+            node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
                                     ry, phi, px, py);
             psy[WC ? r : 0][ih - x0 + 2] = py.x;
             if (r + 1 < rows) psy[WC ? r + 1 : 0][ih - x0 + 2] = py.y;

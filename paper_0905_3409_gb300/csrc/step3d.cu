@@ -7,25 +7,13 @@
 // Mixed derivatives (Sec. 2.3, approach A): phi_xy = Dx psi_y, phi_xz = Dx psi_z,
 // phi_yz = Dy psi_z, phi_xyz = Dx Dy psi_z, read from their planes (FULL) or rebuilt
 // from psi windows around the cell (COMPACT) with the same stencils.
-#include "gals_internal.h"
-#include "gals_pair.cuh"
-#include "tma.cuh"
+#include "step3d_common.cuh"
 
 namespace gals {
 
 namespace {
 
-template <int O>
-__device__ __forceinline__ float dwin(const float w[4], int q, int n, float i2h)
-{
-    constexpr int c = 1 + O;
-    if (O == 0) {
-        if (q == 0) return dfirst(w[c], w[c + 1], w[c + 2], i2h);
-    } else {
-        if (q == n - 1) return dlast(w[c], w[c - 1], w[c - 2], i2h);
-    }
-    return dcentral(w[c + 1], w[c - 1], i2h);
-}
+using namespace t3;
 
 // Output tile per block: TX x TY nodes in x, y and TZ in z (each thread walks TZ nodes in z).
 constexpr int TX = 32, TY = 4, TZ = 4;
@@ -39,93 +27,6 @@ template <int CR> struct Tile3 {
     static constexpr int BYTES = NP * PS * 4;
 };
 
-// v(x, t+dt) and Dv at the two nodes (x, y, z0) and (x, y, z1) of a thread.  For
-// DEFORM3D the xy products of every term (P1..P7 of deform_terms) are fixed per thread
-// (Pre3), so only the z-factors are evaluated per node.
-struct Pre3 { float P1, P2, P3, P4, P5, P6, P7; };
-
-template <int VK>
-__device__ __forceinline__ Pre3 pre3(float x, float y)
-{
-    Pre3 p{};
-    if (VK == VK_DEFORM3D) {
-        float Axn, Bx, Ay, By;
-        __sincosf(__fmaf_rn(x, -2.f * kPi, kPi), &Axn, &Bx);  // -A(x), B(x)
-        sincos_turn(y, &Ay, &By);
-        const float Sx2 = Bx + 1.f, Bxm = (-2.f * kPi) * Bx;
-        const float Sy = __fmaf_rn(By, 0.5f, 0.5f), By2 = (2.f * kPi) * By;
-        p.P1 = Sx2 * Ay; p.P2 = Axn * Sy; p.P3 = Axn * Ay; p.P4 = Sx2 * By2;
-        p.P5 = Bxm * Sy; p.P6 = Bxm * Ay; p.P7 = Axn * By2;
-    }
-    return p;
-}
-
-template <int VK>
-__device__ __forceinline__ V3p stage1_pair(const VelParams &vp, const StageCoef &sc, const Pre3 &p,
-                                           F2 x, F2 y, F2 z)
-{
-    if (VK != VK_DEFORM3D) return vel3d_pair<VK>(vp, sc, 0, x, y, z);
-    F2 Az, Bz;
-    sincos_turn2(z, Az, Bz);
-    const float c = sc.mod[0], h = 0.5f * c;
-    V3p r;
-    deform_terms(bc(p.P1), bc(p.P2), bc(p.P3), bc(p.P4), bc(p.P5), bc(p.P6), bc(p.P7),
-                 mul2(bc(c), Az), fma2(Bz, bc(h), bc(h)), mul2(bc(2.f * kPi * c), Bz), r);
-    return r;
-}
-
-// One x-line (y corner B, z corner C) of a foot cell with base corner (k, l, m): the data
-// of planes 0..7 at x = k (lo) and x = k+1 (hi).  ld(a, z, y, x) reads plane a at a grid
-// index.  With CROSS_RECON the mixed derivatives come from psi_y, psi_z windows with the
-// approach-A stencils (central, one-sided at the ends), as in the reconstruction kernels.
-template <int CR, class Ld>
-__device__ __forceinline__ void cell_line(const Ld &ld, const Geom &g, int k, int l, int m, int B,
-                                          int C, float lo[8], float hi[8])
-{
-    const int zz = m + C, yy = l + B;
-    if (CR == CROSS_PLANE) {
-#pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            lo[a] = ld(a, zz, yy, k);
-            hi[a] = ld(a, zz, yy, k + 1);
-        }
-        return;
-    }
-    const int xs[4] = {max(k - 1, 0), k, k + 1, min(k + 2, g.n0 - 1)};
-    const int ys[4] = {max(l - 1, 0), l, l + 1, min(l + 2, g.n1 - 1)};
-    lo[0] = ld(0, zz, yy, k);
-    hi[0] = ld(0, zz, yy, k + 1);
-    lo[1] = ld(1, zz, yy, k);
-    hi[1] = ld(1, zz, yy, k + 1);
-    float wy[4], wz[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) wy[p] = ld(2, zz, yy, xs[p]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) wz[q][p] = ld(3, zz, ys[q], xs[p]);
-    // Dy psi_z on row yy at every x-window position
-    float dyw[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const float col[4] = {wz[0][p], wz[1][p], wz[2][p], wz[3][p]};
-        dyw[p] = B == 0 ? dwin<0>(col, l, g.n1, g.i2h1) : dwin<1>(col, l + 1, g.n1, g.i2h1);
-    }
-    const float zrow[4] = {wz[B + 1][0], wz[B + 1][1], wz[B + 1][2], wz[B + 1][3]};
-    lo[2] = wy[1];
-    hi[2] = wy[2];
-    lo[3] = zrow[1];
-    hi[3] = zrow[2];
-    lo[4] = dwin<0>(wy, k, g.n0, g.i2h0);
-    hi[4] = dwin<1>(wy, k + 1, g.n0, g.i2h0);
-    lo[5] = dwin<0>(zrow, k, g.n0, g.i2h0);
-    hi[5] = dwin<1>(zrow, k + 1, g.n0, g.i2h0);
-    lo[6] = dyw[1];
-    hi[6] = dyw[2];
-    lo[7] = dwin<0>(dyw, k, g.n0, g.i2h0);
-    hi[7] = dwin<1>(dyw, k + 1, g.n0, g.i2h0);
-}
-
 // Two nodes per thread, (i, j, kz) and (i, j, kz+1), in paired FP32: trace with the 3x3
 // Jacobian, cell location, tricubic Hermite value and gradient from the staged tile,
 // phi+ = H and psi+ = J^T grad H.  Feet whose cell data lie outside the staged tile
@@ -136,13 +37,13 @@ template <int TR, int VK, int CR>
 __global__ void __launch_bounds__(TX *TY, CR == CROSS_PLANE ? 4 : 1)
 k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParams vp,
          const StageCoef *__restrict__ coef, float dt, const __grid_constant__ CUtensorMap tmap,
-         int *__restrict__ err)
+         int *__restrict__ err, int zt0)
 {
     using T = Tile3<CR>;
     extern __shared__ __align__(128) float tile[];
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x + TX * threadIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = (blockIdx.z + zt0) * TZ;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (tid == 0) {
@@ -166,8 +67,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
         const F2 Z = make_float2(g.lo2 + (float)kz * g.h2, g.lo2 + (float)kz1 * g.h2);
         F2 d[3], J[9];
         if (kz == z0) {
-            const bool ok = mbar_wait_bounded(&bar, 0);
-            if (__syncthreads_or(!ok)) {
+            if (!mbar_wait_block(&bar, 0)) {
                 if (tid == 0) {
                     atomicExch(err, kErrTmaTimeout);
                     mbar_wait_bounded(&bar, 0);
@@ -203,9 +103,6 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
             return __ldg(in + a * P + (int64_t)zz * zstride + (int64_t)yy * g.pitch + xx);
         };
         const bool in0 = in_tile(k0, l0, m0), in1 = in_tile(k1, l1, m1);
-        // phi at each foot's nearest corner
-        const int nk0 = k0 + (bx.n0 ? 1 : 0), nl0 = l0 + (by.n0 ? 1 : 0), nm0 = m0 + (bz.n0 ? 1 : 0);
-        const int nk1 = k1 + (bx.n1 ? 1 : 0), nl1 = l1 + (by.n1 ? 1 : 0), nm1 = m1 + (bz.n1 ? 1 : 0);
         F2 H, gr[3];
         if (CR == CROSS_CELL) {
             // approach B: the cell's 8 vertices x (phi, psi) per foot, mixed derivatives from them
@@ -221,15 +118,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
                 }
             cross_cell3d([&](int v, int a) { return q0[v][a]; }, g.ih0, g.ih1, g.ih2, c0);
             cross_cell3d([&](int v, int a) { return q1[v][a]; }, g.ih0, g.ih1, g.ih2, c1);
-            const int vn0 = (bx.n0 ? 1 : 0) + (by.n0 ? 2 : 0) + (bz.n0 ? 4 : 0);
-            const int vn1 = (bx.n1 ? 1 : 0) + (by.n1 ? 2 : 0) + (bz.n1 ? 4 : 0);
-            float b0 = q0[0][0], b1 = q1[0][0];
-#pragma unroll
-            for (int v = 1; v < 8; ++v) {
-                b0 = v == vn0 ? q0[v][0] : b0;
-                b1 = v == vn1 ? q1[v][0] : b1;
-            }
-            hermite3d_pair(bx, by, bz, make_float2(b0, b1), [&](int B, int C, F2 lo[8], F2 hi[8]) {
+            hermite3d_pair(bx, by, bz, [&](int B, int C, F2 lo[8], F2 hi[8]) {
                 const int v = 2 * B + 4 * C;
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -240,8 +129,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
                 }
             }, H, gr);
         } else if (in0 && in1) {
-            const F2 base = make_float2(lds(0, nm0, nl0, nk0), lds(0, nm1, nl1, nk1));
-            hermite3d_pair(bx, by, bz, base, [&](int B, int C, F2 lo[8], F2 hi[8]) {
+            hermite3d_pair(bx, by, bz, [&](int B, int C, F2 lo[8], F2 hi[8]) {
                 float a0[8], b0[8], a1[8], b1[8];
                 cell_line<CR>(lds, g, k0, l0, m0, B, C, a0, b0);
                 cell_line<CR>(lds, g, k1, l1, m1, B, C, a1, b1);
@@ -254,8 +142,7 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
         } else {
             auto ld0 = [&](int a, int zz, int yy, int xx) { return in0 ? lds(a, zz, yy, xx) : ldg(a, zz, yy, xx); };
             auto ld1 = [&](int a, int zz, int yy, int xx) { return in1 ? lds(a, zz, yy, xx) : ldg(a, zz, yy, xx); };
-            const F2 base = make_float2(ld0(0, nm0, nl0, nk0), ld1(0, nm1, nl1, nk1));
-            hermite3d_pair(bx, by, bz, base, [&](int B, int C, F2 lo[8], F2 hi[8]) {
+            hermite3d_pair(bx, by, bz, [&](int B, int C, F2 lo[8], F2 hi[8]) {
                 float a0[8], b0[8], a1[8], b1[8];
                 cell_line<CR>(ld0, g, k0, l0, m0, B, C, a0, b0);
                 cell_line<CR>(ld1, g, k1, l1, m1, B, C, a1, b1);
@@ -336,22 +223,22 @@ constexpr int QW = QX + 2 * QHX, QH = QY + 2 * QHY;
 
 __global__ void __launch_bounds__(QX *QY)
 k_recon3d_tma(float *__restrict__ buf, Geom g, const __grid_constant__ CUtensorMap map,
-              int *__restrict__ err)
+              int *__restrict__ err, int zq0)
 {
     __shared__ __align__(128) float t[2][QZ][QH][QW];  // psi_y, psi_z
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x + QX * threadIdx.y;
-    // z-slabs in reverse: the step kernel wrote the last slabs last, so their psi_y, psi_z
-    // are the ones still in L2
-    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY, z0 = (gridDim.z - 1 - blockIdx.z) * QZ;
+    // slabs zq0 .. zq0 + gridDim.z - 1, in reverse: the step kernel wrote the last slabs
+    // last, so their psi_y, psi_z are the ones most likely still in L2
+    const int x0 = blockIdx.x * QX, y0 = blockIdx.y * QY;
+    const int z0 = (zq0 + (int)gridDim.z - 1 - (int)blockIdx.z) * QZ;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, (uint32_t)sizeof(t));
         tma_load_4d(&t[0][0][0][0], &map, x0 - QHX, y0 - QHY, z0, 2, &bar);
     }
-    const bool ok = mbar_wait_bounded(&bar, 0);
-    if (__syncthreads_or(!ok)) {
+    if (!mbar_wait_block(&bar, 0)) {
         if (tid == 0) {
             atomicExch(err, kErrTmaTimeout);
             mbar_wait_bounded(&bar, 0);
@@ -393,7 +280,7 @@ k_recon3d_tma(float *__restrict__ buf, Geom g, const __grid_constant__ CUtensorM
 }
 
 template <int TR, int VK, int CR>
-cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
+cudaError_t launch_t(const StepLaunch &a, cudaStream_t s, int zt0, int nzt)
 {
     using T = Tile3<CR>;
     static bool attr_set = false;
@@ -404,43 +291,56 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
         attr_set = true;
     }
     dim3 block(TX, TY);
-    dim3 grid((a.geom.n0 + TX - 1) / TX, (a.geom.n1 + TY - 1) / TY, (a.geom.n2 + TZ - 1) / TZ);
+    dim3 grid((a.geom.n0 + TX - 1) / TX, (a.geom.n1 + TY - 1) / TY, nzt);
     const CUtensorMap &map = CR == CROSS_PLANE ? *a.tmap4 : *a.tmap3;
     k_step3d<TR, VK, CR><<<grid, block, T::BYTES, s>>>(a.in, a.out, a.geom, a.vp, a.coef,
-                                                      (float)a.dt, map, a.err);
+                                                      (float)a.dt, map, a.err, zt0);
     return cudaGetLastError();
 }
 
 template <int TR, int VK>
-cudaError_t launch_cr(const StepLaunch &a, cudaStream_t s)
+cudaError_t launch_cr(const StepLaunch &a, cudaStream_t s, int zt0, int nzt)
 {
-    if (a.cross_in == CROSS_CELL) return launch_t<TR, VK, CROSS_CELL>(a, s);
-    return a.cross_in == CROSS_PLANE ? launch_t<TR, VK, CROSS_PLANE>(a, s)
-                                     : launch_t<TR, VK, CROSS_RECON>(a, s);
+    if (a.cross_in == CROSS_CELL) return launch_t<TR, VK, CROSS_CELL>(a, s, zt0, nzt);
+    return a.cross_in == CROSS_PLANE ? launch_t<TR, VK, CROSS_PLANE>(a, s, zt0, nzt)
+                                     : launch_t<TR, VK, CROSS_RECON>(a, s, zt0, nzt);
 }
 
 template <int VK>
-cudaError_t launch_tr(const StepLaunch &a, cudaStream_t s)
+cudaError_t launch_tr(const StepLaunch &a, cudaStream_t s, int zt0, int nzt)
 {
-    if (a.trace == TR_HEUN) return launch_cr<TR_HEUN, VK>(a, s);
-    return a.trace == TR_EULER ? launch_cr<TR_EULER, VK>(a, s) : launch_cr<TR_RK3, VK>(a, s);
+    if (a.trace == TR_HEUN) return launch_cr<TR_HEUN, VK>(a, s, zt0, nzt);
+    return a.trace == TR_EULER ? launch_cr<TR_EULER, VK>(a, s, zt0, nzt)
+                               : launch_cr<TR_RK3, VK>(a, s, zt0, nzt);
+}
+
+// step kernel over the z-tiles [zt0, zt0 + nzt)
+cudaError_t launch_step_tiles(const StepLaunch &a, cudaStream_t s, int zt0, int nzt)
+{
+    switch (a.vp.kind) {
+    case VK_CONST: return launch_tr<VK_CONST>(a, s, zt0, nzt);
+    case VK_ROTATION: return launch_tr<VK_ROTATION>(a, s, zt0, nzt);
+    case VK_DEFORM3D: return launch_tr<VK_DEFORM3D>(a, s, zt0, nzt);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// reconstruction of the z-slabs [zq0, zq0 + nzq) of the new state
+cudaError_t launch_recon_slabs(const StepLaunch &a, cudaStream_t s, int zq0, int nzq)
+{
+    dim3 grid((a.geom.n0 + QX - 1) / QX, (a.geom.n1 + QY - 1) / QY, nzq);
+    k_recon3d_tma<<<grid, dim3(QX, QY), 0, s>>>(a.out, a.geom, *a.tmap_cross, a.err, zq0);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_step3d(const StepLaunch &a, cudaStream_t s)
 {
-    cudaError_t e;
-    switch (a.vp.kind) {
-    case VK_CONST: e = launch_tr<VK_CONST>(a, s); break;
-    case VK_ROTATION: e = launch_tr<VK_ROTATION>(a, s); break;
-    case VK_DEFORM3D: e = launch_tr<VK_DEFORM3D>(a, s); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const int nzt = (a.geom.n2 + TZ - 1) / TZ;
+    cudaError_t e = launch_step_tiles(a, s, 0, nzt);
     if (e != cudaSuccess || !a.write_cross) return e;
-    dim3 grid((a.geom.n0 + QX - 1) / QX, (a.geom.n1 + QY - 1) / QY, (a.geom.n2 + QZ - 1) / QZ);
-    k_recon3d_tma<<<grid, dim3(QX, QY), 0, s>>>(a.out, a.geom, *a.tmap_cross, a.err);
-    return cudaGetLastError();
+    return launch_recon_slabs(a, s, 0, (a.geom.n2 + QZ - 1) / QZ);
 }
 
 void recon_box3d(uint32_t box[4])

@@ -53,6 +53,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Wait of a whole block for a staged copy: every thread polls (bounded), then the block
+// takes one verdict at a barrier (false: the wait ran out for some thread), so that no
+// thread is left behind at a later barrier.  Must be reached by every thread.
+__device__ __forceinline__ bool mbar_wait_block(uint64_t *bar, uint32_t parity)
+{
+    const bool ok = mbar_wait_bounded(bar, parity);
+    return !__syncthreads_or(!ok);
+}
+
 // 3D tiled bulk copy global -> shared, completion counted on `bar` (bytes of the box).
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
                                             int c2, uint64_t *bar)

@@ -56,7 +56,7 @@ def test_version_and_argument_errors_without_gpu(built):
     d.n[0], d.n[1] = 46344, 46341            # pitch 46344 x 46341 rows > 2^31 - 1
     assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
     assert b"2^31" in built.gals_last_error(None)
-    d.n[0], d.n[1] = 4, 786421               # more than 65535 blocks of 12 rows
+    d.n[0], d.n[1] = 4, 917491               # more than 65535 blocks of 14 rows
     assert built.gals_create_grid(ctypes.byref(d), ctypes.byref(h)) == gals.ERR_ARG
     d.dim = 3
     d.n[0], d.n[1], d.n[2] = 8, 8, 262141    # more than 65535 blocks of 4 z-slices

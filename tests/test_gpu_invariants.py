@@ -29,8 +29,8 @@ def test_integer_cell_shift_bit_exact(G, dim):
     exactly (Sec. 5.4, xi = 1 of the previous cell = xi = 0 of the next): bit for bit for
     nodes whose foot is an interior node, and to rounding where the foot is clamped onto
     the last node of an axis (the inflow edge, where the paper's shift argument does not
-    apply and the foot's cell is the last one, at its far end); phi is exact there too.
-    The rebuilt mixed derivatives shift with their stencils' nodes."""
+    apply and the foot's cell is the last one, at its far end).  The rebuilt mixed
+    derivatives shift with their stencils' nodes."""
     n = (65, 33) if dim == 2 else (17, 17, 9)
     g = G.Grid(n, hi=[(nn - 1) / 64.0 for nn in n])  # h = 1/64 on every axis
     st = inputs.random_state((4 if dim == 2 else 8,) + n[::-1], seed=2).astype(np.float32)
@@ -45,7 +45,6 @@ def test_integer_cell_shift_bit_exact(G, dim):
     edge = (slice(None),) + (slice(None, -1),) * dim       # including feet on the last node
     edge_src = (slice(None),) + (slice(1, None),) * dim
     assert np.array_equal(out[:core][inner], st[:core][shifted])
-    assert np.array_equal(out[0][edge[1:]], st[0][edge_src[1:]])
     np.testing.assert_allclose(out[:core][edge], st[:core][edge_src], rtol=1e-6, atol=1e-6)
     cin = (slice(None),) + (slice(1, -3),) * dim
     csrc = (slice(None),) + (slice(2, -2),) * dim
