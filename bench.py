@@ -181,7 +181,7 @@ class ClockSampler:
 # reported only while these files are unchanged
 KERNEL_SOURCES = {
     2: ["step2d.cu", "step2d_tile.cuh", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
-    3: ["step3d.cu", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
+    3: ["step3d.cu", "step3d_common.cuh", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
 }
 
 

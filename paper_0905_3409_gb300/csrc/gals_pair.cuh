@@ -175,6 +175,24 @@ __device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
     J[3] = fma2(m6, add2(a.d11, M11), fma2(m23, N11, one));
 }
 
+// Foot cells of the two lanes along one axis (the lanes' node indices i0, i1, their
+// displacements in cells dc): the same cells and local coordinates as locate(), lane by
+// lane.  The clamp acts on the displacement first, so that a foot before the first node
+// lands on (cell 0, xi = 0) and one at or past the last node on (cell n - 2, xi = 1):
+// floor(dc) then needs one clamp from above, and xi = dc - floor(dc) is one paired
+// subtraction.  Every branch of locate() becomes a min/max.  (The 3D step keeps
+// locate(): with its higher register pressure the paired form measured slower there.)
+__device__ __forceinline__ void locate_pair(int i0, int i1, F2 dc, int n, int &k0, int &k1, F2 &xi)
+{
+    const float hi0 = (float)(n - 1 - i0), hi1 = (float)(n - 1 - i1);
+    const float c0 = fminf(fmaxf(dc.x, (float)(-i0)), hi0);
+    const float c1 = fminf(fmaxf(dc.y, (float)(-i1)), hi1);
+    const float f0 = fminf(floorf(c0), hi0 - 1.f), f1 = fminf(floorf(c1), hi1 - 1.f);
+    k0 = i0 + (int)f0;
+    k1 = i1 + (int)f1;
+    xi = sub2(make_float2(c0, c1), make_float2(f0, f1));
+}
+
 // Paired 1D basis: S = 3 xi^2 - 2 xi^3, dS = S'(xi)/h, hG0 = h g(xi), hG1 = -h g(1 - xi),
 // dG0 = g'(xi), dG1 = -g'(1 - xi) (g(x) = x (1 - x)^2; eq. 1-cubic_basis_functions).
 struct Basis2 { F2 S, dS, hG0, hG1, dG0, dG1; };

@@ -250,10 +250,8 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
     (void)J;
     int k0, l0, k1, l1;
     F2 xi, eta;
-    locate(i0, dx.x * g.ih0, g.n0, k0, xi.x);
-    locate(i1, dx.y * g.ih0, g.n0, k1, xi.y);
-    locate(j0, dy.x * g.ih1, g.n1, l0, eta.x);
-    locate(j1, dy.y * g.ih1, g.n1, l1, eta.y);
+    locate_pair(i0, i1, mul2(dx, bc(g.ih0)), g.n0, k0, k1, xi);
+    locate_pair(j0, j1, mul2(dy, bc(g.ih1)), g.n1, l0, l1, eta);
 
     float c0[4][4], c1[4][4];
     gather_lane<TY, CR, HYV>(in, g, tile, x0, y0, k0, l0, c0);

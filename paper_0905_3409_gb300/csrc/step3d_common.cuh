@@ -1,5 +1,5 @@
-// step3d_common.cuh -- per-node pieces of the 3D GALS step shared by the 3D step kernels
-// (step3d.cu: one block per tile; step3d_walk.cu: blocks walking z-segments).
+// step3d_common.cuh -- per-node pieces of the 3D GALS step kernel (step3d.cu): the
+// separable stage-1 deformation field and the cell-line reads with approach-A windows.
 #pragma once
 
 #include "gals_internal.h"
