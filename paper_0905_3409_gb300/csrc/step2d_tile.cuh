@@ -8,7 +8,8 @@
 //
 // A block of 128 threads owns a tile of 128 columns x TY rows; each thread walks its
 // column two rows at a time in paired FP32 arithmetic (gals_pair.cuh).  The input tile
-// (all state planes, halo 4 columns x 2 rows) is staged into shared memory by one TMA copy;
+// (all state planes, halo 4 columns x HYV rows: 1 in the single-grid kernel, 2 in the
+// batched ones) is staged into shared memory by one TMA copy;
 // feet whose cell leaves the staged tile read global memory instead.  With WC the new
 // psi_y of the tile plus one halo column on each side (2 extra node updates per 128 per
 // row) stays in shared memory and phi_xy+ is written by the same kernel.
