@@ -517,23 +517,31 @@ def run_ours(args, wl):
     achieved = bpn * nodes / step_s / 1e9
     peak, peak_kind = measured_peaks()
 
-    # e2e through the C ABI with host buffers: per step, pinned host -> device state,
-    # one step, device -> pinned host state
+    # e2e through the C ABI with host buffers: per step, the whole state from pinned host
+    # memory, one step, the whole new state back to pinned host memory.  FULL layout: one
+    # gals_step_host call (copies overlapped with the step in bands); COMPACT:
+    # gals_set_state + gals_step + gals_read_state.
     nplanes = 4 if dim == 2 else 8
     pin_in = torch.from_numpy(st_host).pin_memory()
     pin_out = torch.empty_like(pin_in).pin_memory()
     e2e_steps = max(1, min(args.steps, 20))
     g2 = gals.Grid(n, layout=args.layout, stream=stream)
-    g2.set_state(pin_in.numpy(), recon=False)
-    g2.step(vel, dt, 1)
-    g2.read_state(pin_out.numpy())
+    banded = args.layout == "full"
+
+    def e2e_step():
+        if banded:
+            g2.step_host(vel, dt, 0.0, pin_in.numpy(), pin_out.numpy())
+        else:
+            g2.set_state(pin_in.numpy(), recon=False)
+            g2.step(vel, dt, 1)
+            g2.read_state(pin_out.numpy())
+
+    e2e_step()
     torch.cuda.synchronize()
     replicas.barrier(R)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g2.set_state(pin_in.numpy(), recon=False)
-        g2.step(vel, dt, 1)
-        g2.read_state(pin_out.numpy())
+        e2e_step()
     el = time.perf_counter() - t0
     el = replicas.max_over_ranks(R, el, device="cuda")
     e2e_value = replicas.throughput(nodes * e2e_steps, world, el)
@@ -553,7 +561,8 @@ def run_ours(args, wl):
                          "peak_source": peak_kind,
                          "kernel": f"gals step ({launches_per_step} launch(es) per step)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
-                    "d2h_bytes_per_step": io_bytes},
+                    "d2h_bytes_per_step": io_bytes,
+                    "api": "gals_step_host" if banded else "gals_set_state + gals_step + gals_read_state"},
             "gpu_launches": args.steps * launches_per_step + 2,  # + stage-coefficient table, clock
             "clocks": clocks,
         }

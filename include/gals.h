@@ -184,6 +184,23 @@ typedef struct {
  * GALS_ERR_NOMEM, GALS_ERR_CUDA.  Synchronises the grid stream. */
 gals_status gals_diagnostics(gals_grid *grid, const gals_diag_request *req, gals_diag *out);
 
+/* One step from a state in host memory to a state in host memory, for callers that keep
+ * the field on the host.  in[p] (all planes, the layout of gals_set_state, mixed
+ * derivatives used as given) is the state at time t0; it is advanced one step of dt
+ * (as gals_step) and written to out[p] (all planes), and the grid keeps the new state
+ * at t0 + dt for later calls.  The same result as gals_set_state, gals_step and
+ * gals_read_state, bit for bit, but the grid is cut into bands of nodes along its last
+ * axis (rows in 2D, z-levels in 3D): band b is copied in on one stream, stepped on the
+ * grid stream once every band its feet can reach is in (from a bound of the velocity's
+ * speed), and copied out on a third stream, so that with page-locked host buffers the
+ * host-to-device copy of later bands, the device-to-host copy of earlier ones and the
+ * step overlap.  in and out may be the same buffers.  Synchronises.
+ * Errors: GALS_ERR_ARG (null pointers, dt <= 0, non-finite t0, bad velocity),
+ * GALS_ERR_UNSUPPORTED (COMPACT layout, approach B, the surrogate trace, a velocity kind
+ * not available in this dimension), GALS_ERR_CUDA, GALS_ERR_TIMEOUT. */
+gals_status gals_step_host(gals_grid *grid, const gals_velocity *vel, double dt, double t0,
+                           const float *const *in, float *const *out);
+
 /* Wait for the grid's stream; returns the first asynchronous error, if any. */
 gals_status gals_synchronize(gals_grid *grid);
 

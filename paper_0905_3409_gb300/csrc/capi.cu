@@ -37,6 +37,9 @@ struct GraphEntry {
 
 }  // namespace
 
+// at most this many bands in gals_step_host (rows in 2D, z-levels in 3D)
+constexpr int kHostBands = 16;
+
 struct gals_grid {
     int dim = 0;
     int n[3] = {1, 1, 1};
@@ -62,6 +65,9 @@ struct gals_grid {
     double *diag_partials = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // gals_step_host: copy-in and copy-out streams, one event per band and direction
+    cudaStream_t hs_in = nullptr, hs_out = nullptr;
+    cudaEvent_t hs_enter = nullptr, hs_in_ev[kHostBands] = {}, hs_step_ev[kHostBands] = {};
     std::vector<GraphEntry> graphs;
     char err[256] = "";
 };
@@ -101,6 +107,38 @@ gals_status make_velparams(gals_grid *g, const gals_velocity *v, VelParams &vp)
     return GALS_OK;
 }
 
+// Kernel launch descriptor of step s of a call, from buffer cur to buffer cur ^ 1.
+StepLaunch step_launch(gals_grid *g, const VelParams &vp, int trace, double dt, int s, int cur,
+                       bool first_explicit)
+{
+    StepLaunch a{};
+    a.in = g->buf[cur];
+    a.out = g->buf[cur ^ 1];
+    a.geom = g->geom;
+    a.vp = vp;
+    a.coef = g->coef + s;
+    a.dt = dt;
+    a.tmap3 = &g->maps[cur][0];
+    a.tmap4 = &g->maps[cur][1];
+    a.tmap_cross = &g->maps[cur ^ 1][2];
+    a.err = g->err_dev;
+    a.trace = trace == GALS_TRACE_EULER      ? TR_EULER
+              : trace == GALS_TRACE_SURROGATE ? TR_GIVEN
+              : trace == GALS_TRACE_HEUN_PSI  ? TR_HEUN
+                                              : TR_RK3;
+    if (g->cross == GALS_CROSS_CELL) {
+        a.cross_in = CROSS_CELL;  // approach B: mixed derivatives per cell, none stored
+        a.write_cross = 0;
+    } else if (g->layout == GALS_LAYOUT_FULL) {
+        a.cross_in = CROSS_PLANE;
+        a.write_cross = 1;
+    } else {
+        a.cross_in = (s == 0 && first_explicit) ? CROSS_PLANE : CROSS_RECON;
+        a.write_cross = 0;
+    }
+    return a;
+}
+
 cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt, int nsteps,
                         bool first_explicit, const mlp::InferParams *ip = nullptr,
                         const mlp::Check *chk = nullptr)
@@ -109,13 +147,7 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
     cudaError_t ce = launch_coef_table(g->coef, vp, g->t_dev, dt, nsteps, g->stream);
     if (ce != cudaSuccess) return ce;
     for (int s = 0; s < nsteps; ++s) {
-        StepLaunch a{};
-        a.in = g->buf[cur];
-        a.out = g->buf[cur ^ 1];
-        a.geom = g->geom;
-        a.vp = vp;
-        a.coef = g->coef + s;
-        a.dt = dt;
+        StepLaunch a = step_launch(g, vp, trace, dt, s, cur, first_explicit);
         if (trace == GALS_TRACE_SURROGATE) {
             // learned trace of this step (with RK3 fallback per tile), then the Hermite stage
             ce = mlp::launch_mlp_trace(*ip, g->geom, vp, g->coef + s, g->t_dev, s, dt, g->trace_buf,
@@ -123,24 +155,6 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
             if (ce != cudaSuccess) return ce;
             a.vp.given = g->trace_buf;
             a.vp.given_plane = g->geom.plane;
-        }
-        a.tmap3 = &g->maps[cur][0];
-        a.tmap4 = &g->maps[cur][1];
-        a.tmap_cross = &g->maps[cur ^ 1][2];
-        a.err = g->err_dev;
-        a.trace = trace == GALS_TRACE_EULER      ? TR_EULER
-                  : trace == GALS_TRACE_SURROGATE ? TR_GIVEN
-                  : trace == GALS_TRACE_HEUN_PSI  ? TR_HEUN
-                                                  : TR_RK3;
-        if (g->cross == GALS_CROSS_CELL) {
-            a.cross_in = CROSS_CELL;  // approach B: mixed derivatives per cell, none stored
-            a.write_cross = 0;
-        } else if (g->layout == GALS_LAYOUT_FULL) {
-            a.cross_in = CROSS_PLANE;
-            a.write_cross = 1;
-        } else {
-            a.cross_in = (s == 0 && first_explicit) ? CROSS_PLANE : CROSS_RECON;
-            a.write_cross = 0;
         }
         cudaError_t e = g->dim == 2 ? launch_step2d(a, g->stream) : launch_step3d(a, g->stream);
         if (e != cudaSuccess) return e;
@@ -293,6 +307,16 @@ gals_status gals_destroy_grid(gals_grid *g)
     cudaFree(g->coef);
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
+    for (cudaStream_t hs : {g->hs_in, g->hs_out})
+        if (hs) {
+            cudaStreamSynchronize(hs);
+            cudaStreamDestroy(hs);
+        }
+    if (g->hs_enter) cudaEventDestroy(g->hs_enter);
+    for (int b = 0; b < kHostBands; ++b) {
+        if (g->hs_in_ev[b]) cudaEventDestroy(g->hs_in_ev[b]);
+        if (g->hs_step_ev[b]) cudaEventDestroy(g->hs_step_ev[b]);
+    }
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
     return GALS_OK;
@@ -484,6 +508,111 @@ gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int
         if (e != cudaSuccess) return cuda_fail(g, e, "read_state copy");
     }
     if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "read_state sync");
+    return check_device_error(g);
+}
+
+gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, double t0,
+                           const float *const *in, float *const *out)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!in || !out) return fail(g, GALS_ERR_ARG, "in / out is NULL");
+    for (int p = 0; p < g->nplanes; ++p)
+        if (!in[p] || !out[p]) return fail(g, GALS_ERR_ARG, "in[%d] / out[%d] is NULL", p, p);
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(g, GALS_ERR_ARG, "dt must be finite and > 0");
+    if (!std::isfinite(t0)) return fail(g, GALS_ERR_ARG, "t0 is not finite");
+    if (g->layout != GALS_LAYOUT_FULL || g->cross != GALS_CROSS_CENTRAL)
+        return fail(g, GALS_ERR_UNSUPPORTED, "gals_step_host needs the FULL layout and approach A");
+    VelParams vp;
+    gals_status st = make_velparams(g, v, vp);
+    if (st != GALS_OK) return st;
+    if (v->trace == GALS_TRACE_SURROGATE)
+        return fail(g, GALS_ERR_UNSUPPORTED, "gals_step_host does not take the surrogate trace");
+    cudaError_t e = cudaSuccess;
+    if (!g->hs_in) {
+        e = cudaStreamCreateWithFlags(&g->hs_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->hs_out, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->hs_enter, cudaEventDisableTiming);
+        for (int b = 0; b < kHostBands && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&g->hs_in_ev[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->hs_step_ev[b], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(g, e, "copy streams / events");
+    }
+    if (g->coef_cap < 1) {
+        if ((e = cudaMalloc(&g->coef, sizeof(StageCoef) * 64)) != cudaSuccess)
+            return cuda_fail(g, e, "cudaMalloc(coefficient table)");
+        g->coef_cap = 64;
+    }
+    // Bands along the last axis, whole tiles each.  The step of band b reads the input
+    // from every band its feet, cells and staged tiles reach: |foot - node| <= dt * vmax
+    // along that axis, plus the cell's far corner and the tile halo (3 nodes); it waits
+    // for the copy of the last of those bands (all bands if no speed bound is known).
+    // About 64 MB of copies per band, 4 to 16 bands: fewer bands cost a longer fill and
+    // drain of the pipeline, more cost per-copy overhead (measured on GB300: 8 bands best
+    // for a 4096^2 state, 16 for 512^3).
+    const int ax = g->dim - 1, nax = g->n[ax], unit = band_unit(g->dim);
+    const int64_t copy_bytes = 2 * (int64_t)g->nplanes * sizeof(float) * g->n[0] * g->n[1] * g->n[2];
+    const int want = (int)std::min<int64_t>(kHostBands, std::max<int64_t>(4, copy_bytes >> 26));
+    const int R = ((nax + want - 1) / want + unit - 1) / unit * unit;
+    const int nb = (nax + R - 1) / R;
+    const double reach = dt * speed_bound(v, g->dim, g->lo, g->hi) / g->h[ax] + 3.0;
+    const int K = reach < (double)nax ? (int)std::ceil(reach / R) : nb;
+    const Geom &G = g->geom;
+    const size_t row = (size_t)g->n[0] * sizeof(float), dpitch = (size_t)G.pitch * sizeof(float);
+    const size_t rows_per = g->dim == 2 ? 1 : (size_t)g->n[1];  // 2D-copy rows per band node
+    const int cur = g->cur;
+    float *bin = g->buf[cur], *bout = g->buf[cur ^ 1];
+    g->t = t0;
+    // work already queued on the grid stream (a step reading or writing the buffers)
+    // comes first
+    if ((e = cudaEventRecord(g->hs_enter, g->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(g->hs_in, g->hs_enter, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(g->hs_out, g->hs_enter, 0)) != cudaSuccess)
+        return cuda_fail(g, e, "step_host order");
+    if ((e = cudaMemcpyAsync(g->t_dev, &g->t, sizeof(double), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
+        (e = launch_coef_table(g->coef, vp, g->t_dev, dt, 1, g->stream)) != cudaSuccess)
+        return cuda_fail(g, e, "step_host coefficients");
+    auto copy_in = [&](int b) {
+        const size_t r0 = (size_t)b * R * rows_per, nr = (size_t)(std::min(nax, (b + 1) * R) - b * R) * rows_per;
+        for (int p = 0; p < g->nplanes && e == cudaSuccess; ++p)
+            e = cudaMemcpy2DAsync(bin + p * G.plane + r0 * G.pitch, dpitch, in[p] + r0 * g->n[0], row, row,
+                                  nr, cudaMemcpyHostToDevice, g->hs_in);
+        if (e == cudaSuccess) e = cudaEventRecord(g->hs_in_ev[b], g->hs_in);
+    };
+    StepLaunch a = step_launch(g, vp, v->trace, dt, 0, cur, false);
+    auto step_out = [&](int b) {
+        if ((e = cudaStreamWaitEvent(g->stream, g->hs_in_ev[std::min(nb - 1, b + K)], 0)) != cudaSuccess) return;
+        a.band_lo = b * R;
+        a.band_hi = std::min(nax, (b + 1) * R);
+        e = g->dim == 2 ? launch_step2d(a, g->stream) : launch_step3d(a, g->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(g->hs_step_ev[b], g->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->hs_out, g->hs_step_ev[b], 0);
+        const size_t r0 = (size_t)b * R * rows_per, nr = (size_t)(a.band_hi - a.band_lo) * rows_per;
+        for (int p = 0; p < g->nplanes && e == cudaSuccess; ++p)
+            e = cudaMemcpy2DAsync(out[p] + r0 * g->n[0], row, bout + p * G.plane + r0 * G.pitch, dpitch, row,
+                                  nr, cudaMemcpyDeviceToHost, g->hs_out);
+    };
+    // enqueue in pipeline order, so that the first bands are stepped and copied out while
+    // the host is still queueing the copies of later ones
+    for (int b = 0; b <= std::min(nb - 1, K) && e == cudaSuccess; ++b) copy_in(b);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        if (b + K + 1 < nb) copy_in(b + K + 1);
+        if (e == cudaSuccess) step_out(b);
+    }
+    if (e == cudaSuccess) e = launch_advance_time(g->t_dev, 1, dt, g->stream);
+    // every stream is drained before returning, also after a failed launch
+    cudaError_t s1 = cudaStreamSynchronize(g->hs_in), s2 = cudaStreamSynchronize(g->hs_out);
+    cudaError_t s3 = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess) e = s1 != cudaSuccess ? s1 : (s2 != cudaSuccess ? s2 : s3);
+    if (e != cudaSuccess) {
+        g->has_state = false;
+        return cuda_fail(g, e, "step_host");
+    }
+    g->cur ^= 1;
+    g->t = t0 + dt;
+    g->steps = 1;
+    g->cross_explicit = false;
+    g->has_state = true;
     return check_device_error(g);
 }
 

@@ -13,6 +13,10 @@ namespace gals {
 // parameters; on error writes a message to msg and returns the status.
 gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char *msg, size_t len);
 
+// An upper bound of max_i |v_i| over the box [lo, hi] and all times for a descriptor that
+// velparams_from accepted (infinity if none is known).
+double speed_bound(const gals_velocity *v, int dim, const double lo[3], const double hi[3]);
+
 // Size limits of the kernels' index arithmetic and launch grids: 2D planes of at most
 // 2^31 - 1 elements (row pitch x rows, 32-bit offsets in the tile kernels), at most
 // 65535 tile rows of blocks in 2D (n[1] <= 65535 * rows per tile) and at most 65535

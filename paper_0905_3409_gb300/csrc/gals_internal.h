@@ -23,7 +23,13 @@ struct StepLaunch {
     const CUtensorMap *tmap3; // TMA map of `in` for rebuilding them (COMPACT)
     const CUtensorMap *tmap_cross; // 3D FULL: TMA map of `out` with the reconstruction box
     int *err;            // device error word (kErrTmaTimeout on a lost tile copy)
+    // the band of nodes to update along the last axis (2D rows, 3D z-levels), [lo, hi);
+    // hi == 0: all.  lo must be a multiple of band_unit(dim), hi too unless it is n.
+    int band_lo, band_hi;
 };
+
+// Granularity of StepLaunch bands: the 2D tile height, the 3D tile depth.
+int band_unit(int dim);
 
 // Box of the 2D step kernel's staged tile for np planes; its output rows per block.
 void tile_box2d(int np, uint32_t box[3]);

@@ -27,14 +27,14 @@ template <int TR, int VK, int CR, int WC>
 __global__ void __launch_bounds__(TX, GALS_2D_MINB)
 k_step2d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParams vp,
          const StageCoef *__restrict__ coef, float dt, const __grid_constant__ CUtensorMap tmap,
-         int *__restrict__ err)
+         int *__restrict__ err, int yt0)
 {
     extern __shared__ __align__(128) float tile[];
     __shared__ __align__(16) Smem<TY, WC> sm;
     if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
     __syncthreads();
     tile_step2d<TY, TR, VK, CR, WC, HYT>(in, out, g, vp, coef, dt, &tmap, err, blockIdx.x * TX,
-                                    blockIdx.y * TY, tile, sm, 0);
+                                    (blockIdx.y + yt0) * TY, tile, sm, 0);
 }
 
 // phi_xy = d/dx psi_y at every node (approach A with one-sided ends); used after
@@ -61,10 +61,14 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((a.geom.n0 + TX - 1) / TX, (a.geom.n1 + TY - 1) / TY);
+    // tile rows of the band (all by default)
+    const int yt0 = a.band_lo / TY;
+    const int yt1 = ((a.band_hi > 0 ? a.band_hi : a.geom.n1) + TY - 1) / TY;
+    if (yt1 <= yt0) return cudaSuccess;
+    dim3 grid((a.geom.n0 + TX - 1) / TX, yt1 - yt0);
     const CUtensorMap &map = NP == 4 ? *a.tmap4 : *a.tmap3;
     k_step2d<TR, VK, CR, WC><<<grid, TX, GT::bytes(NP), s>>>(a.in, a.out, a.geom, a.vp, a.coef,
-                                                            (float)a.dt, map, a.err);
+                                                            (float)a.dt, map, a.err, yt0);
     return cudaGetLastError();
 }
 
@@ -102,6 +106,8 @@ cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s)
 }
 
 int tile_rows2d() { return TY; }
+
+int band_unit(int dim) { return dim == 2 ? TY : 4; }
 
 void tile_box2d(int np, uint32_t box[3])
 {

@@ -337,10 +337,14 @@ cudaError_t launch_recon_slabs(const StepLaunch &a, cudaStream_t s, int zq0, int
 
 cudaError_t launch_step3d(const StepLaunch &a, cudaStream_t s)
 {
-    const int nzt = (a.geom.n2 + TZ - 1) / TZ;
-    cudaError_t e = launch_step_tiles(a, s, 0, nzt);
+    // z-levels of the band (all by default); the reconstruction of a level needs the new
+    // psi_y, psi_z of that level only
+    static_assert(TZ == 4 && QZ == 4, "bands are whole tiles of both kernels");
+    const int z0 = a.band_lo, z1 = a.band_hi > 0 ? a.band_hi : a.geom.n2;
+    if (z1 <= z0) return cudaSuccess;
+    cudaError_t e = launch_step_tiles(a, s, z0 / TZ, (z1 - z0 + TZ - 1) / TZ);
     if (e != cudaSuccess || !a.write_cross) return e;
-    return launch_recon_slabs(a, s, 0, (a.geom.n2 + QZ - 1) / QZ);
+    return launch_recon_slabs(a, s, z0 / QZ, (z1 - z0 + QZ - 1) / QZ);
 }
 
 void recon_box3d(uint32_t box[4])

@@ -70,6 +70,36 @@ gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char 
     return GALS_OK;
 }
 
+double speed_bound(const gals_velocity *v, int dim, const double lo[3], const double hi[3])
+{
+    // the largest |x - c| over the box along one axis
+    auto reach = [&](int a, double c) { return std::fmax(std::fabs(lo[a] - c), std::fabs(hi[a] - c)); };
+    switch (v->kind) {
+    case GALS_VEL_CONST:
+        return std::fmax(std::fabs(v->c[0]), std::fmax(std::fabs(v->c[1]), dim == 3 ? std::fabs(v->c[2]) : 0.0));
+    case GALS_VEL_ROTATION:  // u = -omega (y - cy), v = omega (x - cx)
+        return std::fabs(v->omega) * std::fmax(reach(0, v->center[0]), reach(1, v->center[1]));
+    case GALS_VEL_VORTEX2D:  // |sin^2 (pi x) sin(2 pi y) cos(pi t / T)| <= 1
+        return 1.0;
+    case GALS_VEL_DEFORM3D:  // the u component carries the factor 2
+        return 2.0;
+    case GALS_VEL_PSEUDO1D: {  // v = exp(d . x) d with d = (sqrt 2, sqrt pi) / sqrt(2 + pi)
+        const double nrm = std::sqrt(2.0 + M_PI), d0 = std::sqrt(2.0) / nrm, d1 = std::sqrt(M_PI) / nrm;
+        return std::exp(d0 * std::fmax(lo[0], hi[0]) + d1 * std::fmax(lo[1], hi[1]));
+    }
+    case GALS_VEL_FOURIER2D: {  // |u| <= pi sum |a| l, |v| <= pi sum |a| k
+        double b = 0.0;
+        for (int m = 0; m < v->nmodes; ++m) {
+            const double *md = v->modes + 5 * m;
+            b += std::fabs(md[0]) * std::fmax(md[1], md[2]);
+        }
+        return M_PI * b;
+    }
+    default:
+        return INFINITY;
+    }
+}
+
 bool grid_size_ok(int dim, const int n[3], char *msg, size_t len)
 {
     if (dim == 2) {

@@ -29,7 +29,7 @@ MAX_MODES = 64
 # every symbol include/gals.h declares
 EXPORTS = [
     "gals_create_grid", "gals_destroy_grid", "gals_set_state", "gals_step", "gals_read_state",
-    "gals_diagnostics", "gals_synchronize", "gals_time", "gals_state_planes", "gals_last_error",
+    "gals_diagnostics", "gals_synchronize", "gals_step_host", "gals_time", "gals_state_planes", "gals_last_error",
     "gals_version",
     "gals_create_batch", "gals_destroy_batch", "gals_batch_set_state", "gals_batch_step",
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
         L.gals_read_state.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
         L.gals_diagnostics.argtypes = [vp, ctypes.POINTER(DiagRequest), ctypes.POINTER(DiagOut)]
         L.gals_synchronize.argtypes = [vp]
+        L.gals_step_host.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
+                                     ctypes.c_double, ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.gals_time.argtypes = [vp]
         L.gals_time.restype = ctypes.c_double
         L.gals_state_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int,
@@ -316,6 +318,23 @@ class Grid:
 
     def synchronize(self):
         _check(lib().gals_synchronize(self._h), self._h)
+
+    def step_host(self, vel: Velocity, dt: float, t0: float, state, out=None):
+        """One step from the host state ``state`` (all planes, at time t0) to ``out`` (a new
+        host array if None), with the copies overlapped with the step in bands; the grid
+        keeps the new state.  Page-locked (pinned) arrays let the copies overlap."""
+        st = np.ascontiguousarray(state, dtype=np.float32)
+        assert st.shape == self.shape, (st.shape, self.shape)
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.shape == self.shape
+        nf = self.nplanes
+        pin = (ctypes.c_void_p * nf)(*[st[p].ctypes.data for p in range(nf)])
+        pout = (ctypes.c_void_p * nf)(*[out[p].ctypes.data for p in range(nf)])
+        d = vel.desc()
+        _check(lib().gals_step_host(self._h, ctypes.byref(d), float(dt), float(t0), pin, pout),
+               self._h)
+        return out
 
     @property
     def time(self) -> float:
