@@ -109,6 +109,9 @@ def lib():
                                       ctypes.c_int]
             L.orc_symdiff.restype = ctypes.c_double
             L.orc_eval_points.argtypes = [ctypes.POINTER(_Grid), pp, ctypes.c_long, dp, dp, dp]
+            L.orc_hermite_cell2.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp, dp]
+            L.orc_curvature_points.argtypes = [ctypes.POINTER(_Grid), pp, ctypes.c_long, dp, dp,
+                                               dp, dp]
             _mlp_bind(L)
             _lib = L
     return _lib
@@ -333,6 +336,28 @@ def eval_points(g, state, pts):
     G = np.zeros(P.shape)
     lib().orc_eval_points(ctypes.byref(g), _planes_ptr(planes), P.shape[0], _dp(P), _dp(H), _dp(G))
     return H, G
+
+
+def hermite_cell2(dim: int, data, h, xi):
+    """H, grad H and the Hessian of the p-cubic interpolant of one cell (Sec. 3.4)."""
+    d = _f64(data).ravel()
+    H = np.zeros(1)
+    G = np.zeros(dim)
+    Hs = np.zeros(dim * dim)
+    lib().orc_hermite_cell2(dim, _dp(d), _dp(_f64(h)), _dp(_f64(xi)), _dp(H), _dp(G), _dp(Hs))
+    return H[0], G, Hs.reshape(dim, dim)
+
+
+def curvature_points(g, state, pts):
+    """H, unit normal and curvature at points from the interpolant (Sec. 3.4)."""
+    planes = _state_list(state, g)
+    P = _f64(pts).reshape(-1, g.dim)
+    H = np.zeros(P.shape[0])
+    N = np.zeros(P.shape)
+    K = np.zeros(P.shape[0])
+    lib().orc_curvature_points(ctypes.byref(g), _planes_ptr(planes), P.shape[0], _dp(P), _dp(H),
+                               _dp(N), _dp(K))
+    return H, N, K
 
 
 # ---------------------------------------------------------------- MLP (surrogate oracle)

@@ -138,3 +138,50 @@ void orc_eval_points(const orc_grid *g, const double *const *planes, long npts,
         for (int d = 0; d < dim; ++d) grad[p * dim + d] = gr[d];
     }
 }
+
+/* Sec. 3.4, eqs. surface_normal and curvature, with the interpolant's own first and
+ * second derivatives inside the cell of each point (cell located as in orc_eval_points) */
+void orc_curvature_points(const orc_grid *g, const double *const *planes, long npts,
+                          const double *pts, double *H, double *normal, double *kappa)
+{
+    int dim = g->dim;
+    for (long p = 0; p < npts; ++p) {
+        int cell[3] = {0, 0, 0};
+        double xi[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            double hi = g->lo[d] + (g->n[d] - 1) * g->h[d];
+            double f = pts[p * dim + d];
+            if (f < g->lo[d]) f = g->lo[d];
+            if (f > hi) f = hi;
+            int c = (int)floor((f - g->lo[d]) / g->h[d]);
+            if (c < 0) c = 0;
+            if (c > g->n[d] - 2) c = g->n[d] - 2;
+            cell[d] = c;
+            xi[d] = (f - (g->lo[d] + c * g->h[d])) / g->h[d];
+        }
+        double data[64], gr[3], hs[9];
+        gather_cell(g, planes, cell, data);
+        orc_hermite_cell2(dim, data, g->h, xi, &H[p], gr, hs);
+        double g2 = 0.0;
+        for (int d = 0; d < dim; ++d) g2 += gr[d] * gr[d];
+        double gn = sqrt(g2);
+        for (int d = 0; d < dim; ++d) normal[p * dim + d] = gn > 0.0 ? gr[d] / gn : 0.0;
+        if (!(gn > 0.0)) {
+            kappa[p] = 0.0;
+            continue;
+        }
+        double num;
+        if (dim == 2) {
+            double px = gr[0], py = gr[1];
+            num = hs[0] * py * py - 2.0 * px * py * hs[1] + hs[3] * px * px;
+        } else {
+            double tr = 0.0, ghg = 0.0;
+            for (int j = 0; j < dim; ++j) {
+                tr += hs[j * dim + j];
+                for (int k = 0; k < dim; ++k) ghg += gr[j] * hs[j * dim + k] * gr[k];
+            }
+            num = g2 * tr - ghg;
+        }
+        kappa[p] = num / (g2 * gn);
+    }
+}

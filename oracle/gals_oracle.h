@@ -82,6 +82,11 @@ void orc_basis1d(double xi, double w[4], double dw[4]);
 void orc_hermite_cell(int dim, const double *data, const double *h,
                       const double *xi, double *H, double *gradH);
 
+/* the same sum with the second derivatives: hessH[j*dim+k] = d^2 H / dx_j dx_k
+ * (Sec. 3.4: derivative quantities inside a cell from the interpolant itself) */
+void orc_hermite_cell2(int dim, const double *data, const double *h, const double *xi,
+                       double *H, double *gradH, double *hessH);
+
 /* velocity and its Jacobian at (x, t) */
 void orc_vel_eval(const orc_velocity *vel, int dim, const double *x, double t,
                   double v[3], double Dv[9]);
@@ -145,6 +150,15 @@ double orc_symdiff(const orc_grid *g, const double *const *a, const double *cons
 /* Hermite value and gradient at arbitrary points (cell located by floor+clamp) */
 void orc_eval_points(const orc_grid *g, const double *const *planes, long npts,
                      const double *pts, double *H, double *grad);
+
+/* Normal and curvature at arbitrary points from the interpolant of the cell holding
+ * each point (Sec. 3.4): n = grad H / |grad H| (eq. surface_normal); in 2D
+ * kappa = (H_xx H_y^2 - 2 H_x H_y H_xy + H_yy H_x^2) / |grad H|^3 (eq. curvature), in 3D
+ * its extension kappa = div(grad H / |grad H|) = (|g|^2 tr(D^2 H) - g^T D^2 H g) / |g|^3,
+ * g = grad H (the sum of the principal curvatures; the 2D formula is its p = 2 case).
+ * Where grad H = 0, n = 0 and kappa = 0.  H[npts], normal[npts*dim], kappa[npts]. */
+void orc_curvature_points(const orc_grid *g, const double *const *planes, long npts,
+                          const double *pts, double *H, double *normal, double *kappa);
 
 #ifdef __cplusplus
 }
