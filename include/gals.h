@@ -201,6 +201,21 @@ gals_status gals_diagnostics(gals_grid *grid, const gals_diag_request *req, gals
 gals_status gals_step_host(gals_grid *grid, const gals_velocity *vel, double dt, double t0,
                            const float *const *in, float *const *out);
 
+/* Value, unit normal and curvature of the current state's interpolant at npoints points
+ * (Sec. 3.4: every first and second derivative inside a cell from the p-cubic interpolant
+ * of that cell; eq. surface_normal n = grad H / |grad H|; eq. curvature in 2D,
+ * kappa = (H_xx H_y^2 - 2 H_x H_y H_xy + H_yy H_x^2) / |grad H|^3, and in 3D its extension
+ * kappa = div(grad H / |grad H|), the sum of the principal curvatures).  points: npoints
+ * rows of dim FP64 coordinates (x first); a point outside the box is clamped into it.
+ * Outputs, any of which may be NULL: H[npoints], normal[npoints * dim], kappa[npoints]
+ * (FP32; n = 0 and kappa = 0 where grad H = 0).  memspace applies to points and outputs
+ * alike; host arrays are staged through a device buffer the grid keeps.  The mixed
+ * derivatives come from the planes (approach A; rebuilt first in the COMPACT layout) or
+ * per cell (approach B).  Synchronises.
+ * Errors: GALS_ERR_ARG, GALS_ERR_STATE, GALS_ERR_NOMEM, GALS_ERR_CUDA. */
+gals_status gals_eval_points(gals_grid *grid, const double *points, int64_t npoints, int memspace,
+                             float *H, float *normal, float *kappa);
+
 /* Wait for the grid's stream; returns the first asynchronous error, if any. */
 gals_status gals_synchronize(gals_grid *grid);
 

@@ -58,6 +58,8 @@ struct gals_grid {
     CUtensorMap maps[2][3];       // TMA maps per buffer: [b][0] COMPACT box, [b][1] FULL box,
                                   // [b][2] 3D reconstruction box
     float *trace_buf = nullptr;   // surrogate trace of the current step: dx, dy, J (6 planes)
+    char *pt_buf = nullptr;       // gals_eval_points: device staging of host points / results
+    size_t pt_cap = 0;
     int *err_dev = nullptr;       // device error word written by kernels (bounded waits)
     StageCoef *coef = nullptr;    // per-step stage coefficients of the current call
     int coef_cap = 0;
@@ -304,6 +306,7 @@ gals_status gals_destroy_grid(gals_grid *g)
     cudaFree(g->t_dev);
     cudaFree(g->err_dev);
     cudaFree(g->trace_buf);
+    cudaFree(g->pt_buf);
     cudaFree(g->coef);
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
@@ -614,6 +617,52 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
     g->cross_explicit = false;
     g->has_state = true;
     return check_device_error(g);
+}
+
+gals_status gals_eval_points(gals_grid *g, const double *points, int64_t npoints, int memspace,
+                             float *H, float *normal, float *kappa)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
+    if (npoints < 0) return fail(g, GALS_ERR_ARG, "npoints must be >= 0");
+    if (npoints > 0 && !points) return fail(g, GALS_ERR_ARG, "points is NULL");
+    if (memspace != GALS_MEM_HOST && memspace != GALS_MEM_DEVICE)
+        return fail(g, GALS_ERR_ARG, "bad memspace %d", memspace);
+    if (npoints == 0) return GALS_OK;
+    gals_status st = ensure_cross(g);
+    if (st != GALS_OK) return st;
+    const int dim = g->dim;
+    const bool cell_b = g->cross == GALS_CROSS_CELL;
+    cudaError_t e;
+    if (memspace == GALS_MEM_DEVICE) {
+        e = launch_eval_points(dim, g->geom, g->lo, g->h, g->buf[g->cur], points, npoints, cell_b, H,
+                               normal, kappa, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        return e == cudaSuccess ? GALS_OK : cuda_fail(g, e, "eval_points");
+    }
+    // host points and results: stage them through a device buffer kept by the grid
+    const size_t pb = sizeof(double) * dim * (size_t)npoints;
+    const size_t ob = sizeof(float) * (size_t)npoints;
+    const size_t need = pb + ob * (2 + dim);
+    if (need > g->pt_cap) {
+        if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
+        cudaFree(g->pt_buf);
+        g->pt_buf = nullptr;
+        g->pt_cap = 0;
+        if ((e = cudaMalloc(&g->pt_buf, need)) != cudaSuccess) return cuda_fail(g, e, "cudaMalloc(points)");
+        g->pt_cap = need;
+    }
+    double *dp = reinterpret_cast<double *>(g->pt_buf);
+    float *dH = reinterpret_cast<float *>(g->pt_buf + pb), *dk = dH + npoints, *dn = dk + npoints;
+    if ((e = cudaMemcpyAsync(dp, points, pb, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+        return cuda_fail(g, e, "points copy");
+    e = launch_eval_points(dim, g->geom, g->lo, g->h, g->buf[g->cur], dp, npoints, cell_b, H ? dH : nullptr,
+                           normal ? dn : nullptr, kappa ? dk : nullptr, g->stream);
+    if (e == cudaSuccess && H) e = cudaMemcpyAsync(H, dH, ob, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && kappa) e = cudaMemcpyAsync(kappa, dk, ob, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess && normal) e = cudaMemcpyAsync(normal, dn, ob * dim, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    return e == cudaSuccess ? GALS_OK : cuda_fail(g, e, "eval_points");
 }
 
 gals_status gals_state_planes(gals_grid *g, float **planes, int nplanes, int64_t *row_pitch)

@@ -56,6 +56,12 @@ cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream
 // Velocity kinds supported per dimension.
 bool vel_supported(int dim, int kind);
 
+// Value, unit normal and curvature of the interpolant at npts points (curvature.cu);
+// pts: npts * dim FP64 coordinates on the device; any output may be null.
+cudaError_t launch_eval_points(int dim, const Geom &g, const double lo[3], const double h[3],
+                               const float *state, const double *pts, int64_t npts, bool cell_b,
+                               float *H, float *normal, float *kappa, cudaStream_t s);
+
 // Diagnostics (diag.cu)
 struct DiagOut {
     unsigned long long n_neg, n_sym, nonfinite;

@@ -29,7 +29,7 @@ MAX_MODES = 64
 # every symbol include/gals.h declares
 EXPORTS = [
     "gals_create_grid", "gals_destroy_grid", "gals_set_state", "gals_step", "gals_read_state",
-    "gals_diagnostics", "gals_synchronize", "gals_step_host", "gals_time", "gals_state_planes", "gals_last_error",
+    "gals_diagnostics", "gals_synchronize", "gals_step_host", "gals_eval_points", "gals_time", "gals_state_planes", "gals_last_error",
     "gals_version",
     "gals_create_batch", "gals_destroy_batch", "gals_batch_set_state", "gals_batch_step",
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
         L.gals_synchronize.argtypes = [vp]
         L.gals_step_host.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
                                      ctypes.c_double, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.gals_eval_points.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp]
         L.gals_time.argtypes = [vp]
         L.gals_time.restype = ctypes.c_double
         L.gals_state_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int,
@@ -318,6 +319,32 @@ class Grid:
 
     def synchronize(self):
         _check(lib().gals_synchronize(self._h), self._h)
+
+    def eval_points(self, points):
+        """Value, unit normal and curvature of the interpolant at points (npts x dim).
+        Host arrays (numpy) or CUDA tensors (torch, float64 points): the results live in
+        the same memory as the points."""
+        dim = len(self.n)
+        if _is_torch(points):
+            import torch
+            P = points.contiguous()
+            assert P.is_cuda and P.dtype == torch.float64 and P.shape[-1] == dim
+            m = P.numel() // dim
+            H = torch.empty(m, dtype=torch.float32, device=P.device)
+            N = torch.empty((m, dim), dtype=torch.float32, device=P.device)
+            K = torch.empty(m, dtype=torch.float32, device=P.device)
+            torch.cuda.current_stream().synchronize()
+            _check(lib().gals_eval_points(self._h, P.data_ptr(), m, MEM_DEVICE, H.data_ptr(),
+                                          N.data_ptr(), K.data_ptr()), self._h)
+            return H, N, K
+        P = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, dim)
+        m = P.shape[0]
+        H = np.empty(m, dtype=np.float32)
+        N = np.empty((m, dim), dtype=np.float32)
+        K = np.empty(m, dtype=np.float32)
+        _check(lib().gals_eval_points(self._h, P.ctypes.data, m, MEM_HOST, H.ctypes.data,
+                                      N.ctypes.data, K.ctypes.data), self._h)
+        return H, N, K
 
     def step_host(self, vel: Velocity, dt: float, t0: float, state, out=None):
         """One step from the host state ``state`` (all planes, at time t0) to ``out`` (a new
