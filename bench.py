@@ -226,7 +226,7 @@ def oracle_state(wl, g, slab=None):
     return st
 
 
-def oracle_leg(wl, budget_s=12.0, max_bands=None):
+def oracle_leg(wl, budget_s=12.0, max_bands=None, trace="rk3", cross="central"):
     """Time the FP64 oracle on row bands (2D) / z-slabs (3D) of the workload: each band
     is an exact, independent part of one step.  Returns (node-updates/s, cores, sample)."""
     import oracle
@@ -246,7 +246,8 @@ def oracle_leg(wl, budget_s=12.0, max_bands=None):
     t0 = time.perf_counter()
     b0 = outer // 3
     while True:
-        oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes)
+        oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes, trace_scheme=trace,
+                         cross=cross)
         nodes += band * inner_nodes
         done += 1
         el = time.perf_counter() - t0
@@ -283,7 +284,8 @@ def run_reference(args, wl):
         return slab[0] + (s * band) % (slab[1] - slab[0])
     for s in range(args.warmup):
         b0 = band_at(s)
-        oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes)
+        oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes, trace_scheme=trace,
+                         cross=cross)
     t0 = time.perf_counter()
     for s in range(args.steps):
         b0 = band_at(s)
@@ -482,10 +484,10 @@ def run_ours(args, wl):
     nodes = int(np.prod(n))
     h = 1.0 / (n[0] - 1)
     dt = h / wl["vmax"]
-    vel = gals.Velocity(trace="rk3", **wl["vel"])
+    vel = gals.Velocity(trace=args.trace, **wl["vel"])
     st_host = initial_state(wl)
     stream = torch.cuda.Stream()
-    g = gals.Grid(n, layout=args.layout, stream=stream)
+    g = gals.Grid(n, layout=args.layout, stream=stream, cross=args.cross)
     g.set_state(st_host, t0=0.0, recon=True)
 
     # warm-up (also captures the CUDA graph for K steps)
@@ -511,8 +513,11 @@ def run_ours(args, wl):
     value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
 
     # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels)
-    launches_per_step = 2 if (args.layout == "full" and dim == 3) else 1
-    bpn = bytes_per_node(dim, args.layout)
+    cell = args.cross == "cell"
+    launches_per_step = 2 if (args.layout == "full" and dim == 3 and not cell) else 1
+    # approach B stores no mixed derivatives: the step moves phi and psi only
+    bpn = bytes_per_node(dim, "compact" if cell else args.layout)
+    default_path = args.trace == "rk3" and not cell
     step_s = ms * 1e-3 / args.steps
     achieved = bpn * nodes / step_s / 1e9
     peak, peak_kind = measured_peaks()
@@ -525,8 +530,8 @@ def run_ours(args, wl):
     pin_in = torch.from_numpy(st_host).pin_memory()
     pin_out = torch.empty_like(pin_in).pin_memory()
     e2e_steps = max(1, min(args.steps, 20))
-    g2 = gals.Grid(n, layout=args.layout, stream=stream)
-    banded = args.layout == "full"
+    g2 = gals.Grid(n, layout=args.layout, stream=stream, cross=args.cross)
+    banded = args.layout == "full" and not cell
 
     def e2e_step():
         if banded:
@@ -553,11 +558,13 @@ def run_ours(args, wl):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "layout": args.layout, "nodes": nodes,
+                       "trace": args.trace, "cross": args.cross,
                        "dt": dt, "bytes_per_node_update": bpn,
                        "l2": f"inputs larger than L2 ({nodes * nplanes * 4 / 1e6:.0f} MB state per buffer)",
                        "parallelism": f"{world} independent replica(s), one per GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(args.workload, args.layout),
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic(args.workload, args.layout) if default_path else None,
                          "peak_source": peak_kind,
                          "kernel": f"gals step ({launches_per_step} launch(es) per step)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
@@ -567,7 +574,8 @@ def run_ours(args, wl):
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:
-            v, cores, sample = oracle_leg(wl, budget_s=args.cpu_budget)
+            v, cores, sample = oracle_leg(wl, budget_s=args.cpu_budget, trace=args.trace,
+                                          cross=args.cross)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": sample}
         print(json.dumps(line))
@@ -745,6 +753,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex4096", choices=sorted(WORKLOADS))
     ap.add_argument("--layout", default="full", choices=["full", "compact"])
+    ap.add_argument("--trace", default="rk3", choices=["rk3", "heun_psi", "euler"],
+                    help="single-grid workloads: backward trace (Sec. 5.1; Heun-psi: Sec. 4)")
+    ap.add_argument("--cross", default="central", choices=["central", "cell"],
+                    help="single-grid workloads: mixed derivatives by approach A or B (Sec. 2.3)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--train-steps", type=int, default=2000, help="learned trace: optimizer steps")
