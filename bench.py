@@ -48,6 +48,12 @@ WORKLOADS = {
     "deform512": dict(dim=3, n=(512, 512, 512), vel=dict(kind="deform3d", T=3.0), vmax=2.0,
                       desc="3D GALS 512^3 nodes on [0,1]^3, FP32, LeVeque deformation T=3, "
                            "sphere SDF r=0.15 at (0.35,0.35,0.35), RK3 trace, CFL 1"),
+    "zalesak512": dict(dim=3, n=(512, 512, 512), vel=dict(kind="rotation", omega=2 * math.pi,
+                                                        center=(0.5, 0.5, 0.5)), vmax=math.pi,
+                       desc="3D GALS 512^3 nodes on [0,1]^3, FP32, Zalesak's slotted sphere "
+                            "(r=0.15 at (0.5,0.75,0.5), slot width 0.05, depth 0.25) in rigid "
+                            "rotation about the z-axis through (0.5,0.5) (omega=2pi), RK3 "
+                            "trace, CFL 1"),
     "batch256": dict(dim=2, n=None, batch=256, vel=dict(kind="fourier2d"), vmax=None,
                      desc="Batched 2D GALS, FP32: 256 independent problems, side lengths uniform "
                           "in [128,1024] (seed 9053409), each an ellipse SDF advected by its own "
@@ -117,6 +123,8 @@ def initial_state(wl):
             st = inputs.slotted_disk_sdf(n)
         else:
             st = inputs.circle_sdf(n)
+    elif wl["vel"]["kind"] == "rotation":
+        return inputs.slotted_sphere_sdf(n, dtype=np.float32)
     else:
         return inputs.sphere_sdf(n, dtype=np.float32)
     return st.astype(np.float32)
@@ -222,7 +230,8 @@ def oracle_state(wl, g, slab=None):
         return oracle.recon_cross(g, initial_state(wl).astype(np.float64))
     st = np.zeros((8, n[2], n[1], n[0]))
     z0, z1 = max(slab[0] - 2, 0), min(slab[1] + 2, n[2])
-    st[:, z0:z1] = inputs.sphere_sdf(n, z_range=(z0, z1))
+    gen = inputs.slotted_sphere_sdf if wl["vel"]["kind"] == "rotation" else inputs.sphere_sdf
+    st[:, z0:z1] = gen(n, z_range=(z0, z1))
     return st
 
 

@@ -253,6 +253,44 @@ def sphere_sdf(n, center=(0.35, 0.35, 0.35), r=0.15, lo=None, hi=None, dtype=np.
     return out
 
 
+def slotted_sphere_sdf(n, center=(0.5, 0.75, 0.5), r=0.15, slot_w=0.05, slot_top=0.85,
+                       lo=None, hi=None, dtype=np.float64, z_range=None):
+    """Zalesak's slotted sphere (Sec. 6.2.3, rescaled to the unit box): the sphere minus
+    the slot {|x - cx| < w/2, y < slot_top} (all z), which opens through the bottom of
+    the sphere and ends at y = slot_top (depth 0.25 for the default sphere).  Level set
+    function max(d_sphere, -d_slot) with d the signed distances to the sphere and to the
+    slot region: its zero set is the slotted sphere exactly; it is the distance to that
+    surface except near the slot's edges.  Gradient of the active branch (the sphere's
+    on ties); zero cross planes.  Built one z-slice at a time; z_range=(z0, z1) returns
+    only those slices."""
+    axes = node_coords(n, lo, hi)
+    z0, z1 = (0, n[2]) if z_range is None else z_range
+    out = np.zeros((8, z1 - z0, n[1], n[0]), dtype=dtype)
+    Y, X = np.meshgrid(axes[1], axes[0], indexing="ij")
+    dx, dy = X - center[0], Y - center[1]
+    hw = slot_w / 2
+    # signed distance to the slot region and its gradient (independent of z)
+    qx, qy = np.abs(dx) - hw, Y - slot_top
+    sx = np.where(dx >= 0, 1.0, -1.0)
+    ox, oy = np.maximum(qx, 0.0), np.maximum(qy, 0.0)
+    dout = np.hypot(ox, oy)
+    d_slot = dout + np.minimum(np.maximum(qx, qy), 0.0)
+    safe = np.where(dout > 0, dout, 1.0)
+    gsx = np.where(dout > 0, ox / safe * sx, np.where(qx >= qy, sx, 0.0))
+    gsy = np.where(dout > 0, oy / safe, np.where(qx >= qy, 0.0, 1.0))
+    for k in range(z0, z1):
+        dz = axes[2][k] - center[2]
+        d = np.sqrt(dx * dx + dy * dy + dz * dz)
+        sd = np.where(d > 0, d, 1.0)
+        d_sph = d - r
+        use_sph = d_sph >= -d_slot
+        out[0, k - z0] = np.where(use_sph, d_sph, -d_slot)
+        out[1, k - z0] = np.where(use_sph, np.where(d > 0, dx / sd, 0.0), -gsx)
+        out[2, k - z0] = np.where(use_sph, np.where(d > 0, dy / sd, 0.0), -gsy)
+        out[3, k - z0] = np.where(use_sph, np.where(d > 0, dz / sd, 0.0), 0.0)
+    return out
+
+
 def cube_sdf(n, center=(0.35, 0.35, 0.35), half=0.15, lo=None, hi=None):
     """Exact signed distance to an axis-aligned cube and its gradient."""
     X, Y, Z = _mesh(n, lo, hi)

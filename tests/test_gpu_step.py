@@ -168,6 +168,15 @@ def test_3d_rotation_cube(gals):
                center=(0.5, 0.5, 0.5))
 
 
+@pytest.mark.parametrize("layout", ["full", "compact"])
+def test_3d_zalesak_sphere_rotation(gals, layout):
+    """Zalesak's slotted sphere (Sec. 6.2.3) in rigid rotation about the z-axis, CFL 0.9."""
+    n = (26, 24, 20)
+    st = inputs.slotted_sphere_sdf(n, center=(0.5, 0.7, 0.5), r=0.2, slot_w=0.1, slot_top=0.8)
+    check_step(gals, n, st, "rotation", 0.9 / (25 * math.pi), t0=0.1, steps=3, layout=layout,
+               recon=True, omega=2 * math.pi, center=(0.5, 0.5, 0.5))
+
+
 def test_3d_gaussian_explicit_cross(gals):
     n = (16, 17, 18)
     st = inputs.gaussian_bump3d(n)

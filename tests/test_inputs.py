@@ -62,3 +62,39 @@ def test_batch_problems_deterministic():
     assert [p.n for p in a] == [p.n for p in b]
     assert all(128 <= p.n <= 1024 for p in a)
     assert all(np.array_equal(p.modes, q.modes) for p, q in zip(a, b))
+
+
+def test_slotted_sphere_sign_gradient_and_slices():
+    """Zalesak's slotted sphere: the sign at known nodes, a unit gradient that matches
+    one-sided differences of phi wherever those agree (away from the kinks of the max),
+    phi exact (|x - c| - r) on the sphere away from the slot, and z_range slices."""
+    n = (33, 33, 33)                                  # h = 1/32: 0.5 and 0.75 are nodes
+    st = inputs.slotted_sphere_sdf(n)
+    phi = st[0]
+    assert phi[16, 24, 16] > 0                        # the centre lies in the slot
+    assert phi[16, 22, 16] > 0                        # (0.5, 0.6875, 0.5): slot, lower
+    assert phi[16, 28, 16] < 0                        # (0.5, 0.875, 0.5): above the slot end
+    assert phi[16, 24, 13] < 0                        # (0.40625, 0.75, 0.5): the body
+    assert phi[16, 24, 24] > 0                        # (0.75, 0.75, 0.5): outside
+    assert np.allclose(st[1] ** 2 + st[2] ** 2 + st[3] ** 2, 1.0)
+    assert not np.any(st[4:])
+    eps = 1e-6
+    for ax in range(3):
+        lo, hi = [0.0] * 3, [1.0] * 3
+        lo[ax] += eps
+        hi[ax] += eps
+        fp = inputs.slotted_sphere_sdf(n, lo=lo, hi=hi)[0]
+        lo[ax] -= 2 * eps
+        hi[ax] -= 2 * eps
+        fm = inputs.slotted_sphere_sdf(n, lo=lo, hi=hi)[0]
+        fwd, bwd = (fp - phi) / eps, (phi - fm) / eps
+        smooth = np.abs(fwd - bwd) < 1e-4
+        assert smooth.mean() > 0.95
+        assert np.max(np.abs(st[1 + ax][smooth] - 0.5 * (fwd + bwd)[smooth])) < 1e-4
+    X, Y, Z = np.meshgrid(*inputs.node_coords(n), indexing="xy")
+    X, Y, Z = (a.transpose(2, 0, 1) for a in (X, Y, Z))   # to [z][y][x]
+    d = np.sqrt((X - 0.5) ** 2 + (Y - 0.75) ** 2 + (Z - 0.5) ** 2)
+    far = (np.abs(X - 0.5) > 0.1) | (Y > 0.95)
+    assert np.allclose(phi[far], d[far] - 0.15, atol=1e-15)
+    part = inputs.slotted_sphere_sdf(n, z_range=(5, 12))
+    assert np.array_equal(part, st[:, 5:12])
