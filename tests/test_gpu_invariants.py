@@ -98,6 +98,27 @@ def test_compact_equals_full_bitwise(G, dim):
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("n0", [129, 130, 131, 256, 300])
+@pytest.mark.parametrize("cfl", [0.9, 2.5])
+def test_full_equals_compact_across_tiles(G, n0, cfl):
+    """Grids several 128-column tiles wide, five steps in one call (one CUDA graph).  The
+    FULL step writes phi_xy+ of a tile's edge columns from the new psi_y of the halo
+    columns it updates itself; COMPACT rebuilds every mixed derivative from psi_y when it
+    reads it.  The two layouts must agree bit for bit, also with feet outside the staged
+    tile (CFL 2.5, read from global memory) and with a last tile one to three columns wide."""
+    n = (n0, 23)
+    st = inputs.circle_sdf(n, center=(0.5, 0.5), r=0.3).astype(np.float32)
+    vel = G.Velocity("vortex2d", T=8.0)
+    outs = []
+    for layout in ("full", "compact"):
+        g = G.Grid(n, layout=layout)
+        g.set_state(st, t0=0.3, recon=True)
+        g.step(vel, cfl / (n0 - 1), 5)
+        outs.append(g.read_state())
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_graph_replay_equals_single_steps(G):
     """A steady field, so the result cannot depend on how the clock sums dt."""
     n = (50, 50)
