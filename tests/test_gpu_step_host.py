@@ -44,6 +44,8 @@ CASES = [
     ((150, 200), dict(kind="vortex2d", T=8.0), 0.8),
     ((129, 61), dict(kind="rotation", omega=2 * math.pi, center=(0.5, 0.5, 0.0)), 2.5),
     ((24, 20, 37), dict(kind="deform3d", T=3.0), 0.4),
+    # feet six cells away: a band's step needs rows beyond the next band's first rows
+    ((70, 64), dict(kind="rotation", omega=2 * math.pi, center=(0.5, 0.5, 0.0)), 6.0),
 ]
 
 
