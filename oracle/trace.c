@@ -16,7 +16,7 @@
  * With Dv the usual Jacobian, the chain rule puts the inner Jacobian on the
  * right (the paper's grad x1 . grad v(x1) is the transpose of Dv(x1) J1).
  * orc_flowmap_rk4 integrates the same backward flow with classical RK4 and the
- * variational equation dJ/dtau = Dv(X,tau) J, as an accurate judge.
+ * variational equation dJ/dtau = Dv(X,tau) J: an accurate reference for the traces.
  */
 #include <string.h>
 #include "gals_oracle.h"
