@@ -153,26 +153,25 @@ __device__ __forceinline__ void trace2d_pair(const V2p &a, const VelParams &vp,
     const F2 J1_00 = fma2(mdt, a.d00, one), J1_01 = mul2(mdt, a.d01);
     const F2 J1_10 = mul2(mdt, a.d10), J1_11 = fma2(mdt, a.d11, one);
     const V2p b = vel2d_pair<VK>(vp, sc, scp, 1, fma2(mdt, a.u, x), fma2(mdt, a.v, y));
-    // M = Dv2 J1
-    const F2 M00 = fma2(b.d00, J1_00, mul2(b.d01, J1_10)), M01 = fma2(b.d00, J1_01, mul2(b.d01, J1_11));
-    const F2 M10 = fma2(b.d10, J1_00, mul2(b.d11, J1_10)), M11 = fma2(b.d10, J1_01, mul2(b.d11, J1_11));
-    // stage 2: x2 = x - dt (v1 + v2)/4, J2 = I - dt (Dv1 + Dv2 J1)/4
-    const F2 mq = bc(-0.25f * dt);
-    const F2 J2_00 = fma2(mq, add2(a.d00, M00), one), J2_01 = mul2(mq, add2(a.d01, M01));
-    const F2 J2_10 = mul2(mq, add2(a.d10, M10)), J2_11 = fma2(mq, add2(a.d11, M11), one);
+    // S = Dv1 + Dv2 J1 (Dv1 is the accumulator of the product)
+    const F2 S00 = fma2(b.d00, J1_00, fma2(b.d01, J1_10, a.d00));
+    const F2 S01 = fma2(b.d00, J1_01, fma2(b.d01, J1_11, a.d01));
+    const F2 S10 = fma2(b.d10, J1_00, fma2(b.d11, J1_10, a.d10));
+    const F2 S11 = fma2(b.d10, J1_01, fma2(b.d11, J1_11, a.d11));
+    // stage 2: x2 = x - dt (v1 + v2)/4, J2 = I - dt S / 4, kept as G = (-2 dt / 3) J2
+    const F2 mq = bc(-0.25f * dt), m23 = bc(-2.f * dt / 3.f), kq = bc((-2.f * dt / 3.f) * (-0.25f * dt));
+    const F2 G00 = fma2(kq, S00, m23), G01 = mul2(kq, S01), G10 = mul2(kq, S10), G11 = fma2(kq, S11, m23);
     const V2p c = vel2d_pair<VK>(vp, sc, scp, 2, fma2(mq, add2(a.u, b.u), x),
                                  fma2(mq, add2(a.v, b.v), y));
-    const F2 N00 = fma2(c.d00, J2_00, mul2(c.d01, J2_10)), N01 = fma2(c.d00, J2_01, mul2(c.d01, J2_11));
-    const F2 N10 = fma2(c.d10, J2_00, mul2(c.d11, J2_10)), N11 = fma2(c.d10, J2_01, mul2(c.d11, J2_11));
     // foot = x - dt (w3 + (w1 + w2 - 2 w3)/6): exact for constant v;
-    // J = I - dt (Dv1 + M)/6 - 2 dt N / 3 (= I when Dv = 0)
-    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f), m6 = bc(-dt / 6.f), m23 = bc(-2.f * dt / 3.f);
+    // J = I - dt S / 6 - 2 dt Dv3 J2 / 3 = (I - dt S / 6) + Dv3 G (= I when Dv = 0)
+    const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f), m6 = bc(-dt / 6.f);
     dx = mul2(mdt, fma2(fma2(m2, c.u, add2(a.u, b.u)), i6, c.u));
     dy = mul2(mdt, fma2(fma2(m2, c.v, add2(a.v, b.v)), i6, c.v));
-    J[0] = fma2(m6, add2(a.d00, M00), fma2(m23, N00, one));
-    J[1] = fma2(m6, add2(a.d01, M01), mul2(m23, N01));
-    J[2] = fma2(m6, add2(a.d10, M10), mul2(m23, N10));
-    J[3] = fma2(m6, add2(a.d11, M11), fma2(m23, N11, one));
+    J[0] = fma2(c.d00, G00, fma2(c.d01, G10, fma2(m6, S00, one)));
+    J[1] = fma2(c.d00, G01, fma2(c.d01, G11, mul2(m6, S01)));
+    J[2] = fma2(c.d10, G00, fma2(c.d11, G10, mul2(m6, S10)));
+    J[3] = fma2(c.d10, G01, fma2(c.d11, G11, fma2(m6, S11, one)));
 }
 
 // Foot cells of the two lanes along one axis (the lanes' node indices i0, i1, their
@@ -317,13 +316,14 @@ __device__ __forceinline__ V3p vel3d_pair(const VelParams &vp, const StageCoef &
     return r;
 }
 
-__device__ __forceinline__ void matmul3_pair(const F2 *A, const F2 *B, F2 *C)
+// C = A B + D (3x3, row-major), D the accumulator of each entry's chain
+__device__ __forceinline__ void matmul3_acc_pair(const F2 *A, const F2 *B, const F2 *D, F2 *C)
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
-            C[3 * i + j] = fma2(A[3 * i], B[j], fma2(A[3 * i + 1], B[3 + j], mul2(A[3 * i + 2], B[6 + j])));
+            C[3 * i + j] = fma2(A[3 * i], B[j], fma2(A[3 * i + 1], B[3 + j], fma2(A[3 * i + 2], B[6 + j], D[3 * i + j])));
 }
 
 // 3D gradient update of the CIR form by Heun's method (see heun_psi2); Df, Dn as there.
@@ -362,27 +362,31 @@ __device__ __forceinline__ void trace3d_pair(const V3p &a, const VelParams &vp, 
     for (int e = 0; e < 9; ++e) J1[e] = (e % 4) == 0 ? fma2(mdt, a.d[e], one) : mul2(mdt, a.d[e]);
     const V3p b = vel3d_pair<VK>(vp, sc, 1, fma2(mdt, a.v[0], x), fma2(mdt, a.v[1], y),
                                  fma2(mdt, a.v[2], z));
-    F2 M[9];
-    matmul3_pair(b.d, J1, M);
+    // S = Dv1 + Dv2 J1 (Dv1 is the accumulator of the product)
+    F2 S[9];
+    matmul3_acc_pair(b.d, J1, a.d, S);
     const F2 mq = bc(-0.25f * dt);
     F2 J2[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e)
-        J2[e] = (e % 4) == 0 ? fma2(mq, add2(a.d[e], M[e]), one) : mul2(mq, add2(a.d[e], M[e]));
+    for (int e = 0; e < 9; ++e) J2[e] = (e % 4) == 0 ? fma2(mq, S[e], one) : mul2(mq, S[e]);
     F2 s1[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) s1[i] = add2(a.v[i], b.v[i]);
     const V3p c = vel3d_pair<VK>(vp, sc, 2, fma2(mq, s1[0], x), fma2(mq, s1[1], y), fma2(mq, s1[2], z));
     F2 N[9];
-    matmul3_pair(c.d, J2, N);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            N[3 * i + j] = fma2(c.d[3 * i], J2[j], fma2(c.d[3 * i + 1], J2[3 + j], mul2(c.d[3 * i + 2], J2[6 + j])));
     // d = -dt (w3 + (w1 + w2 - 2 w3)/6): exact for constant v;
-    // J = I - dt (Dv1 + M)/6 - 2 dt N / 3 (= I when Dv = 0)
+    // J = I - dt S / 6 - 2 dt N / 3 (= I when Dv = 0)
     const F2 i6 = bc(1.f / 6.f), m2 = bc(-2.f), m6 = bc(-dt / 6.f), m23 = bc(-2.f * dt / 3.f);
 #pragma unroll
     for (int i = 0; i < 3; ++i) d[i] = mul2(mdt, fma2(fma2(m2, c.v[i], s1[i]), i6, c.v[i]));
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        J[e] = fma2(m6, add2(a.d[e], M[e]), (e % 4) == 0 ? fma2(m23, N[e], one) : mul2(m23, N[e]));
+        J[e] = fma2(m6, S[e], (e % 4) == 0 ? fma2(m23, N[e], one) : mul2(m23, N[e]));
 }
 
 // Tricubic Hermite value and gradient for two feet, streamed over the four x-lines of
