@@ -291,6 +291,7 @@ def run_reference(args, wl):
         if wl["dim"] == 2:
             return (outer // 4 + s * band) % (outer - band)
         return slab[0] + (s * band) % (slab[1] - slab[0])
+    trace, cross = args.trace, args.cross
     for s in range(args.warmup):
         b0 = band_at(s)
         oracle.step_band(g, ov, None, 0.0, dt, b0, b0 + band, planes=planes, trace_scheme=trace,
@@ -298,7 +299,8 @@ def run_reference(args, wl):
     t0 = time.perf_counter()
     for s in range(args.steps):
         b0 = band_at(s)
-        oracle.step_band(g, ov, None, s * dt, dt, b0, b0 + band, planes=planes)
+        oracle.step_band(g, ov, None, s * dt, dt, b0, b0 + band, planes=planes, trace_scheme=trace,
+                         cross=cross)
     el = time.perf_counter() - t0
     nodes = args.steps * band * inner_nodes
     value = nodes / el
@@ -310,7 +312,8 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": wl["desc"] + " (FP64 CPU oracle)", "nodes_per_step_sample": band * inner_nodes},
+        "config": {"workload": wl["desc"] + " (FP64 CPU oracle)", "nodes_per_step_sample": band * inner_nodes,
+                   "trace": trace, "cross": cross},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

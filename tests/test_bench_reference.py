@@ -1,0 +1,27 @@
+"""The benchmark's reference arm (the FP64 oracle timed on the host cores) runs on a CPU
+and prints one JSON line with the fields the benchmark contract names, for the default
+workload and for a 3D workload with the variant options."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("extra", [[], ["--workload", "deform512", "--trace", "heun_psi", "--cross", "cell"]])
+def test_reference_arm_json_line(extra):
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"] + extra, cwd=ROOT, env=env, capture_output=True,
+                         text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["unit"] == "node-updates/s" and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    if extra:
+        assert line["config"]["trace"] == "heun_psi" and line["config"]["cross"] == "cell"
