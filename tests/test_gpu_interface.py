@@ -1,5 +1,6 @@
 """Final interface location after whole runs, GPU (FP32) against the FP64 oracle run from the
-same initial data: the interface the method leaves must lie within 1e-4 of the oracle's.
+same initial data: the interface the method leaves must lie within 1e-4 of the oracle's
+(2D below; 3D in the last test).
 
 Runs: configuration 1 (64^2 nodes, circle r = 0.15 at (0.5, 0.75) with exact gradient and
 phi_xy = 0 as given, single vortex T = 8, dt = h, 504 steps: the flow stretches the circle
@@ -51,6 +52,36 @@ def test_final_interface_matches_oracle(G, N):
     e_orc = oracle.symdiff(og, orc, init, Q)[0] / perim
     apart = oracle.symdiff(og, gpu, orc, Q)[0] / perim
     print(f"{N}^2, {steps} steps: interface error GPU {e_gpu:.6e}, oracle {e_orc:.6e}, "
+          f"GPU vs oracle {apart:.3e}, max |dphi| {np.max(np.abs(gpu[0] - orc[0])):.3e}")
+    assert abs(e_gpu - e_orc) <= 1e-4
+    assert apart <= 1e-4
+
+
+@pytest.mark.parametrize("N", [40, 64])
+def test_final_interface_matches_oracle_3d(G, N):
+    """LeVeque's deformation field (T = 3, modulated by cos(pi t / T)), sphere r = 0.15 at
+    (0.35, 0.35, 0.35), dt = h (CFL 2: feet up to two cells away) through the whole period:
+    the GPU's and the oracle's final interfaces, measured against the initial sphere and
+    against each other per unit of the sphere's area."""
+    n = (N, N, N)
+    h = 1.0 / (N - 1)
+    steps = int(math.ceil(3.0 / h - 1e-9))
+    dt = 3.0 / steps
+    st = inputs.sphere_sdf(n, center=(0.35, 0.35, 0.35), r=R0).astype(np.float32)
+    g = G.Grid(n)
+    g.set_state(st, t0=0.0, recon=True)
+    init = g.read_state().astype(np.float64)  # mixed derivatives as the GPU rebuilt them
+    g.step(G.Velocity("deform3d", T=3.0), dt, steps)
+    gpu = g.read_state().astype(np.float64)
+    g.close()
+    og = oracle.grid(n)
+    orc = oracle.run(og, oracle.velocity("deform3d", T=3.0), init, 0.0, dt, steps)
+    area = 4 * math.pi * R0 ** 2
+    qq = 4
+    e_gpu = oracle.symdiff(og, gpu, init, qq)[0] / area
+    e_orc = oracle.symdiff(og, orc, init, qq)[0] / area
+    apart = oracle.symdiff(og, gpu, orc, qq)[0] / area
+    print(f"{N}^3, {steps} steps: interface error GPU {e_gpu:.6e}, oracle {e_orc:.6e}, "
           f"GPU vs oracle {apart:.3e}, max |dphi| {np.max(np.abs(gpu[0] - orc[0])):.3e}")
     assert abs(e_gpu - e_orc) <= 1e-4
     assert apart <= 1e-4
