@@ -38,15 +38,17 @@ k_step2d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
 }
 
 // phi_xy = d/dx psi_y at every node (approach A with one-sided ends); used after
-// set_state and for the COMPACT layout's read-out.
+// set_state and for the COMPACT layout's read-out.  Blocks of 32 x 8 nodes; the grid's
+// y dimension is capped at 65535 and its blocks stride over the rows beyond.
 __global__ void __launch_bounds__(256) k_recon2d(float *__restrict__ buf, Geom g)
 {
     const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    if (i >= g.n0 || j >= g.n1) return;
-    const float *py = buf + 2 * g.plane + (size_t)j * g.pitch;
-    float v = dline(i, g.n0, g.i2h0, [&](int q) { return py[q]; });
-    buf[3 * g.plane + (size_t)j * g.pitch + i] = v;
+    if (i >= g.n0) return;
+    for (int j = blockIdx.y * 8 + threadIdx.y; j < g.n1; j += gridDim.y * 8) {
+        const float *py = buf + 2 * g.plane + (size_t)j * g.pitch;
+        float v = dline(i, g.n0, g.i2h0, [&](int q) { return py[q]; });
+        buf[3 * g.plane + (size_t)j * g.pitch + i] = v;
+    }
 }
 
 template <int TR, int VK, int CR, int WC>
@@ -119,7 +121,7 @@ void tile_box2d(int np, uint32_t box[3])
 cudaError_t launch_recon2d(const Geom &g, float *buf, cudaStream_t s)
 {
     dim3 block(32, 8);
-    dim3 grid((g.n0 + 31) / 32, (g.n1 + 7) / 8);
+    dim3 grid((g.n0 + 31) / 32, std::min((g.n1 + 7) / 8, 65535));
     k_recon2d<<<grid, block, 0, s>>>(buf, g);
     return cudaGetLastError();
 }

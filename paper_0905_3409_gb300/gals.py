@@ -269,7 +269,8 @@ class Grid:
     # -- state
     def set_state(self, state, t0: float = 0.0, recon: bool = False):
         """state: numpy array (host) or torch CUDA tensor (device), float32 planes;
-        1+dim planes (cross derivatives rebuilt) or all planes."""
+        1+dim planes (cross derivatives rebuilt) or all planes.  The data is copied before
+        the call returns."""
         nf = state.shape[0]
         if _is_torch(state):
             import torch
@@ -278,7 +279,6 @@ class Grid:
             torch.cuda.current_stream().synchronize()  # producer work on torch's stream
             ptrs = (ctypes.c_void_p * nf)(*[st[p].data_ptr() for p in range(nf)])
             mem = MEM_DEVICE
-            self._keep = st
         else:
             st = np.ascontiguousarray(state, dtype=np.float32)
             ptrs = (ctypes.c_void_p * nf)(*[st[p].ctypes.data for p in range(nf)])
