@@ -21,8 +21,12 @@ def G():
     return gals
 
 
-def _problems():
-    sizes = [(130, 97), (64, 64), (257, 200), (37, 41), (128, 129), (300, 17)]
+SIZES = [(130, 97), (64, 64), (257, 200), (37, 41), (128, 129), (300, 17)]
+# the smallest problems the ABI takes, and problems one or two tiles narrow in either axis
+TINY = [(4, 4), (5, 4), (4, 5), (6, 1030), (1030, 6), (129, 4), (4, 129)]
+
+
+def _problems(sizes=SIZES):
     probs = inputs.batch_problems(len(sizes), seed=7)
     states, vels, dts = [], [], []
     for (nx, ny), p in zip(sizes, probs):
@@ -35,8 +39,9 @@ def _problems():
 
 
 @pytest.mark.parametrize("layout", ["full", "compact"])
-def test_batch_equals_single_grids(G, layout):
-    sizes, states, modes, dts = _problems()
+@pytest.mark.parametrize("sizes", [SIZES, TINY], ids=["mixed", "tiny"])
+def test_batch_equals_single_grids(G, layout, sizes):
+    sizes, states, modes, dts = _problems(sizes)
     vels = [G.Velocity("fourier2d", modes=m) for m in modes]
     singles = []
     for n, st, v, dt in zip(sizes, states, vels, dts):

@@ -146,7 +146,7 @@ def test_random_state_high_cfl(gals):
 
 
 @pytest.mark.parametrize("layout", ["full", "compact"])
-@pytest.mark.parametrize("n", [(21, 18, 17), (33, 9, 12)])
+@pytest.mark.parametrize("n", [(21, 18, 17), (33, 9, 12), (4, 4, 4), (5, 4, 6), (37, 5, 4)])
 def test_3d_deform(gals, n, layout):
     st = inputs.sphere_sdf(n, center=(0.4, 0.45, 0.5), r=0.25)
     check_step(gals, n, st, "deform3d", 0.5 / (max(n) - 1), t0=0.2, steps=2, layout=layout,
