@@ -9,7 +9,8 @@ oracle's approach-A reconstruction of the GPU's own gradients).
 * 2D with 46340 x 46340 nodes: 2,147,395,600 per plane, just under the 2^31 - 1 elements
   a plane may hold (34 GB per state buffer, 4 planes): plane offsets past 2^31 elements.
   Built on the device; checked on windows as at the benchmark size (a node's new state
-  depends on the state within three cells only)."""
+  depends on the state within three cells only); the diagnostics (area of {phi < 0}) and
+  the point evaluation run on the whole grid."""
 import math
 
 import numpy as np
@@ -128,10 +129,17 @@ def test_2d_largest_plane(G):
     g.read_state(buf)
     torch.cuda.synchronize()
     after = [buf[:, w[1]:w[1] + size, w[0]:w[0] + size].double().cpu().numpy() for w in wins]
+    # diagnostics and point evaluation on the whole grid (64-bit cell and node indices)
+    d = g.diagnostics(q=1)
+    pts = np.concatenate([(np.asarray(w) + margin + rng.uniform(0, size - 2 * margin - 1, (3, 2))) * h
+                          for w in wins])
+    Hp, _, _ = g.eval_points(pts)
     g.close()
+    assert d["nonfinite"] == 0
+    assert abs(d["measure_negative"] - math.pi * r * r) < 1e-5, d["measure_negative"]
     del buf
     torch.cuda.empty_cache()
-    worst = [0.0, 0.0, 0.0]
+    worst, worst_h = [0.0, 0.0, 0.0], []
     for w, b, a in zip(wins, before, after):
         og = oracle.grid((size, size), lo=[w[0] * h, w[1] * h], hi=[(w[0] + size - 1) * h, (w[1] + size - 1) * h])
         ref = oracle.step(og, oracle.velocity("vortex2d", T=8.0), b, t, dt)
@@ -147,4 +155,9 @@ def test_2d_largest_plane(G):
         assert dpsi <= TOL_PSI, (w, dpsi)
         assert dcr <= cr_tol, (w, dcr, cr_tol)
         worst = [max(worst[0], dphi), max(worst[1], dpsi), max(worst[2], dcr)]
-    print("2D 46340^2 windows worst |dphi| |dpsi| |dcross|:", worst)
+        k = len(worst_h)
+        Ho, _ = oracle.eval_points(og, a, pts[3 * k:3 * k + 3])
+        worst_h.append(np.max(np.abs(Hp[3 * k:3 * k + 3] - Ho)))
+        assert worst_h[-1] <= 8 * 2.0 ** -24 * (1.0 + np.max(np.abs(Ho))), (w, worst_h[-1])
+    print("2D 46340^2 windows worst |dphi| |dpsi| |dcross|:", worst, "points |dH|:", max(worst_h),
+          "area", d["measure_negative"])
