@@ -80,6 +80,35 @@ def test_noalloc_matches_diagnostics_twice(G, dim):
     assert _noalloc(G, a, None, 0)["nonfinite"] == a.diagnostics(q=0)["nonfinite"] == 1
 
 
+def test_noalloc_at_its_node_limit(G):
+    """16384 x 16384 nodes, the most the fixed scratch serves (one FP64 partial per 16384
+    nodes): the results of gals_diagnostics, with and without a reference state."""
+    import torch
+    N = 16384
+    n = (N, N)
+    h = 1.0 / (N - 1)
+    grids = []
+    for cx, cy, r in ((0.5, 0.75, 0.15), (0.51, 0.74, 0.16)):
+        st = torch.empty((3, N, N), dtype=torch.float32, device="cuda")
+        X = (torch.arange(N, device="cuda", dtype=torch.float64) * h).float()
+        dx, dy = (X - cx)[None, :], (X - cy)[:, None]
+        torch.add(dx * dx, dy * dy, out=st[0])
+        st[0].sqrt_()
+        torch.div(dx, st[0], out=st[1])
+        torch.div(dy, st[0], out=st[2])
+        st[0].sub_(r)
+        g = G.Grid(n)
+        g.set_state(st, recon=True)
+        del st
+        grids.append(g)
+    torch.cuda.empty_cache()
+    a, b = grids
+    _same(_noalloc(G, a, b, 1), a.diagnostics(q=1, reference=b))
+    _same(_noalloc(G, a, None, 2), a.diagnostics(q=2))
+    a.close()
+    b.close()
+
+
 def test_noalloc_rejects_oversize_and_bad_args(G):
     L = G.lib()
     assert L.gals_noalloc_max_nodes() == 16384 * 16384
