@@ -85,3 +85,52 @@ def test_final_interface_matches_oracle_3d(G, N):
           f"GPU vs oracle {apart:.3e}, max |dphi| {np.max(np.abs(gpu[0] - orc[0])):.3e}")
     assert abs(e_gpu - e_orc) <= 1e-4
     assert apart <= 1e-4
+
+
+def test_vortex_refinement_to_benchmark_size(G):
+    """Configuration 1's run (circle r = 0.15 at (0.5, 0.75), single vortex T = 8, dt = h)
+    on 64^2 to 4096^2 nodes (the benchmark's grid: 32760 steps): the interface error
+    against the initial circle falls at every refinement."""
+    errs, areas = [], []
+    for N in (64, 128, 256, 512, 1024, 2048, 4096):
+        n = (N, N)
+        h = 1.0 / (N - 1)
+        st = inputs.circle_sdf(n).astype(np.float32)
+        g, ref = G.Grid(n), G.Grid(n)
+        g.set_state(st, t0=0.0)
+        ref.set_state(st, t0=0.0)
+        g.step(G.Velocity("vortex2d", T=T), h, int(round(T / h)))
+        d = g.diagnostics(q=4, reference=ref)
+        g.close()
+        ref.close()
+        assert d["nonfinite"] == 0
+        errs.append(d["measure_symdiff"] / (2 * math.pi * R0))
+        areas.append(d["measure_negative"] / (math.pi * R0 * R0) - 1.0)
+    print("single vortex, N = 64 ... 4096: interface error",
+          ", ".join(f"{e:.3e}" for e in errs), "; area change", ", ".join(f"{a:+.2e}" for a in areas))
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1)), errs
+
+
+def test_zalesak_disk_revolution_at_benchmark_size(G):
+    """Zalesak's slotted disk (Sec. 6.2.3) through one revolution of the rigid rotation
+    omega = 2 pi about (0.5, 0.5) on 4096^2 nodes, dt = h / pi (12865 steps): the disk comes
+    back with an interface error (symmetric difference over 2 pi r) below 1e-3 and its area
+    within 1e-3."""
+    N = 4096
+    n = (N, N)
+    h = 1.0 / (N - 1)
+    steps = int(math.ceil(math.pi / h - 1e-9))
+    st = inputs.slotted_disk_sdf(n).astype(np.float32)
+    g, ref = G.Grid(n), G.Grid(n)
+    g.set_state(st, t0=0.0, recon=True)
+    ref.set_state(st, t0=0.0, recon=True)
+    g.step(G.Velocity("rotation", omega=2 * math.pi, center=(0.5, 0.5, 0.0)), 1.0 / steps, steps)
+    d = g.diagnostics(q=4, reference=ref)
+    a0 = ref.diagnostics(q=4)["measure_negative"]
+    g.close()
+    ref.close()
+    e = d["measure_symdiff"] / (2 * math.pi * R0)
+    da = d["measure_negative"] / a0 - 1.0
+    print(f"Zalesak disk, 4096^2, one revolution ({steps} steps): interface error {e:.3e}, "
+          f"area change {da:+.3e}")
+    assert d["nonfinite"] == 0 and e < 1e-3 and abs(da) < 1e-3
