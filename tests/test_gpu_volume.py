@@ -59,3 +59,12 @@ def test_volume_loss_table(G, shape):
     assert all(v < 0 for v in ours)
     assert all(abs(ours[i + 1]) < abs(ours[i]) for i in range(len(ours) - 1))
     assert all(abs(v - p) <= 2.5 for v, p in zip(ours, PAPER[shape])), (ours, PAPER[shape])
+
+
+@pytest.mark.parametrize("shape", ["sphere", "cube"])
+def test_volume_loss_refined_to_benchmark_size(G, shape):
+    """The same runs on 256^3 and 512^3 nodes (the benchmark's grid; 1278 steps): the loss
+    keeps shrinking past the paper's finest grid."""
+    ours = [_loss(G, shape, n) for n in (200, 256, 512)]
+    print(f"volume change {shape}: n=200 {ours[0]:+.3f} %, n=256 {ours[1]:+.3f} %, n=512 {ours[2]:+.3f} %")
+    assert abs(ours[2]) < abs(ours[1]) < abs(ours[0])
