@@ -3,6 +3,10 @@
 Each ``csrc/*.cu`` file is compiled by nvcc in parallel into ``_build/*.o`` and the
 objects are linked into ``paper_0905_3409_gb300/libgals.so``.  Only the files whose
 sources (or the shared headers) changed are recompiled.
+
+``build_checked()`` builds the same sources with ``-DGALS_CHECKED`` into
+``libgals_checked.so`` (objects in ``_build_checked``): the step kernels test their
+data-dependent indexes and report a violation through the grid's error word.
 """
 from __future__ import annotations
 
@@ -42,8 +46,8 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     if _stale(obj, [src] + _headers()):
         cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,20 +57,26 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra=(), build_dir: str = BUILD, lib: str = LIB) -> str:
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if _stale(LIB, objs):
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart"]
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    if _stale(lib, objs):
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(LIB + ".tmp", LIB)
+        os.replace(lib + ".tmp", lib)
     if verbose:
-        print(f"built {LIB}")
-    return LIB
+        print(f"built {lib}")
+    return lib
+
+
+def build_checked(verbose: bool = False) -> str:
+    """The checked build: libgals_checked.so (see the module docstring)."""
+    return build(verbose, extra=("-DGALS_CHECKED",), build_dir=os.path.join(HERE, "_build_checked"),
+                 lib=os.path.join(HERE, "libgals_checked.so"))
 
 
 if __name__ == "__main__":

@@ -252,6 +252,9 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
         gals_destroy_grid(g);
         return st;
     }
+#ifdef GALS_CHECKED
+    g->geom.chk = g->err_dev;  // the checked build's bounds errors land in the error word
+#endif
     if ((e = cudaMemsetAsync(g->err_dev, 0, sizeof(int), g->stream)) != cudaSuccess) {
         gals_status st = cuda_fail(nullptr, e, "cudaMemset");
         gals_destroy_grid(g);
@@ -328,6 +331,7 @@ gals_status gals_destroy_grid(gals_grid *g)
 gals_status gals_set_state(gals_grid *g, const float *const *fields, int nfields, int memspace,
                            double t0, int flags)
 {
+    NvtxRange nvtx_range("gals_set_state");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!fields) return fail(g, GALS_ERR_ARG, "fields is NULL");
     const int core = 1 + g->dim;
@@ -371,6 +375,7 @@ gals_status gals_set_state(gals_grid *g, const float *const *fields, int nfields
 
 gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nsteps)
 {
+    NvtxRange nvtx_range("gals_step");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(g, GALS_ERR_ARG, "dt must be finite and > 0");
@@ -463,6 +468,9 @@ static gals_status check_device_error(gals_grid *g)
     if (e != cudaSuccess) return cuda_fail(g, e, "error word");
     if (code == 0) return GALS_OK;
     cudaMemset(g->err_dev, 0, sizeof(int));
+    if ((code & 0xff) == kErrBounds)
+        return fail(g, GALS_ERR_CUDA, "checked build: an index left its buffer (source line %d)",
+                    code >> 8);
     return fail(g, GALS_ERR_TIMEOUT, "a bounded device wait ran out (code %d); results of the "
                 "affected steps are invalid", code);
 }
@@ -488,6 +496,7 @@ static gals_status ensure_cross(gals_grid *g)
 
 gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int memspace)
 {
+    NvtxRange nvtx_range("gals_read_state");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (!fields || nfields < 1 || nfields > g->nplanes)
@@ -517,6 +526,7 @@ gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int
 gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, double t0,
                            const float *const *in, float *const *out)
 {
+    NvtxRange nvtx_range("gals_step_host");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!in || !out) return fail(g, GALS_ERR_ARG, "in / out is NULL");
     for (int p = 0; p < g->nplanes; ++p)
@@ -622,6 +632,7 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
 gals_status gals_eval_points(gals_grid *g, const double *points, int64_t npoints, int memspace,
                              float *H, float *normal, float *kappa)
 {
+    NvtxRange nvtx_range("gals_eval_points");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (npoints < 0) return fail(g, GALS_ERR_ARG, "npoints must be >= 0");
@@ -677,6 +688,7 @@ gals_status gals_state_planes(gals_grid *g, float **planes, int nplanes, int64_t
 
 gals_status gals_diagnostics(gals_grid *g, const gals_diag_request *req, gals_diag *out)
 {
+    NvtxRange nvtx_range("gals_diagnostics");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!req || !out) return fail(g, GALS_ERR_ARG, "request/out is NULL");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");

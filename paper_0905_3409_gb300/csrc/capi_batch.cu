@@ -179,6 +179,9 @@ gals_status check_err(gals_batch *b)
     if (e != cudaSuccess) return bcuda(b, e, "error word");
     if (code == 0) return GALS_OK;
     cudaMemset(b->err_dev, 0, sizeof(int));
+    if ((code & 0xff) == kErrBounds)
+        return bfail(b, GALS_ERR_CUDA, "checked build: an index left its buffer (source line %d)",
+                     code >> 8);
     return bfail(b, GALS_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", code);
 }
 
@@ -264,6 +267,9 @@ gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch
         (e = cudaMalloc(&b->err_dev, sizeof(int))) != cudaSuccess)
         return bail(e, "cudaMalloc(descriptors)");
     if ((e = cudaMemsetAsync(b->err_dev, 0, sizeof(int), b->stream)) != cudaSuccess) return bail(e, "cudaMemset");
+#ifdef GALS_CHECKED
+    for (BatchProb &P : b->probs) P.g.chk = b->err_dev;  // checked build: bounds errors
+#endif
     if ((e = cudaMemcpyAsync(b->probs_dev, b->probs.data(), sizeof(BatchProb) * count, cudaMemcpyHostToDevice,
                              b->stream)) != cudaSuccess)
         return bail(e, "descriptor upload");
@@ -364,6 +370,7 @@ gals_status gals_batch_set_state(gals_batch *b, int index, const float *const *f
 
 gals_status gals_batch_step(gals_batch *b, const gals_velocity *vels, const double *dt, int nsteps)
 {
+    NvtxRange nvtx_range("gals_batch_step");
     if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return bfail(b, GALS_ERR_ARG, "nsteps must be >= 0");
     std::vector<VelParams> vps;
@@ -469,6 +476,7 @@ gals_status gals_batch_get_tuning(const gals_batch *b, gals_batch_tuning *t)
 gals_status gals_batch_autotune(gals_batch *b, const gals_velocity *vels, const double *dt,
                                 int trial_steps, gals_batch_tuning *out)
 {
+    NvtxRange nvtx_range("gals_batch_autotune");
     if (!b) return bfail(nullptr, GALS_ERR_ARG, "batch is NULL");
     if (trial_steps < 1) return bfail(b, GALS_ERR_ARG, "trial_steps must be >= 1");
     std::vector<VelParams> vps;

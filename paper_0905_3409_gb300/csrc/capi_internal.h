@@ -7,6 +7,17 @@
 #include "gals_internal.h"
 #include "mlp_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range over one ABI call (named after the call), for timeline profilers; free when no
+// profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 namespace gals {
 
 // Validate a velocity descriptor for a grid of dimension `dim` and fill the kernels'

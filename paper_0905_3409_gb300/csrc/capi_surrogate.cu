@@ -235,6 +235,7 @@ gals_status gals_surrogate_destroy(gals_surrogate *s)
 gals_status gals_surrogate_train(gals_surrogate *s, const gals_velocity *vel, double dt, double h,
                                  const gals_train_opts *o, gals_train_report *report)
 {
+    NvtxRange nvtx_range("gals_surrogate_train");
     if (!s) return sfail(nullptr, GALS_ERR_ARG, "surrogate is NULL");
     if (!o) return sfail(s, GALS_ERR_ARG, "opts is NULL");
     if (!(dt > 0.0) || !(h > 0.0) || !std::isfinite(dt) || !std::isfinite(h))

@@ -64,7 +64,39 @@ struct Geom {
     float ih0, ih1, ih2;        // 1/h
     float i2h0, i2h1, i2h2;     // 1/(2h)
     float lo0, lo1, lo2;
+#ifdef GALS_CHECKED
+    int *chk = nullptr;         // device error word of the checked build (see GALS_CHK)
+#endif
 };
+
+// Checked build (-DGALS_CHECKED, libgals_checked.so): GALS_CHK(g, i, n) tests a
+// data-dependent index of the step kernels (staged-tile and global gathers, stores) against
+// its buffer [0, n).  The first violation is recorded in *g.chk as kErrBounds with the
+// source line above the low byte, and the access is redirected to element 0, so a checked
+// run never leaves its buffers.  Without the flag the macro is the index itself and Geom
+// has no chk field, so the normal build's kernels are unchanged.
+constexpr int kErrBounds = 2;
+
+__device__ __forceinline__ int64_t checked_index(int *word, int64_t i, int64_t n, int line)
+{
+    if (i >= 0 && i < n) return i;
+    if (word) atomicCAS(word, 0, kErrBounds | (line << 8));
+    return 0;
+}
+
+#ifdef GALS_CHECKED
+#define GALS_CHK(g, i, n) \
+    ((decltype((i) + 0))::gals::checked_index((g).chk, (int64_t)(i), (int64_t)(n), __LINE__))
+#else
+#define GALS_CHK(g, i, n) (i)
+#endif
+
+// Nodes of one plane in row-major order (rows of `pitch` floats): every node index of a
+// plane lies below this.
+__device__ __forceinline__ int64_t plane_extent(const Geom &g)
+{
+    return (int64_t)g.n2 * g.n1 * g.pitch;
+}
 
 // Time-dependent scalars of the three RK3 stage times (t+dt, t, t+dt/2) of one step.
 // A table of these (one entry per step of a gals_step call) is filled once per call by

@@ -178,7 +178,8 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
     constexpr int TH = Geo<TY, HYV>::TH, PS = Geo<TY, HYV>::PS;
     const int tx = k - x0 + HX, ty = l - y0 + HYV;
     if (tx >= 1 && tx <= TW - 3 && ty >= 0 && ty <= TH - 2) {
-        const float *t = tile + ty * TW + tx;
+        // every read below is t[o + a PS] with -1 <= o <= TW + 2, a < 4
+        const float *t = tile + GALS_CHK(g, ty * TW + tx, PS - TW - 2);
 #pragma unroll
         for (int B = 0; B < 2; ++B) {
 #pragma unroll
@@ -202,7 +203,8 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
     const float *Pphi = in, *Ppx = in + g.plane, *Ppy = in + 2 * g.plane;
 #pragma unroll
     for (int B = 0; B < 2; ++B) {
-        const int r = (l + B) * g.pitch + k;
+        // the reads below lie in r - 1 .. r + 2 of a plane, inside row l + B
+        const int r = GALS_CHK(g, (l + B) * g.pitch + k, plane_extent(g));
 #pragma unroll
         for (int A = 0; A < 2; ++A) {
             const int v = A + 2 * B;
@@ -361,13 +363,13 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
                 node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
                                             cx, ry, phi, px, py);
             }
-            const int o = j0 * g.pitch + i;
+            const int o = GALS_CHK(g, j0 * g.pitch + i, plane_extent(g));
             out[o] = phi.x;
             out[g.plane + o] = px.x;
             out[2 * g.plane + o] = py.x;
             if (WC) psy[WC ? r : 0][tid + 2] = py.x;
             if (r + 1 < rows) {
-                const int o1 = o + g.pitch;
+                const int o1 = GALS_CHK(g, o + g.pitch, plane_extent(g));
                 out[o1] = phi.y;
                 out[g.plane + o1] = px.y;
                 out[2 * g.plane + o1] = py.y;
@@ -393,15 +395,15 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             F2 phi, px, py;
             node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
                                     ry, phi, px, py);
-            psy[WC ? r : 0][ih - x0 + 2] = py.x;
-            if (r + 1 < rows) psy[WC ? r + 1 : 0][ih - x0 + 2] = py.y;
+            psy[WC ? r : 0][GALS_CHK(g, ih - x0 + 2, TX + 3)] = py.x;
+            if (r + 1 < rows) psy[WC ? r + 1 : 0][GALS_CHK(g, ih - x0 + 2, TX + 3)] = py.y;
         }
         __syncthreads();
         if (i < g.n0) {
             for (int r = 0; r < rows; ++r) {
                 const float *line = psy[WC ? r : 0];
                 const float v = dline(i, g.n0, g.i2h0, [&](int q) { return line[q - x0 + 2]; });
-                out[3 * g.plane + (y0 + r) * g.pitch + i] = v;
+                out[3 * g.plane + GALS_CHK(g, (y0 + r) * g.pitch + i, plane_extent(g))] = v;
             }
         }
     }

@@ -97,10 +97,11 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
                 : (tx >= 1 && tx <= T::W - 3 && ty >= 1 && ty <= T::H - 3 && tz >= 0 && tz <= T::D - 2);
         };
         auto lds = [&](int a, int zz, int yy, int xx) {
-            return tile[a * T::PS + ((zz - z0 + HZ) * T::H + yy - y0 + T::HY) * T::W + xx - x0 + HX];
+            return tile[GALS_CHK(g, a * T::PS + ((zz - z0 + HZ) * T::H + yy - y0 + T::HY) * T::W + xx - x0 + HX,
+                                 T::NP * T::PS)];
         };
         auto ldg = [&](int a, int zz, int yy, int xx) {
-            return __ldg(in + a * P + (int64_t)zz * zstride + (int64_t)yy * g.pitch + xx);
+            return __ldg(in + a * P + GALS_CHK(g, (int64_t)zz * zstride + (int64_t)yy * g.pitch + xx, plane_extent(g)));
         };
         const bool in0 = in_tile(k0, l0, m0), in1 = in_tile(k1, l1, m1);
         F2 H, gr[3];
@@ -165,14 +166,15 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
                 psi[a] = fma2(J[a], gr[0], fma2(J[3 + a], gr[1], mul2(J[6 + a], gr[2])));
         }
         if (!valid) continue;
-        const int64_t o = (int64_t)kz * zstride + (int64_t)j * g.pitch + i;
+        const int64_t o = GALS_CHK(g, (int64_t)kz * zstride + (int64_t)j * g.pitch + i, plane_extent(g));
         out[o] = H.x;
 #pragma unroll
         for (int a = 0; a < 3; ++a) out[(a + 1) * P + o] = psi[a].x;
         if (two) {
-            out[o + zstride] = H.y;
+            const int64_t o1 = GALS_CHK(g, o + zstride, plane_extent(g));
+            out[o1] = H.y;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) out[(a + 1) * P + o + zstride] = psi[a].y;
+            for (int a = 0; a < 3; ++a) out[(a + 1) * P + o1] = psi[a].y;
         }
     }
 }

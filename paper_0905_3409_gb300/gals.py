@@ -14,7 +14,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgals.so")
+# GALS_LIB selects another build of the same ABI (the checked build, libgals_checked.so)
+LIB_PATH = os.environ.get("GALS_LIB") or os.path.join(_HERE, "libgals.so")
 
 # enums of gals.h
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE, ERR_UNSUPPORTED = \
