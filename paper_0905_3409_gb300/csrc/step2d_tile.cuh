@@ -178,8 +178,12 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
     constexpr int TH = Geo<TY, HYV>::TH, PS = Geo<TY, HYV>::PS;
     const int tx = k - x0 + HX, ty = l - y0 + HYV;
     if (tx >= 1 && tx <= TW - 3 && ty >= 0 && ty <= TH - 2) {
+#ifdef GALS_CHECKED
         // every read below is t[o + a PS] with -1 <= o <= TW + 2, a < 4
         const float *t = tile + GALS_CHK(g, ty * TW + tx, PS - TW - 2);
+#else
+        const float *t = tile + ty * TW + tx;
+#endif
 #pragma unroll
         for (int B = 0; B < 2; ++B) {
 #pragma unroll
@@ -403,7 +407,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             for (int r = 0; r < rows; ++r) {
                 const float *line = psy[WC ? r : 0];
                 const float v = dline(i, g.n0, g.i2h0, [&](int q) { return line[q - x0 + 2]; });
-                out[3 * g.plane + GALS_CHK(g, (y0 + r) * g.pitch + i, plane_extent(g))] = v;
+                out[GALS_CHK(g, 3 * g.plane + (y0 + r) * g.pitch + i, 4 * g.plane)] = v;
             }
         }
     }

@@ -101,7 +101,11 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
                                  T::NP * T::PS)];
         };
         auto ldg = [&](int a, int zz, int yy, int xx) {
+#ifdef GALS_CHECKED
             return __ldg(in + a * P + GALS_CHK(g, (int64_t)zz * zstride + (int64_t)yy * g.pitch + xx, plane_extent(g)));
+#else
+            return __ldg(in + a * P + (int64_t)zz * zstride + (int64_t)yy * g.pitch + xx);
+#endif
         };
         const bool in0 = in_tile(k0, l0, m0), in1 = in_tile(k1, l1, m1);
         F2 H, gr[3];
@@ -171,10 +175,16 @@ k_step3d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
 #pragma unroll
         for (int a = 0; a < 3; ++a) out[(a + 1) * P + o] = psi[a].x;
         if (two) {
+#ifdef GALS_CHECKED
             const int64_t o1 = GALS_CHK(g, o + zstride, plane_extent(g));
             out[o1] = H.y;
 #pragma unroll
             for (int a = 0; a < 3; ++a) out[(a + 1) * P + o1] = psi[a].y;
+#else
+            out[o + zstride] = H.y;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out[(a + 1) * P + o + zstride] = psi[a].y;
+#endif
         }
     }
 }
