@@ -29,6 +29,14 @@ def built():
     return gals.lib()
 
 
+def test_checked_library_builds_and_exports_the_same_symbols():
+    """The checked build (-DGALS_CHECKED) compiles for sm_103a and exports the same ABI."""
+    from paper_0905_3409_gb300 import build
+    L = ctypes.CDLL(build.build_checked())
+    missing = [n for n in sorted(_declared()) if not hasattr(L, n)]
+    assert not missing, missing
+
+
 def test_library_exports_all_declared_symbols(built):
     decl = _declared()
     assert decl, "no declarations found"
