@@ -26,6 +26,12 @@
  *     has finished; errors of asynchronous work surface at the next synchronising
  *     call (gals_read_state, gals_diagnostics, gals_synchronize).
  *   - Handles are not thread-safe: use one handle per host thread.
+ *   - libgals_checked.so, built from the same sources with -DGALS_CHECKED, exports the
+ *     same ABI; there the step kernels test every data-dependent index against its
+ *     buffer, and an index outside it fails the next synchronising call with
+ *     GALS_ERR_CUDA (the message names the source line).  The normal build has no tests.
+ *   - The step, state, diagnostics and point-evaluation calls are NVTX ranges named after
+ *     the call.
  */
 #ifndef GALS_H
 #define GALS_H
