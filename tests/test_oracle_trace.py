@@ -164,3 +164,57 @@ def test_rk4_flowmap_rotation_and_richardson():
     r = np.max(np.abs(f8 - fr)) / np.max(np.abs(f16 - fr))
     rj = np.max(np.abs(J8 - Jr)) / np.max(np.abs(J16 - Jr))
     assert 12.0 < r < 20.0 and 12.0 < rj < 20.0
+
+
+def _golden():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as f:
+        return json.load(f)
+
+
+def test_deform3d_values_at_exact_points():
+    """LeVeque's field of Sec. 6.2.4 at points where every sine is exact (values worked
+    out by hand from the printed formulas, stored with their derivation): a global sign
+    flip, a swapped component, the garbled sin(2 pi x y) reading or a wrong modulation
+    fails."""
+    gold = _golden()["deform3d_point_values"]
+    vel = oracle.velocity("deform3d", T=gold["T"])
+    for pt in gold["points"]:
+        v, D = oracle.vel_eval(vel, 3, pt["x"], pt["t"])
+        assert np.allclose(v, pt["v"], atol=1e-14), (pt["x"], v)
+        assert np.allclose(D, np.array(pt["Dv"]), atol=1e-13), (pt["x"], D)
+
+
+def _fourier_psi(modes, x, y, t):
+    """Stream function of the Fourier fields, written out again from its definition:
+    Psi = sum_m a_m sin(k_m pi x) sin(l_m pi y) cos(2 pi n_m t + chi_m)."""
+    return sum(a * math.sin(k * math.pi * x) * math.sin(l * math.pi * y)
+               * math.cos(2 * math.pi * n * t + chi) for a, k, l, n, chi in modes)
+
+
+def test_fourier_velocity_is_rotated_stream_function_gradient():
+    """v = (-dPsi/dy, dPsi/dx) by central differences of an independently written Psi:
+    the field running the wrong way round, or a mode's k and l exchanged, fails."""
+    modes = inputs.fourier_modes(16, seed=5, periodic=True)
+    vel = oracle.velocity("fourier2d", modes=modes)
+    rng = np.random.default_rng(8)
+    eps = 1e-6
+    for _ in range(12):
+        x, y, t = rng.uniform(0.02, 0.98), rng.uniform(0.02, 0.98), rng.uniform(0, 1)
+        v, _ = oracle.vel_eval(vel, 2, (x, y), t)
+        u_ref = -(_fourier_psi(modes, x, y + eps, t) - _fourier_psi(modes, x, y - eps, t)) / (2 * eps)
+        w_ref = (_fourier_psi(modes, x + eps, y, t) - _fourier_psi(modes, x - eps, y, t)) / (2 * eps)
+        assert v == pytest.approx([u_ref, w_ref], abs=1e-7)
+
+
+def test_fourier_single_mode_hand_values():
+    """One mode Psi = sin(pi x) sin(2 pi y) (a = 1, k = 1, l = 2, steady): at (1/4, 1/8)
+    u = -Psi_y = -2 pi sin(pi/4) cos(pi/4) = -pi, v = Psi_x = pi cos(pi/4) sin(pi/4) = pi/2,
+    du/dx = -2 pi^2 cos(pi/4)^2 = -pi^2, du/dy = 4 pi^2 sin(pi/4)^2 = 2 pi^2,
+    dv/dx = -pi^2 sin(pi/4)^2 = -pi^2/2, dv/dy = pi^2."""
+    vel = oracle.velocity("fourier2d", modes=np.array([[1.0, 1.0, 2.0, 0.0, 0.0]]))
+    v, D = oracle.vel_eval(vel, 2, (0.25, 0.125), 0.37)
+    p2 = math.pi ** 2
+    assert v == pytest.approx([-math.pi, math.pi / 2], abs=1e-14)
+    assert np.allclose(D, [[-p2, 2 * p2], [-p2 / 2, p2]], atol=1e-13)
