@@ -185,6 +185,45 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+SPIN_CYCLES = 200_000  # ~0.1 ms at 2 GHz: covers the host's graph submission
+
+
+def time_windows(step_k, stream, R, min_s=1.0, min_windows=5, max_windows=4000):
+    """CUDA-event times (ms) of repeated windows of K steps on `stream`.  Each window is
+    bracketed by a barrier and a device synchronise on both sides; a short spin kernel
+    queued on the stream ahead of the first event keeps the host's submission of the
+    K-step graph out of the window.  The number of windows makes at least `min_s` of
+    timed load (so that the clock samples cover a steady state); every rank runs the
+    same number, from the slowest rank's first window."""
+    import torch
+    from paper_0905_3409_gb300 import replicas
+
+    def one():
+        replicas.barrier(R)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(SPIN_CYCLES)
+        e0.record(stream)
+        step_k()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    first = replicas.max_over_ranks(R, one(), device="cuda")
+    n = int(min(max(math.ceil(min_s * 1e3 / max(first, 1e-3)), min_windows), max_windows))
+    wins = [one() for _ in range(n)]
+    replicas.barrier(R)
+    return wins
+
+
+def window_summary(wins):
+    w = np.asarray(wins)
+    return {"count": int(w.size), "median_ms": float(np.median(w)), "min_ms": float(w.min()),
+            "max_ms": float(w.max()), "timed_s": float(w.sum() / 1e3)}
+
+
 # the sources that define each benchmarked kernel: a recorded DRAM traffic figure is
 # reported only while these files are unchanged
 KERNEL_SOURCES = {
@@ -309,6 +348,7 @@ def run_reference(args, wl):
              f"({band * inner_nodes} node updates) of the {n} grid"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "ranks_measured": 1,  # one CPU process on rank 0, whatever the launch's rank count
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -389,18 +429,9 @@ def run_batch(args, wl):
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
-    replicas.barrier(R)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(vels, dts, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    replicas.barrier(R)
-    ms = e0.elapsed_time(e1)
+    wins = time_windows(lambda: b.step(vels, dts, args.steps), stream, R)
     clocks = sampler.stop() if rank == 0 else None
-    ms = replicas.max_over_ranks(R, ms, device="cuda")
+    ms = replicas.max_over_ranks(R, float(np.median(wins)), device="cuda")
     value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
     bpn = bytes_per_node(2, args.layout)
     achieved = bpn * nodes / (ms * 1e-3 / args.steps) / 1e9
@@ -427,6 +458,7 @@ def run_batch(args, wl):
             "config": {"workload": wl["desc"], "layout": args.layout, "problems": len(sizes),
                        "nodes": nodes, "bytes_per_node_update": bpn, "tuning": tuning,
                        "l2": f"inputs larger than L2 ({nodes * 16 / 1e6:.0f} MB state per buffer)",
+                       "timing": "median of repeated K-step windows", "windows": window_summary(wins),
                        "parallelism": f"{world} independent replica(s), one per GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(args.workload, args.layout),
@@ -469,6 +501,7 @@ def run_reference_batch(args, wl):
     sample = f"each step: one band of {band} rows of the largest problem ({p.n}^2)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "ranks_measured": 1,  # one CPU process on rank 0, whatever the launch's rank count
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": wl["desc"] + " (FP64 CPU oracle)"},
@@ -510,18 +543,9 @@ def run_ours(args, wl):
     sampler = ClockSampler(local)
     if rank == 0:
         sampler.start()
-    replicas.barrier(R)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    g.step(vel, dt, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    replicas.barrier(R)
-    ms = e0.elapsed_time(e1)
+    wins = time_windows(lambda: g.step(vel, dt, args.steps), stream, R)
     clocks = sampler.stop() if rank == 0 else None
-    ms = replicas.max_over_ranks(R, ms, device="cuda")
+    ms = replicas.max_over_ranks(R, float(np.median(wins)), device="cuda")
     value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
 
     # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels)
@@ -573,6 +597,9 @@ def run_ours(args, wl):
                        "trace": args.trace, "cross": args.cross,
                        "dt": dt, "bytes_per_node_update": bpn,
                        "l2": f"inputs larger than L2 ({nodes * nplanes * 4 / 1e6:.0f} MB state per buffer)",
+                       "timing": "median of repeated K-step windows (CUDA events on the grid "
+                                 "stream, barrier + synchronize around each)",
+                       "windows": window_summary(wins),
                        "parallelism": f"{world} independent replica(s), one per GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
@@ -590,10 +617,78 @@ def run_ours(args, wl):
                                           cross=args.cross)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": sample}
-        print(json.dumps(line))
     g.close()
     g2.close()
+    if args.workload == "vortex4096" and not args.no_secondary:
+        sec = secondary_3d(args, R, local, stream)
+        if rank == 0:
+            line["secondary"] = sec
+    if rank == 0:
+        print(json.dumps(line))
     replicas.finish(R)
+
+
+def sphere_state_device(n, center=(0.35, 0.35, 0.35), r=0.15):
+    """phi = |x - c| - r and psi = (x - c)/|x - c| on the device (float32 planes), the
+    sphere initial data of the 3D deformation test, built slice by slice."""
+    import torch
+    nx, ny, nz = n
+    st = torch.empty((4, nz, ny, nx), dtype=torch.float32, device="cuda")
+    ax = [torch.arange(m, device="cuda", dtype=torch.float64) / (m - 1) for m in n]
+    dx = (ax[0] - center[0])[None, :]
+    dy = (ax[1] - center[1])[:, None]
+    for k in range(nz):
+        dz = float(ax[2][k] - center[2])
+        d = torch.sqrt(dx * dx + dy * dy + dz * dz)
+        st[0, k] = (d - r).float()
+        st[1, k] = (dx / d).float()
+        st[2, k] = (dy / d).float()
+        st[3, k] = (dz / d).float()
+    return st
+
+
+def secondary_3d(args, R, local, stream):
+    """The 512^3 deformation workload timed in the same run with the same protocol
+    (graph replay of K >= 50 steps, repeated windows, CUDA events on the grid stream)."""
+    import torch
+    from paper_0905_3409_gb300 import gals
+    wl = WORKLOADS["deform512"]
+    n = wl["n"]
+    nodes = int(np.prod(n))
+    dt = 1.0 / (n[0] - 1) / wl["vmax"]
+    K = max(args.steps, 50)
+    vel = gals.Velocity(**wl["vel"])
+    g = gals.Grid(n, stream=stream)
+    st = sphere_state_device(n)
+    g.set_state(st, t0=0.0, recon=True)
+    del st
+    torch.cuda.empty_cache()
+    g.step(vel, dt, args.warmup)
+    g.step(vel, dt, K)  # captures the K-step graph
+    g.synchronize()
+    sampler = ClockSampler(local)
+    if R.rank == 0:
+        sampler.start()
+    wins = time_windows(lambda: g.step(vel, dt, K), stream, R)
+    clocks = sampler.stop() if R.rank == 0 else None
+    ms = replicas_max(R, float(np.median(wins)))
+    g.close()
+    bpn = bytes_per_node(3, "full")
+    achieved = bpn * nodes / (ms * 1e-3 / K) / 1e9
+    peak, peak_kind = measured_peaks()
+    return {"workload": wl["desc"], "nodes": nodes, "steps": K, "dt": dt,
+            "value": nodes * K * R.world / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / K,
+            "windows": window_summary(wins),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": recorded_traffic("deform512", "full"),
+                         "kernel": "k_step3d + k_recon3d_tma (2 launches per step)"},
+            "gpu_launches_per_window": 2 * K + 2, "clocks": clocks}
+
+
+def replicas_max(R, v):
+    from paper_0905_3409_gb300 import replicas
+    return replicas.max_over_ranks(R, v, device="cuda")
 
 
 # ---------------------------------------------------------------------- learned trace
@@ -771,6 +866,8 @@ def main():
                     help="single-grid workloads: mixed derivatives by approach A or B (Sec. 2.3)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: skip the 512^3 3D line timed in the same run")
     ap.add_argument("--train-steps", type=int, default=2000, help="learned trace: optimizer steps")
     ap.add_argument("--tol", type=float, default=0.05,
                     help="learned trace: residual-check tolerance (cells and Jacobian entries)")

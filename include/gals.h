@@ -383,24 +383,30 @@ const char *gals_surrogate_last_error(const gals_surrogate *s);
  * __device__ array of about 128 KB that each device holding the library keeps until
  * the process exits) instead of allocating.
  *
- *   state       device pointer of plane 0 (plane order as above, FULL: all planes);
- *               plane p starts at state + p*plane_stride, node (i,j,k) of a plane at
- *               (k*n[1] + j)*row_pitch + i.  gals_state_planes gives these for a grid.
+ *   state       device pointer of plane 0 (plane order as above, all 4 / 8 planes with
+ *               valid mixed derivatives; plane p starts at state + p*plane_stride, node
+ *               (i,j,k) of a plane at (k*n[1] + j)*row_pitch + i.  gals_state_planes gives
+ *               these for a grid; for a COMPACT grid its mixed-derivative planes hold valid
+ *               data only after gals_read_state, and the call cannot tell stale ones apart).
  *   reference   NULL, or another state of the same shape and layout.
+ *   row_pitch   floats per row, n[0] <= row_pitch <= 2^31 - 1.
+ *   plane_stride floats per plane, at least row_pitch * n[1] (* n[2] in 3D).
  *   q           samples per cell and axis, 0..16.
  *   cuda_stream stream to order the work on (NULL: the legacy default stream).
  *   out         host struct; t and steps are 0 (the state has no clock here).
  * Limits and rules:
  *   - grids of more than gals_noalloc_max_nodes() nodes (268,435,456) are rejected
  *     with GALS_ERR_ARG: the scratch holds one partial sum per 16384 nodes;
- *   - the first call on a device looks up the scratch's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - set-up: the first call on a device looks up the scratch's device address
+ *     (cudaGetSymbolAddress), and so does the first call after that device's context
+ *     changed (cudaDeviceReset, another current context); make that first call before
+ *     any stream capture;
  *   - every call on a device shares the one scratch area, which keeps the last call's
  *     contents (each call clears what must start at zero): calls whose GPU work
  *     overlaps -- on different streams or host threads -- race and give wrong results;
- *   - synchronises `cuda_stream`.
+ *   - synchronises `cuda_stream` before returning.
  * Errors: GALS_ERR_ARG (dims, pointers, q, strides, size limit), GALS_ERR_CUDA; the
- * message is in gals_noalloc_last_error(). */
+ * message is in gals_noalloc_last_error(), which is per host thread. */
 gals_status gals_diagnostics_noalloc(int dim, const int *n, const double *lo, const double *hi,
                                      const float *state, const float *reference,
                                      int64_t row_pitch, int64_t plane_stride, int q,

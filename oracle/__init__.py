@@ -88,6 +88,8 @@ def lib():
             L.orc_step.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Velocity), ctypes.c_int,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, pp, pp,
                                    ctypes.c_int]
+            L.orc_step_given.argtypes = [ctypes.POINTER(_Grid), ctypes.c_int, pp, pp, pp, pp,
+                                         ctypes.c_int]
             L.orc_step_nodes.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Velocity),
                                          ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, pp, ctypes.c_long,
@@ -259,6 +261,22 @@ def step(g, vel, state, t, dt, trace_scheme="rk3", cross="central", nthreads=Non
                    _CROSS_NAMES[cross], float(t), float(dt),
                    _planes_ptr(ins), _planes_ptr(outs),
                    default_threads() if nthreads is None else int(nthreads))
+    return np.stack(outs).reshape(shape)
+
+
+def step_given(g, state, disp, jac, cross="central", nthreads=None):
+    """One step with the backward map given per node instead of traced: ``disp`` is
+    (dim, *grid) of foot - x, ``jac`` is (dim, dim, *grid) with jac[a, b] = d foot_a / d x_b."""
+    shape = np.shape(state)
+    ins = _state_list(state, g)
+    dim = g.dim
+    d = [np.ascontiguousarray(np.asarray(disp[a], dtype=np.float64)).ravel() for a in range(dim)]
+    J = [np.ascontiguousarray(np.asarray(jac[a][b], dtype=np.float64)).ravel()
+         for a in range(dim) for b in range(dim)]
+    outs = [np.empty_like(p) for p in ins]
+    lib().orc_step_given(ctypes.byref(g), _CROSS_NAMES[cross], _planes_ptr(ins), _planes_ptr(d),
+                         _planes_ptr(J), _planes_ptr(outs),
+                         default_threads() if nthreads is None else int(nthreads))
     return np.stack(outs).reshape(shape)
 
 

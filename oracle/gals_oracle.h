@@ -121,6 +121,14 @@ void orc_step(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
               double t, double dt, const double *const *in, double *const *out,
               int nthreads);
 
+/* full step with the backward map given instead of traced (the learned flow map
+ * supplies it): node x_j's foot is x_j + disp[d][j] and its Jacobian
+ * J[a][b] = d foot_a / d x_b is jac[dim*a + b][j]; then Sec. 4 step 2 at that foot,
+ * psi+ = J^T grad H (eq. superconsistency) and the cross reconstruction, as orc_step */
+void orc_step_given(const orc_grid *g, int cross, const double *const *in,
+                    const double *const *disp, const double *const *jac, double *const *out,
+                    int nthreads);
+
 /* new state (all planes) at a list of nodes only; for parity checks at full size */
 void orc_step_nodes(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
                     double t, double dt, const double *const *in, long nsel,

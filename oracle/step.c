@@ -103,19 +103,13 @@ void orc_cross_cell(int dim, const double *h, double *data)
 #undef D3
 }
 
-void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
-                     double t, double dt, const double *const *in,
-                     int i, int j, int k, double *phi, double psi[3])
+/* steps 2 of Sec. 4 at one foot point: the cell the foot falls into (clamped into the box,
+ * floor, clamped to [0, n-2]), its 4^p data (approach B rebuilds the mixed entries per
+ * cell), and the interpolant's value and gradient there (eq. p-cubic_interpolant) */
+static void eval_at_foot(const orc_grid *g, int cross, const double *const *in,
+                         const double foot[3], double *H, double gradH[3])
 {
     int dim = g->dim;
-    int idx[3] = {i, j, k};
-    double x[3] = {0, 0, 0}, foot[3], J[9];
-    for (int d = 0; d < dim; ++d) x[d] = g->lo[d] + idx[d] * g->h[d];
-
-    /* step 1: backward trace with Jacobian */
-    orc_trace(trace, vel, dim, x, t, dt, foot, J);
-
-    /* locate the cell (floor, clamped) */
     int cell[3] = {0, 0, 0};
     double xi[3] = {0, 0, 0};
     for (int d = 0; d < dim; ++d) {
@@ -129,8 +123,6 @@ void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int 
         cell[d] = c;
         xi[d] = (f - (g->lo[d] + c * g->h[d])) / g->h[d];
     }
-
-    /* step 2: gather the 4^p cell data and evaluate the interpolant */
     int np = 1 << dim;
     double data[64];
     for (int v = 0; v < np; ++v) {
@@ -141,8 +133,35 @@ void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int 
         for (int a = 0; a < np; ++a) data[v * np + a] = in[plane_of(dim, a)][nid];
     }
     if (cross == ORC_CROSS_CELL && dim >= 2) orc_cross_cell(dim, g->h, data);
-    double H, gradH[3] = {0, 0, 0};
-    orc_hermite_cell(dim, data, g->h, xi, &H, gradH);
+    gradH[0] = gradH[1] = gradH[2] = 0.0;
+    orc_hermite_cell(dim, data, g->h, xi, H, gradH);
+}
+
+/* superconsistent update (eq. superconsistency): psi+ = J^T grad H(foot) */
+static void superconsistent_psi(int dim, const double J[9], const double gradH[3], double psi[3])
+{
+    for (int a = 0; a < dim; ++a) {
+        double s = 0.0;
+        for (int b = 0; b < dim; ++b) s += J[3 * b + a] * gradH[b];
+        psi[a] = s;
+    }
+}
+
+void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int cross,
+                     double t, double dt, const double *const *in,
+                     int i, int j, int k, double *phi, double psi[3])
+{
+    int dim = g->dim;
+    int idx[3] = {i, j, k};
+    double x[3] = {0, 0, 0}, foot[3], J[9];
+    for (int d = 0; d < dim; ++d) x[d] = g->lo[d] + idx[d] * g->h[d];
+
+    /* step 1: backward trace with Jacobian */
+    orc_trace(trace, vel, dim, x, t, dt, foot, J);
+
+    /* step 2: the interpolant of the foot's cell */
+    double H, gradH[3];
+    eval_at_foot(g, cross, in, foot, &H, gradH);
 
     *phi = H;
     if (trace == ORC_TRACE_HEUN_PSI) {
@@ -167,12 +186,46 @@ void orc_node_update(const orc_grid *g, const orc_velocity *vel, int trace, int 
         for (int a = 0; a < dim; ++a) psi[a] = gradH[a] + 0.5 * dt * (k1[a] + k2[a]);
         return;
     }
-    /* superconsistent update: psi+ = J^T grad H(foot) */
-    for (int a = 0; a < dim; ++a) {
-        double s = 0.0;
-        for (int b = 0; b < dim; ++b) s += J[3 * b + a] * gradH[b];
-        psi[a] = s;
+    superconsistent_psi(dim, J, gradH, psi);
+}
+
+void orc_step_given(const orc_grid *g, int cross, const double *const *in,
+                    const double *const *disp, const double *const *jac, double *const *out,
+                    int nthreads)
+{
+    int dim = g->dim;
+    int nz = dim == 3 ? g->n[2] : 1, ny = dim >= 2 ? g->n[1] : 1;
+    long rows = (long)nz * ny;
+    (void)nthreads;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (long r = 0; r < rows; ++r) {
+        int k = (int)(r / ny), j = (int)(r % ny);
+        int idx[3] = {0, j, k};
+        for (int i = 0; i < g->n[0]; ++i) {
+            idx[0] = i;
+            long id = node_index(g, i, j, k);
+            double foot[3] = {0, 0, 0}, J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int d = 0; d < dim; ++d) foot[d] = g->lo[d] + idx[d] * g->h[d] + disp[d][id];
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) J[3 * a + b] = jac[dim * a + b][id];
+            double H, gradH[3], psi[3];
+            eval_at_foot(g, cross, in, foot, &H, gradH);
+            superconsistent_psi(dim, J, gradH, psi);
+            out[0][id] = H;
+            for (int a = 0; a < dim; ++a) out[1 + a][id] = psi[a];
+        }
     }
+    if (dim == 1) return;
+    if (cross == ORC_CROSS_ZERO || cross == ORC_CROSS_CELL) {
+        long N = total_nodes(g);
+        int first = dim == 2 ? 3 : 4, nc = dim == 2 ? 1 : 4;
+        for (int c = 0; c < nc; ++c) memset(out[first + c], 0, N * sizeof(double));
+        return;
+    }
+    orc_recon_cross(g, out);
 }
 
 /* stencil of the first-derivative approximation along one axis at index i:

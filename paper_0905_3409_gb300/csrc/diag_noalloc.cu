@@ -13,6 +13,7 @@
 // The scratch holds the result counters and one FP64 partial sum per block of the node
 // pass, one block per kNodesPerPartial nodes, so its capacity bounds the grid size.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -34,35 +35,72 @@ struct Scratch {
 };
 
 // The scratch itself (about 128 KB per device).  In host code this name is only a
-// stand-in: its device address comes from cudaGetSymbolAddress, once per device.
+// stand-in: its device address comes from cudaGetSymbolAddress, once per device (and
+// context).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(Scratch)];
 
 std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;  // unique id of the context the address belongs to
+    void *addr = nullptr;
+};
+ScratchSlot g_slot[kMaxDevices];
 
-// Device address of the scratch on the current device (looked up on first use).
+// Unique id of the driver's current context (cuCtxGetCurrent, cuCtxGetId; reached through
+// the runtime's driver entry points so that the library links against the runtime only);
+// 0 when no context is current or the driver does not offer the calls.  Ids are never
+// reused within a process, unlike context handles.
+unsigned long long current_context_id()
+{
+    typedef int (*CtxGetCurrent)(void **);
+    typedef int (*CtxGetId)(void *, unsigned long long *);
+    auto entry = [](const char *name) -> void * {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return p;
+    };
+    static CtxGetCurrent get_current = reinterpret_cast<CtxGetCurrent>(entry("cuCtxGetCurrent"));
+    static CtxGetId get_id = reinterpret_cast<CtxGetId>(entry("cuCtxGetId"));
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of the scratch on the current device.  The lookup
+// (cudaGetSymbolAddress) is the set-up: it runs on the first call on a device, and again
+// only if that device's context has changed since (after cudaDeviceReset, or when the
+// caller made another context current), because the address belongs to one context.
 cudaError_t scratch_address(Scratch **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long id = current_context_id();  // 0 before a context is current
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    ScratchSlot &slot = g_slot[dev];
+    if (!slot.addr || id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        slot.addr = p;
+        slot.ctx_id = current_context_id();
     }
-    *out = static_cast<Scratch *>(g_scratch_addr[dev]);
+    *out = static_cast<Scratch *>(slot.addr);
     return cudaSuccess;
 }
 
-char g_noalloc_err[256] = "";
+// the message of the calling thread's last failed call
+thread_local char g_noalloc_err[256] = "";
 
 gals_status nfail(gals_status st, const char *msg)
 {
     std::strncpy(g_noalloc_err, msg, sizeof(g_noalloc_err) - 1);
+    g_noalloc_err[sizeof(g_noalloc_err) - 1] = '\0';
     return st;
 }
 
@@ -87,14 +125,18 @@ gals_status gals_diagnostics_noalloc(int dim, const int *n, const double *lo, co
         if (n[i] < 4) return nfail(GALS_ERR_ARG, "every n[i] must be >= 4");
         if (!std::isfinite(lo[i]) || !std::isfinite(hi[i]) || !(hi[i] > lo[i]))
             return nfail(GALS_ERR_ARG, "need finite lo < hi");
-        nodes *= n[i];
+        nodes *= n[i];  // n[i] < 2^31 and nodes <= kMaxNodes < 2^29 before: no overflow
+        if (nodes > kMaxNodes)
+            return nfail(GALS_ERR_ARG, "grid larger than the no-allocation scratch allows "
+                                       "(gals_noalloc_max_nodes() nodes)");
     }
     const int64_t rows = (int64_t)n[1] * (dim == 3 ? n[2] : 1);
-    if (row_pitch < n[0] || plane_stride < row_pitch * rows)
-        return nfail(GALS_ERR_ARG, "row_pitch / plane_stride smaller than the grid");
-    if (nodes > kMaxNodes)
-        return nfail(GALS_ERR_ARG, "grid larger than the no-allocation scratch allows "
-                                   "(gals_noalloc_max_nodes() nodes)");
+    // the kernels keep the row pitch in an int and index planes as p * plane_stride
+    // (p < 8) in 64 bits
+    if (row_pitch < n[0] || row_pitch > INT32_MAX)
+        return nfail(GALS_ERR_ARG, "row_pitch must be in [n[0], 2^31 - 1]");
+    if (plane_stride < row_pitch * rows || plane_stride > INT64_MAX / 8)  // rows < 2^29
+        return nfail(GALS_ERR_ARG, "plane_stride smaller than a plane, or too large");
     Geom G{};
     G.n0 = n[0]; G.n1 = n[1]; G.n2 = dim == 3 ? n[2] : 1;
     G.pitch = (int)row_pitch;

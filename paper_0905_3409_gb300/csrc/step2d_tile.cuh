@@ -208,6 +208,12 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
 #pragma unroll
     for (int B = 0; B < 2; ++B) {
         // the reads below lie in r - 1 .. r + 2 of a plane, inside row l + B
+#ifdef GALS_CHECKED
+        // the whole window: the cell's first column k <= n0 - 2 and the row exist (a read
+        // past the row's end would wrap into the next row unseen by the index test below)
+        (void)GALS_CHK(g, k, g.n0 - 1);
+        (void)GALS_CHK(g, l + B, g.n1);
+#endif
         const int r = GALS_CHK(g, (l + B) * g.pitch + k, plane_extent(g));
 #pragma unroll
         for (int A = 0; A < 2; ++A) {

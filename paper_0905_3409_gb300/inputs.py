@@ -168,15 +168,19 @@ def ellipse_sdf(n, center, a, b, angle, lo=None, hi=None, iters=120):
     lo_t = np.full_like(y0, -b * b)
     hi_t = np.sqrt(a * a * y0 * y0 + b * b * y1 * y1) + 1e-300
     hi_t = np.maximum(hi_t, 0.0)
+    def ratio(num, den, coord):
+        # num/den where the coordinate is non-zero, 0 on the axis (where den may reach 0)
+        return np.divide(num, den, out=np.zeros_like(num), where=coord > 0)
+
     for _ in range(iters):
         mid = 0.5 * (lo_t + hi_t)
-        F = (a * y0 / (mid + a * a)) ** 2 + (b * y1 / (mid + b * b)) ** 2 - 1.0
+        F = ratio(a * y0, mid + a * a, y0) ** 2 + ratio(b * y1, mid + b * b, y1) ** 2 - 1.0
         pos = F > 0
         lo_t = np.where(pos, mid, lo_t)
         hi_t = np.where(pos, hi_t, mid)
     t = 0.5 * (lo_t + hi_t)
-    x0 = a * a * y0 / (t + a * a)
-    x1 = b * b * y1 / (t + b * b)
+    x0 = ratio(a * a * y0, t + a * a, y0)
+    x1 = ratio(b * b * y1, t + b * b, y1)
     # major-axis special case
     axis = (y1 == 0)
     thr = (a * a - b * b) / a

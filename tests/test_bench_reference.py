@@ -45,3 +45,4 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["ranks_measured"] == 1  # the value is one CPU process's, not a 2-way sum

@@ -134,6 +134,64 @@ def test_training_lowers_loss_and_fallback(G, field):
         g.step(G.Velocity("fourier2d", modes=modes * 1.01, trace="surrogate", surrogate=S), dt, 1)
 
 
+def test_learned_step_matches_oracle_given_map(G, field):
+    """One step driven by the network alone (residual check off, no fallback) on a
+    ragged grid (257 x 130 nodes, h = 1/256 on [0,1] x [0, 129/256]: a partial last
+    tile in x and in y) against the oracle step fed the same backward map.  The map is
+    rebuilt on the host from the network's normalised outputs y at the nodes' inputs
+    (2x - 1, 2y - 1, 2 (t mod 1) - 1), by the documented rule: foot - x = (y0 s0 h,
+    y1 s1 h), J = I + dt [[y2 s2, y3 s3], [y4 s4, y5 s5]] (s: the output scales), in FP64.
+    The outputs come from the tensor-core forward pass (the tile code the step runs),
+    which is itself held to the FP64 oracle network below; the oracle then does the
+    Hermite stage and psi+ = J^T grad H (Sec. 4 step 2, eq. superconsistency).  A wrong
+    scale, h or dt factor, a transposed J or a shifted input fails the per-step
+    tolerances."""
+    modes, n, h, dt = field
+    vel = G.Velocity("fourier2d", modes=modes)
+    S = G.Surrogate(seed=17)
+    S.train(vel, dt, h, steps=300, batch=8192, lr=2e-3, lr_min=1e-4)
+    S.set_check(tol_x=1e9, tol_J=1e9, samples=1)
+    shape = (257, 130)
+    hi = (1.0, (shape[1] - 1) * h)
+    t0 = 0.3
+    st = inputs.circle_sdf(shape, center=(0.45, 0.27), r=0.15, lo=(0.0, 0.0), hi=hi).astype(np.float32)
+    g = G.Grid(shape, lo=(0.0, 0.0), hi=hi)
+    g.set_state(st, t0=t0, recon=True)
+    before = g.read_state().astype(np.float64)
+    S.stats(reset=True)
+    g.step(G.Velocity("fourier2d", modes=modes, trace="surrogate", surrogate=S), dt, 1)
+    after = g.read_state().astype(np.float64)
+    tiles, falls = S.stats()
+    assert falls == 0 and tiles == ((shape[0] + 127) // 128) * shape[1]
+
+    # the network's inputs at every node, in the kernel's FP32 arithmetic
+    i = np.arange(shape[0], dtype=np.float32)
+    j = np.arange(shape[1], dtype=np.float32)
+    hf = np.float32(h)
+    xs, ys = np.meshgrid(i * hf, j * hf)  # (ny, nx), x fastest
+    phase = np.float32(t0 - math.floor(t0))
+    X = np.stack([np.float32(2) * xs - np.float32(1), np.float32(2) * ys - np.float32(1),
+                  np.full_like(xs, np.float32(2) * phase - np.float32(1))], -1).reshape(-1, 3)
+    Y = S.forward(X).astype(np.float64)
+    params, scales = S.get_params()
+    Yref = oracle.mlp_forward(SIZES, params.astype(np.float64), X.astype(np.float64))
+    assert np.max(np.abs(Y - Yref)) <= 2e-2 * max(1.0, np.max(np.abs(Yref)))
+    s = scales.astype(np.float64)
+    Y = Y.reshape(shape[1], shape[0], 6)
+    disp = np.stack([Y[..., 0] * s[0] * h, Y[..., 1] * s[1] * h])
+    jac = np.array([[1.0 + dt * Y[..., 2] * s[2], dt * Y[..., 3] * s[3]],
+                    [dt * Y[..., 4] * s[4], 1.0 + dt * Y[..., 5] * s[5]]])
+    assert np.max(np.abs(disp)) > 0.2 * h  # the network moves the feet
+    ref = oracle.step_given(oracle.grid(shape, lo=(0.0, 0.0), hi=hi), before, disp, jac)
+    dphi = np.max(np.abs(after[0] - ref[0]))
+    dpsi = np.max(np.abs(after[1:3] - ref[1:3]))
+    assert dphi <= 1e-5 and dpsi <= 1e-4, (dphi, dpsi)
+    # mixed derivatives: the oracle's approach-A rebuild of the GPU's own gradients
+    rec = oracle.recon_cross(oracle.grid(shape, lo=(0.0, 0.0), hi=hi), after)
+    scale = max(1.0, np.max(np.abs(after[1:3])))
+    assert np.max(np.abs(after[3] - rec[3])) <= 2e-6 * scale / h + 1e-6 * scale / h
+
+
 def test_surrogate_against_plain_trace(G, field):
     """What the learned trace gains (or loses) against the plain RK3 trace: node updates
     per second and the distance of each run's interface from a 4x finer-in-time RK3

@@ -400,3 +400,57 @@ def test_cross_cell_diagnostics():
     want = f(x, y)[0] - 0.3
     assert np.max(np.abs(hb - want)) < 1e-13 and np.max(np.abs(ha - want)) < 1e-13
     assert np.max(np.abs(hz - want)) > 1e-6
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_step_given_affine_map_exact(dim):
+    """A step fed a backward map instead of a trace (the form the learned flow map
+    uses): for linear phi = a.x + b and the affine map foot = A x + d, the interpolant
+    reproduces phi exactly (Sec. 2.3), so phi+ = a.(A x + d) + b and psi+ = A^T a
+    (eq. superconsistency with J = A).  A is not symmetric, so a transposed J fails."""
+    n = (9, 8, 7)[:dim]
+    g = oracle.grid(n)
+    rng = np.random.default_rng(21)
+    a = rng.uniform(-1, 1, dim)
+    b = 0.3
+    A = np.eye(dim) + 0.1 * rng.uniform(-1, 1, (dim, dim))
+    d = rng.uniform(-0.01, 0.01, dim)
+    axes = [np.linspace(0, 1, m) for m in n]
+    X = np.stack(np.meshgrid(*axes[::-1], indexing="ij")[::-1])  # X[c] = coordinate c, x fastest
+    st = np.zeros((oracle.nplanes(dim),) + tuple(n[::-1]))
+    st[0] = np.tensordot(a, X, 1) + b
+    for c in range(dim):
+        st[1 + c] = a[c]
+    # a contraction about the centre keeps every foot inside the box
+    A = 0.7 * A
+    foot = np.tensordot(A, X - 0.5, 1) + (0.5 + d).reshape((dim,) + (1,) * dim)
+    assert foot.min() >= 0 and foot.max() <= 1
+    disp = foot - X
+    jac = np.broadcast_to(A.reshape((dim, dim) + (1,) * dim), (dim, dim) + tuple(n[::-1]))
+    out = oracle.step_given(g, st, disp, jac)
+    assert np.allclose(out[0], np.tensordot(a, foot, 1) + b, atol=1e-13)
+    for c in range(dim):
+        assert np.allclose(out[1 + c], (A.T @ a)[c], atol=1e-13)
+    assert np.allclose(out[1 + dim:], 0.0, atol=1e-9)  # mixed derivatives of linear data
+
+
+@pytest.mark.parametrize("dim,kind,kw", [(2, "vortex2d", dict(T=8.0)), (3, "deform3d", dict(T=3.0))])
+def test_step_given_with_traced_map_equals_step(dim, kind, kw):
+    """Fed the RK3 trace's own feet and Jacobians, the given-map step is the RK3 step."""
+    n = (13, 11, 9)[:dim]
+    g = oracle.grid(n)
+    st = inputs.sphere_sdf(n, center=(0.45, 0.5, 0.5), r=0.25) if dim == 3 else \
+        inputs.circle_sdf(n, center=(0.45, 0.55), r=0.25)
+    st = oracle.recon_cross(g, np.asarray(st, dtype=np.float64))
+    vel = oracle.velocity(kind, **kw)
+    t, dt = 0.3, 0.07
+    ref = oracle.step(g, vel, st, t, dt)
+    disp = np.zeros((dim,) + tuple(n[::-1]))
+    jac = np.zeros((dim, dim) + tuple(n[::-1]))
+    for idx in np.ndindex(*n[::-1]):
+        x = np.array([idx[::-1][c] / (n[c] - 1) for c in range(dim)])
+        foot, J = oracle.trace("rk3", vel, dim, x, t, dt)
+        disp[(slice(None),) + idx] = foot - x
+        jac[(slice(None), slice(None)) + idx] = J
+    out = oracle.step_given(g, st, disp, jac)
+    assert np.max(np.abs(out - ref)) < 1e-12
