@@ -533,6 +533,7 @@ def run_ours(args, wl):
     st_host = initial_state(wl)
     stream = torch.cuda.Stream()
     g = gals.Grid(n, layout=args.layout, stream=stream, cross=args.cross)
+    g.set_time_loop(args.loop)
     g.set_state(st_host, t0=0.0, recon=True)
 
     # warm-up (also captures the CUDA graph for K steps)
@@ -548,9 +549,11 @@ def run_ours(args, wl):
     ms = replicas.max_over_ranks(R, float(np.median(wins)), device="cuda")
     value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
 
-    # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels)
+    # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels);
+    # with --loop persistent a 2D FULL approach-A call is one launch (CFL 1 here)
     cell = args.cross == "cell"
     launches_per_step = 2 if (args.layout == "full" and dim == 3 and not cell) else 1
+    persistent = args.loop == "persistent" and dim == 2 and args.layout == "full" and not cell
     # approach B stores no mixed derivatives: the step moves phi and psi only
     bpn = bytes_per_node(dim, "compact" if cell else args.layout)
     default_path = args.trace == "rk3" and not cell
@@ -595,7 +598,7 @@ def run_ours(args, wl):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "layout": args.layout, "nodes": nodes,
                        "trace": args.trace, "cross": args.cross,
-                       "dt": dt, "bytes_per_node_update": bpn,
+                       "dt": dt, "bytes_per_node_update": bpn, "time_loop": args.loop,
                        "l2": f"inputs larger than L2 ({nodes * nplanes * 4 / 1e6:.0f} MB state per buffer)",
                        "timing": "median of repeated K-step windows (CUDA events on the grid "
                                  "stream, barrier + synchronize around each)",
@@ -605,11 +608,13 @@ def run_ours(args, wl):
                          "frac": achieved / peak,
                          "traffic": recorded_traffic(args.workload, args.layout) if default_path else None,
                          "peak_source": peak_kind,
-                         "kernel": f"gals step ({launches_per_step} launch(es) per step)"},
+                         "kernel": ("k_step2d_run (persistent: the K steps in one launch)" if persistent
+                                    else f"gals step ({launches_per_step} launch(es) per step)")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes,
                     "api": "gals_step_host" if banded else "gals_set_state + gals_step + gals_read_state"},
-            "gpu_launches": args.steps * launches_per_step + 2,  # + stage-coefficient table, clock
+            # + stage-coefficient table and clock advance kernels
+            "gpu_launches": (1 if persistent else args.steps * launches_per_step) + 2,
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -865,6 +870,8 @@ def main():
     ap.add_argument("--cross", default="central", choices=["central", "cell"],
                     help="single-grid workloads: mixed derivatives by approach A or B (Sec. 2.3)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--loop", default="launches", choices=["launches", "persistent"],
+                    help="single-grid workloads: time loop of the K-step call")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="default workload: skip the 512^3 3D line timed in the same run")

@@ -152,11 +152,30 @@ gals_status gals_set_state(gals_grid *grid, const float *const *fields, int nfie
  * superconsistent form of Sec. 5.1; M = P A of Sec. 5.2).  Step s uses the velocity at
  * the stage times of the step from t0 + s*dt.  Feet outside the box are clamped into it
  * (outflow or tangential boundaries need no data, Sec. 4.1).  nsteps > 1 is replayed
- * from a cached CUDA graph.  Asynchronous on the grid stream.
+ * from a cached CUDA graph (of one launch per step, or of one persistent launch, see
+ * gals_set_time_loop).  Asynchronous on the grid stream.
  * Errors: GALS_ERR_ARG (dt <= 0 or non-finite, nsteps < 0, bad velocity descriptor),
  * GALS_ERR_STATE (no state loaded), GALS_ERR_UNSUPPORTED (velocity kind not available in
  * this dimension), GALS_ERR_CUDA (launch failure). */
 gals_status gals_step(gals_grid *grid, const gals_velocity *vel, double dt, int nsteps);
+
+/* Time loop of gals_step calls with nsteps > 1.
+ *   LAUNCHES    one launch per step, replayed from a cached CUDA graph (the default).
+ *   PERSISTENT  where it applies (2D, FULL layout, approach A, the Euler / RK3 / Heun-psi
+ *               traces, and feet at most 126 columns and 12 rows from their node by the
+ *               velocity's speed bound) the whole call is one persistent launch: blocks take
+ *               (step, tile) items in order and a tile of step s starts once the 3 x 3 tiles
+ *               around it have finished step s - 1, so no step waits for the last tiles of
+ *               the previous one to drain; elsewhere one launch per step.  On a GB300 it
+ *               runs 8 % slower than LAUNCHES on the 4096^2 single vortex (0.148 against
+ *               0.137 ms per step): the per-tile flag fence and acquire cost more than the
+ *               drained tails it saves.
+ * Both give the same results bit for bit. */
+enum { GALS_LOOP_LAUNCHES = 0, GALS_LOOP_PERSISTENT = 1 };
+
+/* Select the time loop of later gals_step calls (default LAUNCHES); synchronises when it
+ * changes.  Errors: GALS_ERR_ARG. */
+gals_status gals_set_time_loop(gals_grid *grid, int mode);
 
 /* Copy the current state out (all planes, or the first nfields).  In the COMPACT layout
  * the mixed derivatives are rebuilt first.  Synchronises the grid stream.
@@ -239,6 +258,17 @@ const char *gals_last_error(const gals_grid *grid);
 
 /* Library version string. */
 const char *gals_version(void);
+
+/* Test hook for the failure path of the bounded device waits (not in the paper).  In the
+ * checked build (libgals_checked.so) it sets, for grids created afterwards, how many
+ * polls a step kernel's wait for its staged tile makes before the wait counts as lost
+ * (default 2^24), and with skip_copy != 0 the tile copy that completes the wait is not
+ * issued, so every wait runs out: the kernel records GALS_ERR_TIMEOUT's code in the
+ * grid's error word and returns, and the next synchronising call on that grid returns
+ * GALS_ERR_TIMEOUT.  gals_checked_wait_test(1u << 24, 0) restores the defaults.  The
+ * normal build returns GALS_ERR_UNSUPPORTED and changes nothing.
+ * Errors: GALS_ERR_ARG (polls < 1), GALS_ERR_UNSUPPORTED. */
+gals_status gals_checked_wait_test(uint32_t polls, int skip_copy);
 
 /* ------------------------------------------------------------------------------------
  * Batched 2D mode: many independent problems of uneven size advanced together, one

@@ -71,6 +71,8 @@ struct gals_grid {
     cudaStream_t hs_in = nullptr, hs_out = nullptr;
     cudaEvent_t hs_enter = nullptr, hs_in_ev[kHostBands] = {}, hs_step_ev[kHostBands] = {};
     std::vector<GraphEntry> graphs;
+    int loop = GALS_LOOP_LAUNCHES; // time loop of multi-step calls (gals_set_time_loop)
+    int *run_ctl = nullptr;       // persistent 2D loop: ticket, abort word, per-tile flags
     char err[256] = "";
 };
 
@@ -86,8 +88,17 @@ gals_status fail(gals_grid *g, gals_status st, const char *fmt, ...)
     return st;
 }
 
+#ifdef GALS_CHECKED
+// test hook of the checked build (gals_checked_wait_test), read by gals_create_grid
+uint32_t g_test_wait_polls = 1u << 24;
+int g_test_skip_copy = 0;
+#endif
+
 gals_status cuda_fail(gals_grid *g, cudaError_t e, const char *what)
 {
+    // the runtime keeps a failed call's error as the thread's last error; a non-sticky one
+    // (a failed allocation) would otherwise fail the next launch check of any handle
+    cudaGetLastError();
     return fail(g, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
                 cudaGetErrorString(e));
 }
@@ -141,13 +152,51 @@ StepLaunch step_launch(gals_grid *g, const VelParams &vp, int trace, double dt, 
     return a;
 }
 
+// Whether a call of nsteps steps runs as one persistent launch (launch_step2d_run): 2D,
+// FULL layout, approach A, an analytic trace, and feet (at most reach[a] cells from their
+// node along axis a) within the launch's dependency radius.
+bool use_run(const gals_grid *g, int trace, int nsteps, const double reach[2])
+{
+    return g->loop == GALS_LOOP_PERSISTENT && g->dim == 2 && nsteps >= 2 && g->layout == GALS_LAYOUT_FULL &&
+           g->cross == GALS_CROSS_CENTRAL && trace != GALS_TRACE_SURROGATE &&
+           reach[0] <= run2d_max_cells(0) && reach[1] <= run2d_max_cells(1);
+}
+
 cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt, int nsteps,
                         bool first_explicit, const mlp::InferParams *ip = nullptr,
-                        const mlp::Check *chk = nullptr)
+                        const mlp::Check *chk = nullptr, bool run = false)
 {
     int cur = g->cur;
     cudaError_t ce = launch_coef_table(g->coef, vp, g->t_dev, dt, nsteps, g->stream);
     if (ce != cudaSuccess) return ce;
+    if (run) {
+        // persistent launches of fewer than 2^31 - 2^20 work items (tiles x steps) each:
+        // the ticket counter also counts one final draw per block
+        const int tiles = run2d_tiles(g->geom);
+        const int chunk = (int)((INT32_MAX - (1 << 20)) / tiles);
+        for (int s0 = 0; s0 < nsteps; s0 += chunk) {
+            StepLaunch a = step_launch(g, vp, trace, dt, 0, cur, first_explicit);
+            RunLaunch r{};
+            r.buf[0] = g->buf[0];
+            r.buf[1] = g->buf[1];
+            r.cur = cur;
+            r.geom = g->geom;
+            r.vp = vp;
+            r.coef = g->coef + s0;
+            r.dt = dt;
+            r.trace = a.trace;
+            r.tmap[0] = &g->maps[0][1];
+            r.tmap[1] = &g->maps[1][1];
+            r.err = g->err_dev;
+            r.ctl = g->run_ctl;
+            r.nsteps = nsteps - s0 < chunk ? nsteps - s0 : chunk;
+            if ((ce = cudaMemsetAsync(g->run_ctl, 0, sizeof(int) * (4 + (size_t)tiles), g->stream)) != cudaSuccess ||
+                (ce = launch_step2d_run(r, g->stream)) != cudaSuccess)
+                return ce;
+            if (r.nsteps & 1) cur ^= 1;
+        }
+        return launch_advance_time(g->t_dev, nsteps, dt, g->stream);
+    }
     for (int s = 0; s < nsteps; ++s) {
         StepLaunch a = step_launch(g, vp, trace, dt, s, cur, first_explicit);
         if (trace == GALS_TRACE_SURROGATE) {
@@ -176,6 +225,36 @@ bool same_key(const GraphEntry &e, int nsteps, int cur, int fe, int trace, int l
 }  // namespace
 
 extern "C" {
+
+gals_status gals_set_time_loop(gals_grid *g, int mode)
+{
+    if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (mode != GALS_LOOP_LAUNCHES && mode != GALS_LOOP_PERSISTENT) return fail(g, GALS_ERR_ARG, "unknown time loop");
+    if (mode != g->loop) {
+        // cached graphs hold the other loop
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "sync");
+        for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+        g->graphs.clear();
+        g->loop = mode;
+    }
+    return GALS_OK;
+}
+
+gals_status gals_checked_wait_test(uint32_t polls, int skip_copy)
+{
+#ifdef GALS_CHECKED
+    if (polls < 1) return fail(nullptr, GALS_ERR_ARG, "polls must be >= 1");
+    g_test_wait_polls = polls;
+    g_test_skip_copy = skip_copy != 0;
+    return GALS_OK;
+#else
+    (void)polls;
+    (void)skip_copy;
+    return fail(nullptr, GALS_ERR_UNSUPPORTED,
+                "the wait test hook exists only in the checked build (libgals_checked.so)");
+#endif
+}
 
 const char *gals_version(void) { return "gals-gb300 0.1 (sm_103a)"; }
 
@@ -224,6 +303,10 @@ gals_status gals_create_grid(const gals_grid_desc *d, gals_grid **out)
     G.ih0 = (float)(1.0 / g->h[0]); G.ih1 = (float)(1.0 / g->h[1]); G.ih2 = (float)(1.0 / g->h[2]);
     G.i2h0 = (float)(0.5 / g->h[0]); G.i2h1 = (float)(0.5 / g->h[1]); G.i2h2 = (float)(0.5 / g->h[2]);
     G.lo0 = (float)g->lo[0]; G.lo1 = (float)g->lo[1]; G.lo2 = (float)g->lo[2];
+#ifdef GALS_CHECKED
+    G.wait_polls = g_test_wait_polls;
+    G.skip_copy = g_test_skip_copy;
+#endif
 
     cudaError_t e;
     if (d->cuda_stream) {
@@ -313,6 +396,7 @@ gals_status gals_destroy_grid(gals_grid *g)
     cudaFree(g->coef);
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
+    cudaFree(g->run_ctl);
     for (cudaStream_t hs : {g->hs_in, g->hs_out})
         if (hs) {
             cudaStreamSynchronize(hs);
@@ -420,6 +504,14 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
             return cuda_fail(g, e, "cudaMalloc(coefficient table)");
         g->coef_cap = cap;
     }
+    const double vmax = speed_bound(v, g->dim, g->lo, g->hi);
+    const double reach[2] = {dt * vmax / g->h[0], dt * vmax / g->h[1]};
+    const bool run = use_run(g, v->trace, nsteps, reach);
+    if (run && !g->run_ctl) {
+        if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
+        if ((e = cudaMalloc(&g->run_ctl, sizeof(int) * (4 + (size_t)run2d_tiles(g->geom)))) != cudaSuccess)
+            return cuda_fail(g, e, "cudaMalloc(time-loop control)");
+    }
     if (nsteps == 1) {
         if ((e = issue_steps(g, vp, v->trace, dt, 1, fe, &ip, &chk)) != cudaSuccess)
             return cuda_fail(g, e, "step launch");
@@ -431,7 +523,7 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
             cudaGraph_t graph;
             if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(g, e, "begin capture");
-            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe, &ip, &chk);
+            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe, &ip, &chk, run);
             e = cudaStreamEndCapture(g->stream, &graph);
             if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
             if (e != cudaSuccess) return cuda_fail(g, e, "end capture");

@@ -74,6 +74,9 @@ gals_status bfail(gals_batch *b, gals_status st, const char *fmt, ...)
 
 gals_status bcuda(gals_batch *b, cudaError_t e, const char *what)
 {
+    // the runtime keeps a failed call's error as the thread's last error; a non-sticky one
+    // (a failed allocation) would otherwise fail the next launch check of any handle
+    cudaGetLastError();
     return bfail(b, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
                  cudaGetErrorString(e));
 }
@@ -268,7 +271,11 @@ gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch
         return bail(e, "cudaMalloc(descriptors)");
     if ((e = cudaMemsetAsync(b->err_dev, 0, sizeof(int), b->stream)) != cudaSuccess) return bail(e, "cudaMemset");
 #ifdef GALS_CHECKED
-    for (BatchProb &P : b->probs) P.g.chk = b->err_dev;  // checked build: bounds errors
+    for (BatchProb &P : b->probs) {  // memset above cleared the geometry's defaults
+        P.g.chk = b->err_dev;            // checked build: bounds errors
+        P.g.wait_polls = Geom{}.wait_polls;
+        P.g.skip_copy = 0;
+    }
 #endif
     if ((e = cudaMemcpyAsync(b->probs_dev, b->probs.data(), sizeof(BatchProb) * count, cudaMemcpyHostToDevice,
                              b->stream)) != cudaSuccess)

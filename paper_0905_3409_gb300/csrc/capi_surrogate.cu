@@ -59,6 +59,9 @@ gals_status sfail(gals_surrogate *s, gals_status st, const char *fmt, ...)
 
 gals_status scuda(gals_surrogate *s, cudaError_t e, const char *what)
 {
+    // the runtime keeps a failed call's error as the thread's last error; a non-sticky one
+    // (a failed allocation) would otherwise fail the next launch check of any handle
+    cudaGetLastError();
     return sfail(s, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
                  cudaGetErrorString(e));
 }

@@ -66,6 +66,10 @@ struct Geom {
     float lo0, lo1, lo2;
 #ifdef GALS_CHECKED
     int *chk = nullptr;         // device error word of the checked build (see GALS_CHK)
+    // test hook of the checked build (gals_checked_wait_test): polls of a staged-tile
+    // wait before it counts as lost, and whether the copy that completes it is issued
+    uint32_t wait_polls = 1u << 24;
+    int skip_copy = 0;
 #endif
 };
 

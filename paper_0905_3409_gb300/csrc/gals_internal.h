@@ -28,6 +28,27 @@ struct StepLaunch {
     int band_lo, band_hi;
 };
 
+// Persistent 2D time loop (FULL layout, approach A): nsteps steps from buffer cur in one
+// launch; ctl holds 4 + run2d_tiles(geom) ints, zero before the launch (ticket counter,
+// abort word, per-tile step flags).  Feet must stay within run2d_max_cells(axis) cells of
+// their node.
+struct RunLaunch {
+    float *buf[2];
+    int cur;
+    Geom geom;
+    VelParams vp;
+    const StageCoef *coef;     // stage coefficients of the launch's steps
+    double dt;
+    int trace;                 // TR_EULER / TR_RK3 / TR_HEUN
+    const CUtensorMap *tmap[2]; // FULL-box TMA maps of buf[0], buf[1]
+    int *err;
+    int *ctl;
+    int nsteps;
+};
+int run2d_tiles(const Geom &g);
+int run2d_max_cells(int axis);
+cudaError_t launch_step2d_run(const RunLaunch &a, cudaStream_t s);
+
 // Granularity of StepLaunch bands: the 2D tile height, the 3D tile depth.
 int band_unit(int dim);
 

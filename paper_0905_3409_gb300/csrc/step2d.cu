@@ -37,6 +37,104 @@ k_step2d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
                                     (blockIdx.y + yt0) * TY, tile, sm, 0);
 }
 
+// ---------------------------------------------------------------- persistent time loop
+//
+// All steps of one call in one launch (FULL layout, approach A).  Work items are
+// (step, tile) pairs numbered step-major; a block takes the next item from a ticket counter
+// and, for step s > 0, first waits until the 3 x 3 tiles around its own have finished step
+// s - 1 (a per-tile flag holds the number of steps a tile has finished in this launch).
+// With feet at most TY - 2 rows and TX - 2 columns from their node those are every tile
+// whose output the step reads (the staged tile, global gathers) and every tile that still
+// reads the region the step overwrites (the ping-pong buffer of step s - 1's input), so
+// the order of the per-step launches is kept where it matters and nowhere else: blocks
+// move on to the next step while the last tiles of the previous one drain.  Items are
+// handed out in increasing order and a block waits only for smaller items, so the launch
+// finishes whatever the number of resident blocks.  Every wait is bounded; a wait that
+// runs out sets the launch's abort word and the error word, and every block returns.
+constexpr int kErrRunTimeout = 3;
+constexpr uint32_t kSpinLimit = 1u << 22;  // flag polls (~0.2 us each) before giving up
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int TR, int VK>
+__global__ void __launch_bounds__(TX, GALS_2D_MINB)
+k_step2d_run(float *__restrict__ buf0, float *__restrict__ buf1, Geom g, VelParams vp,
+             const StageCoef *__restrict__ coef, float dt, const __grid_constant__ CUtensorMap tmap0,
+             const __grid_constant__ CUtensorMap tmap1, int *__restrict__ err, int *__restrict__ ctl,
+             int nsteps, int cur)
+{
+    extern __shared__ __align__(128) float tile[];
+    __shared__ __align__(16) Smem<TY, 1> sm;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0) mbar_init(&sm.bar, 1);
+    const int ntx = (g.n0 + TX - 1) / TX, nty = (g.n1 + TY - 1) / TY, ntiles = ntx * nty;
+    const int total = ntiles * nsteps;  // < 2^31 - 2^20 (host)
+    int *ticket = ctl, *abort_word = ctl + 1, *flags = ctl + 4;
+    // thread 0 draws the block's next item one item ahead, so that the draw's latency
+    // hides behind a tile (a block waits only for items smaller than the one it holds,
+    // and it finishes its current item before the drawn one: no cycle of waits)
+    int next = 0;
+    if (tid == 0) next = atomicAdd(ticket, 1);
+    uint32_t parity = 0;
+    for (;;) {
+        if (tid == 0) s_item = next;
+        __syncthreads();
+        const int t = s_item;
+        if (t >= total) break;
+        const int st = t / ntiles, tt = t - st * ntiles, bx = tt % ntx, by = tt / ntx;
+        // wait until the 3 x 3 tiles around this one have finished step st - 1: one flag
+        // per thread of the first warp, in parallel
+        bool lost = false;
+        if (st > 0 && tid < 9) {
+            const int nx = bx + tid % 3 - 1, ny = by + tid / 3 - 1;
+            if (nx >= 0 && nx < ntx && ny >= 0 && ny < nty) {
+                const int *f = flags + ny * ntx + nx;
+                for (uint32_t it = 0; ld_acquire_gpu(f) < st; ++it) {
+                    if (it >= kSpinLimit || *(volatile int *)abort_word) {
+                        lost = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+        }
+        if (__syncthreads_or(lost)) {
+            if (tid == 0 && atomicExch(abort_word, 1) == 0) atomicExch(err, kErrRunTimeout);
+            break;
+        }
+        const int b = (cur + st) & 1;
+        if (tid == 0) {
+            // the tile copy is an async-proxy read of data other blocks wrote through the
+            // generic proxy (acquired above, ordered before this thread by the barrier)
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        const bool ok = tile_step2d<TY, TR, VK, CROSS_PLANE, 1, HYT, true>(
+            b ? buf1 : buf0, b ? buf0 : buf1, g, vp, coef + st, dt, b ? &tmap1 : &tmap0, err,
+            bx * TX, by * TY, tile, sm, parity, [&]() { next = atomicAdd(ticket, 1); });
+        parity ^= 1u;
+        if (!ok) {  // block-uniform: the staged copy was lost
+            if (tid == 0) atomicExch(abort_word, 1);
+            break;
+        }
+        __syncthreads();  // every store of the tile is issued before thread 0 publishes it
+        if (tid == 0) {
+            __threadfence();
+            st_release_gpu(flags + tt, st + 1);
+        }
+    }
+}
+
 // phi_xy = d/dx psi_y at every node (approach A with one-sided ends); used after
 // set_state and for the COMPACT layout's read-out.  Blocks of 32 x 8 nodes; the grid's
 // y dimension is capped at 65535 and its blocks stride over the rows beyond.
@@ -107,7 +205,54 @@ cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s)
     }
 }
 
+template <int TR, int VK>
+cudaError_t launch_run_t(const RunLaunch &a, cudaStream_t s)
+{
+    auto kern = k_step2d_run<TR, VK>;
+    static int blocks_per_sm = 0;  // per instantiation
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, GT::bytes(4));
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TX, GT::bytes(4));
+        if (e != cudaSuccess) return e;
+        blocks_per_sm = nb > 0 ? nb : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t items = (int64_t)run2d_tiles(a.geom) * a.nsteps;
+    const int64_t want = (int64_t)blocks_per_sm * (sms > 0 ? sms : 1);
+    const int grid = (int)(want < items ? want : items);
+    kern<<<grid, TX, GT::bytes(4), s>>>(a.buf[0], a.buf[1], a.geom, a.vp, a.coef, (float)a.dt, *a.tmap[0],
+                                        *a.tmap[1], a.err, a.ctl, a.nsteps, a.cur);
+    return cudaGetLastError();
+}
+
+template <int VK>
+cudaError_t launch_run_tr(const RunLaunch &a, cudaStream_t s)
+{
+    if (a.trace == TR_HEUN) return launch_run_t<TR_HEUN, VK>(a, s);
+    return a.trace == TR_EULER ? launch_run_t<TR_EULER, VK>(a, s) : launch_run_t<TR_RK3, VK>(a, s);
+}
+
 int tile_rows2d() { return TY; }
+
+int run2d_tiles(const Geom &g) { return ((g.n0 + TX - 1) / TX) * ((g.n1 + TY - 1) / TY); }
+
+int run2d_max_cells(int axis) { return axis == 0 ? TX - 2 : TY - 2; }
+
+cudaError_t launch_step2d_run(const RunLaunch &a, cudaStream_t s)
+{
+    switch (a.vp.kind) {
+    case VK_CONST: return launch_run_tr<VK_CONST>(a, s);
+    case VK_ROTATION: return launch_run_tr<VK_ROTATION>(a, s);
+    case VK_VORTEX2D: return launch_run_tr<VK_VORTEX2D>(a, s);
+    case VK_PSEUDO1D: return launch_run_tr<VK_PSEUDO1D>(a, s);
+    case VK_FOURIER2D: return launch_run_tr<VK_FOURIER2D>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 int band_unit(int dim) { return dim == 2 ? TY : 4; }
 

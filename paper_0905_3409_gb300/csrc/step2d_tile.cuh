@@ -167,10 +167,18 @@ __device__ __forceinline__ V2p stage1_pair(const VelParams &vp, const StageCoef 
     return vel2d_pair<VK>(vp, sc, scp, 0, x, y);
 }
 
+// A state value read from global memory: through the read-only path, or (COH) through
+// L2 only, for a persistent launch whose earlier steps wrote the buffer in the same launch.
+template <bool COH>
+__device__ __forceinline__ float ld_state(const float *p)
+{
+    return COH ? __ldcg(p) : __ldg(p);
+}
+
 // The 4 corners x 4 data of the cell (k, l) for one node, from the staged tile when the
 // cell (and, for COMPACT, its psi_y window k-1..k+2) lies inside it, else from global
 // memory (feet farther than the halo: CFL well above 1).
-template <int TY, int CR, int HYV = HY>
+template <int TY, int CR, int HYV = HY, bool COH = false>
 __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const Geom &g,
                                             const float *__restrict__ tile, int x0, int y0, int k,
                                             int l, float c[4][4])
@@ -218,14 +226,14 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
 #pragma unroll
         for (int A = 0; A < 2; ++A) {
             const int v = A + 2 * B;
-            c[v][0] = __ldg(Pphi + r + A);
-            c[v][1] = __ldg(Ppx + r + A);
-            c[v][2] = __ldg(Ppy + r + A);
-            if (CR == CROSS_PLANE) c[v][3] = __ldg(in + 3 * g.plane + r + A);
+            c[v][0] = ld_state<COH>(Pphi + r + A);
+            c[v][1] = ld_state<COH>(Ppx + r + A);
+            c[v][2] = ld_state<COH>(Ppy + r + A);
+            if (CR == CROSS_PLANE) c[v][3] = ld_state<COH>(in + 3 * g.plane + r + A);
         }
         if (CR == CROSS_RECON) {
-            const float w[4] = {__ldg(Ppy + r - (k > 0 ? 1 : 0)), c[2 * B][2], c[2 * B + 1][2],
-                                __ldg(Ppy + r + (k + 2 < g.n0 ? 2 : 1))};
+            const float w[4] = {ld_state<COH>(Ppy + r - (k > 0 ? 1 : 0)), c[2 * B][2], c[2 * B + 1][2],
+                                ld_state<COH>(Ppy + r + (k + 2 < g.n0 ? 2 : 1))};
             c[2 * B][3] = cross_from_window<0>(w, k, g.n0, g.i2h0);
             c[2 * B + 1][3] = cross_from_window<1>(w, k + 1, g.n0, g.i2h0);
         }
@@ -235,7 +243,7 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
 
 // Update of two nodes (i0, j0) and (i1, j1): phi+, psi_x+, psi_y+ per lane; the staged
 // tile has HYV halo rows.
-template <int TY, int TR, int VK, int CR, int HYV = HY>
+template <int TY, int TR, int VK, int CR, int HYV = HY, bool COH = false>
 __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const Geom &g,
                                             const float *__restrict__ tile, int x0, int y0,
                                             const VelParams &vp, const StageCoef &sc,
@@ -267,8 +275,8 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
     locate_pair(j0, j1, mul2(dy, bc(g.ih1)), g.n1, l0, l1, eta);
 
     float c0[4][4], c1[4][4];
-    gather_lane<TY, CR, HYV>(in, g, tile, x0, y0, k0, l0, c0);
-    gather_lane<TY, CR, HYV>(in, g, tile, x0, y0, k1, l1, c1);
+    gather_lane<TY, CR, HYV, COH>(in, g, tile, x0, y0, k0, l0, c0);
+    gather_lane<TY, CR, HYV, COH>(in, g, tile, x0, y0, k1, l1, c1);
     F2 c[4][4];
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -294,16 +302,21 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
 
 // One tile step: origin (x0, y0).  `tile` is the dynamic shared buffer for the staged
 // input, `sm` the static part; the barrier sm.bar must be initialised (count 1) and
-// `parity` is the phase this tile's copy completes.  Returns false (after recording
+// `parity` is the phase this tile's copy completes.  COH: global-memory gathers go
+// through L2 (see ld_state).  after_issue() runs on thread 0 right after it issued the copy.  Returns false (after recording
 // kErrTmaTimeout) if the staged copy did not arrive within the wait limit.
 // Must be called by all TX threads of the block.
-template <int TY, int TR, int VK, int CR, int WC, int HYV = HY>
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <int TY, int TR, int VK, int CR, int WC, int HYV = HY, bool COH = false, class Hook = NoHook>
 __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float *__restrict__ out,
                                             const Geom &g, const VelParams &vp,
                                             const StageCoef *__restrict__ coef, float dt,
                                             const CUtensorMap *tmap, int *__restrict__ err,
                                             int x0, int y0, float *tile, Smem<TY, WC> &sm,
-                                            uint32_t parity)
+                                            uint32_t parity, Hook after_issue = Hook())
 {
     auto &psy = sm.psy;
     auto &scp_s = sm.scp;
@@ -311,9 +324,16 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
     constexpr int NP = CR == CROSS_PLANE ? 4 : 3;
 
     // stage the input tile (all planes, halo HX x HY) with one TMA copy
+#ifdef GALS_CHECKED
+    const uint32_t polls = g.wait_polls;
+    if (tid == 0 && !g.skip_copy) {  // test hook: a copy never issued, a wait that runs out
+#else
+    constexpr uint32_t polls = kWaitLimit;
     if (tid == 0) {
+#endif
         mbar_arrive_expect_tx(&sm.bar, Geo<TY, HYV>::bytes(NP));
         tma_load_3d(tile, tmap, x0 - HX, y0 - HYV, 0, &sm.bar);
+        after_issue();  // thread 0's own work while the copy is in flight
     }
     const StageCoef &sc = *coef;
     if (VK == VK_FOURIER2D) {
@@ -351,10 +371,10 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
     if (VK == VK_FOURIER2D) fcol = fourier_col(xs);
 
     // bounded wait for the tile; a block-uniform verdict so no thread is left at a barrier
-    if (!mbar_wait_block(&sm.bar, parity)) {
+    if (!mbar_wait_block(&sm.bar, parity, polls)) {
         if (tid == 0) {
             atomicExch(err, kErrTmaTimeout);
-            mbar_wait_bounded(&sm.bar, parity);  // let a late copy land before giving up
+            mbar_wait_bounded(&sm.bar, parity, polls);  // let a late copy land before giving up
         }
         return false;
     }
@@ -367,10 +387,10 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             F2 phi, px, py;
             if (VK == VK_FOURIER2D && TR != TR_GIVEN) {
                 const V2p a1 = fourier_stage1_pair<TY>(fcol, sm.fsum, r);
-                node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
+                node2d_pair<TY, TR, VK, CR, HYV, COH>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
                                             cx, ry, phi, px, py, &a1);
             } else {
-                node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
+                node2d_pair<TY, TR, VK, CR, HYV, COH>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
                                             cx, ry, phi, px, py);
             }
             const int o = GALS_CHK(g, j0 * g.pitch + i, plane_extent(g));
@@ -403,7 +423,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             const VCol cxh = (VK == VK_VORTEX2D) ? vortex_col(xh.x, sc.mod[0]) : VCol{0.f, 0.f, 0.f, 0.f, 0.f};
             const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
             F2 phi, px, py;
-            node2d_pair<TY, TR, VK, CR, HYV>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
+            node2d_pair<TY, TR, VK, CR, HYV, COH>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
                                     ry, phi, px, py);
             psy[WC ? r : 0][GALS_CHK(g, ih - x0 + 2, TX + 3)] = py.x;
             if (r + 1 < rows) psy[WC ? r + 1 : 0][GALS_CHK(g, ih - x0 + 2, TX + 3)] = py.y;

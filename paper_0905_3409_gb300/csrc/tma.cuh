@@ -45,10 +45,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of the barrier; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Bounded wait for phase `parity` of the barrier; false if `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint32_t limit = kWaitLimit)
 {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -56,9 +57,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // Wait of a whole block for a staged copy: every thread polls (bounded), then the block
 // takes one verdict at a barrier (false: the wait ran out for some thread), so that no
 // thread is left behind at a later barrier.  Must be reached by every thread.
-__device__ __forceinline__ bool mbar_wait_block(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_block(uint64_t *bar, uint32_t parity,
+                                                uint32_t limit = kWaitLimit)
 {
-    const bool ok = mbar_wait_bounded(bar, parity);
+    const bool ok = mbar_wait_bounded(bar, parity, limit);
     return !__syncthreads_or(!ok);
 }
 

@@ -36,6 +36,7 @@ EXPORTS = [
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
     "gals_batch_set_tuning", "gals_batch_get_tuning", "gals_batch_nodes", "gals_batch_last_error",
     "gals_diagnostics_noalloc", "gals_noalloc_max_nodes", "gals_noalloc_last_error",
+    "gals_checked_wait_test", "gals_set_time_loop",
     "gals_surrogate_create", "gals_surrogate_destroy", "gals_surrogate_train",
     "gals_surrogate_set_check", "gals_surrogate_stats", "gals_surrogate_get_params",
     "gals_surrogate_set_params", "gals_surrogate_bind", "gals_surrogate_forward",
@@ -151,6 +152,7 @@ def lib() -> ctypes.CDLL:
             vp, ctypes.POINTER(DiagOut)]
         L.gals_noalloc_max_nodes.restype = ctypes.c_int64
         L.gals_noalloc_last_error.restype = ctypes.c_char_p
+        L.gals_checked_wait_test.argtypes = [ctypes.c_uint32, ctypes.c_int]
         fp = ctypes.POINTER(ctypes.c_float)
         L.gals_surrogate_create.argtypes = [ctypes.POINTER(MlpDesc), ctypes.POINTER(vp)]
         L.gals_surrogate_destroy.argtypes = [vp]
@@ -290,6 +292,11 @@ class Grid:
     def step(self, vel: Velocity, dt: float, nsteps: int = 1):
         d = vel.desc()
         _check(lib().gals_step(self._h, ctypes.byref(d), float(dt), int(nsteps)), self._h)
+
+    def set_time_loop(self, mode: str):
+        """"launches" (one launch per step, the default) or "persistent" (one launch per
+        multi-step call where it applies)."""
+        _check(lib().gals_set_time_loop(self._h, {"launches": 0, "persistent": 1}[mode]), self._h)
 
     def read_state(self, out=None, nfields=None):
         """Copy the state into ``out`` (numpy or torch CUDA tensor of self.shape);

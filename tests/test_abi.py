@@ -81,3 +81,14 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(gals.GridDesc) == 4 + 12 + 24 + 24 + 4 + 4 + 8  # layout, cross_scheme: 80
     assert gals.GridDesc.cross_scheme.offset == 68 and gals.GridDesc.cuda_stream.offset == 72
     assert ctypes.sizeof(gals.DiagOut) == 11 * 8
+
+
+def test_wait_test_hook_only_in_checked_build(built):
+    """gals_checked_wait_test changes nothing in the normal build (UNSUPPORTED); the checked
+    build validates its argument (no CUDA call either way)."""
+    from paper_0905_3409_gb300 import build
+    assert built.gals_checked_wait_test(ctypes.c_uint32(2048), 1) == gals.ERR_UNSUPPORTED
+    L = ctypes.CDLL(build.build_checked())
+    L.gals_checked_wait_test.argtypes = [ctypes.c_uint32, ctypes.c_int]
+    assert L.gals_checked_wait_test(0, 1) == gals.ERR_ARG
+    assert L.gals_checked_wait_test(1 << 24, 0) == gals.OK

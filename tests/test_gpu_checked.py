@@ -1,8 +1,8 @@
 """The checked build (libgals_checked.so, compiled with -DGALS_CHECKED: the step kernels
 test every data-dependent index against its buffer and report a violation through the
 grid's error word, which fails the call with the source line) on small odd grids,
-tile-edge sizes, large CFL, both layouts, approach B, the batched mode and the banded
-host step.  No index may leave its buffer, and the results must be those of the normal
+tile-edge sizes, large CFL, both layouts, approach B, the persistent 2D time loop, the
+batched mode and the banded host step.  No index may leave its buffer, and the results must be those of the normal
 build bit for bit.  The checked library runs in a child process (GALS_LIB), the normal one
 in the test's own."""
 import math
@@ -47,6 +47,15 @@ def run_cases():
         g.step(G.Velocity(**vel), cells / (max(n) - 1), 3)
         out[f"case{c}"] = g.read_state()
         out[f"diag{c}"] = np.array([v for v in g.diagnostics(q=2).values()], dtype=np.float64)
+        g.close()
+    # the persistent 2D time loop (feet 2.5 cells away: gathers from global memory too)
+    for c, (n, vel, cells) in enumerate((((130, 67), ROT, 2.5), ((300, 45), dict(kind="vortex2d", T=8.0), 0.9))):
+        st = inputs.circle_sdf(n, center=(0.45, 0.55), r=0.3).astype(np.float32)
+        g = G.Grid(n)
+        g.set_time_loop("persistent")
+        g.set_state(st, t0=0.2, recon=True)
+        g.step(G.Velocity(**vel), cells / (max(n) - 1), 4)
+        out[f"persist{c}"] = g.read_state()
         g.close()
     sizes = [(4, 4), (5, 4), (130, 17), (6, 129)]
     probs = inputs.batch_problems(len(sizes), seed=3)
