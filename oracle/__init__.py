@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 # enums of gals_oracle.h
-VEL_CONST, VEL_ROTATION, VEL_VORTEX2D, VEL_DEFORM3D, VEL_PSEUDO1D, VEL_FOURIER2D = range(6)
+VEL_CONST, VEL_ROTATION, VEL_VORTEX2D, VEL_DEFORM3D, VEL_PSEUDO1D, VEL_FOURIER2D, VEL_WAVES2D = range(7)
 TRACE_EULER, TRACE_RK3, TRACE_HEUN_PSI = 0, 1, 2
 CROSS_CENTRAL, CROSS_ZERO, CROSS_CELL = 0, 1, 2
 _CROSS_NAMES = {"central": CROSS_CENTRAL, "zero": CROSS_ZERO, "cell": CROSS_CELL}
@@ -33,6 +33,7 @@ _CROSS_NAMES = {"central": CROSS_CENTRAL, "zero": CROSS_ZERO, "cell": CROSS_CELL
 _VEL_NAMES = {
     "const": VEL_CONST, "rotation": VEL_ROTATION, "vortex2d": VEL_VORTEX2D,
     "deform3d": VEL_DEFORM3D, "pseudo1d": VEL_PSEUDO1D, "fourier2d": VEL_FOURIER2D,
+    "waves2d": VEL_WAVES2D,
 }
 _TRACE_NAMES = {"euler": TRACE_EULER, "rk3": TRACE_RK3, "heun_psi": TRACE_HEUN_PSI}
 
@@ -148,7 +149,8 @@ def _f64(a) -> np.ndarray:
 def velocity(kind: str, T: float = 1.0, omega: float = 0.0, center=(0.5, 0.5, 0.5),
              c=(0.0, 0.0, 0.0), modes=None):
     """Build the oracle's velocity descriptor.  ``modes``: (m,5) array of
-    (a, k, l, n, chi) for the Fourier stream-function field."""
+    (a, k, l, n, chi) for the Fourier stream-function field, (m,6) array of
+    (a, kx, ky, phase, n, chi) for the plane-wave field."""
     v = _Velocity()
     v.kind = _VEL_NAMES[kind]
     v.T = float(T)
@@ -157,7 +159,7 @@ def velocity(kind: str, T: float = 1.0, omega: float = 0.0, center=(0.5, 0.5, 0.
         v.center[i] = float(center[i]) if i < len(center) else 0.0
         v.c[i] = float(c[i]) if i < len(c) else 0.0
     if modes is not None:
-        m = _f64(modes).reshape(-1, 5)
+        m = _f64(modes).reshape(-1, 6 if kind == "waves2d" else 5)
         v._modes_keep = m  # keep alive
         v.nmodes = m.shape[0]
         v.modes = _dp(m)

@@ -34,7 +34,9 @@ enum {
     ORC_VEL_VORTEX2D = 2,  /* single vortex, stream fn (1/pi)cos(pi t/T)sin^2(pi x)sin^2(pi y) (Sec. 6.1.2) */
     ORC_VEL_DEFORM3D = 3,  /* LeVeque 3D deformation modulated by cos(pi t/T) (Sec. 6.2.4) */
     ORC_VEL_PSEUDO1D = 4,  /* eq. velocity_1 (Sec. 6.1.1) */
-    ORC_VEL_FOURIER2D = 5  /* stream fn sum_m a_m sin(k pi x) sin(l pi y) cos(2 pi n t + chi) */
+    ORC_VEL_FOURIER2D = 5, /* stream fn sum_m a_m sin(k pi x) sin(l pi y) cos(2 pi n t + chi) */
+    ORC_VEL_WAVES2D = 6    /* stream fn sum_m a_m sin(kx x + ky y + phase) cos(2 pi n t + chi)
+                              (plane waves of any wave vector; not in the paper) */
 };
 
 /* EULER, RK3: superconsistent traces (Sec. 5.1 examples); psi+ = J^T grad H(foot).
@@ -60,8 +62,9 @@ typedef struct {
     double omega;      /* ROTATION angular speed */
     double center[3];  /* ROTATION center */
     double c[3];       /* CONST velocity */
-    int nmodes;        /* FOURIER2D: number of modes */
-    const double *modes; /* FOURIER2D: 5 doubles per mode: a, k, l, n, chi */
+    int nmodes;        /* FOURIER2D, WAVES2D: number of modes */
+    const double *modes; /* FOURIER2D: 5 doubles per mode: a, k, l, n, chi;
+                            WAVES2D: 6 doubles per mode: a, kx, ky, phase, n, chi */
 } orc_velocity;
 
 typedef struct {

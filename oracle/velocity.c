@@ -16,6 +16,8 @@
  *   PSEUDO1D   v = (1/sqrt(2+pi)) exp((sqrt2 x + sqrtpi y)/sqrt(2+pi)) (sqrt2, sqrtpi)
  *              (eq. velocity_1, Sec. 6.1.1).
  *   FOURIER2D  v = (-dPsi/dy, dPsi/dx), Psi = sum_m a_m sin(k_m pi x) sin(l_m pi y) cos(2 pi n_m t + chi_m).
+ *   WAVES2D    v = (-dPsi/dy, dPsi/dx), Psi = sum_m a_m sin(kx_m x + ky_m y + phase_m) cos(2 pi n_m t + chi_m)
+ *              (a costly field: no separable form, one sine and cosine per mode).
  * Each field is written out from its definition; derivatives by hand.
  */
 #include <math.h>
@@ -114,6 +116,24 @@ void orc_vel_eval(const orc_velocity *vel, int dim, const double *x, double t,
             Dv[1] += a * skx * l * pi * l * pi * sly * c;
             Dv[3] += -a * k * pi * k * pi * skx * sly * c;
             Dv[4] += a * k * pi * ckx * l * pi * cly * c;
+        }
+        break;
+    }
+    case ORC_VEL_WAVES2D: {
+        for (int m = 0; m < vel->nmodes; ++m) {
+            const double *md = vel->modes + 6 * m;
+            double a = md[0], kx = md[1], ky = md[2], phase = md[3], n = md[4], chi = md[5];
+            double c = a * cos(2.0 * pi * n * t + chi);
+            double th = kx * x[0] + ky * x[1] + phase;
+            double s = sin(th), co = cos(th);
+            /* Psi_m = c sin(th): Psi_x = c kx cos(th), Psi_y = c ky cos(th);
+             * u = -Psi_y, v = Psi_x */
+            v[0] += -c * ky * co;
+            v[1] += c * kx * co;
+            Dv[0] += c * ky * kx * s;     /* du/dx */
+            Dv[1] += c * ky * ky * s;     /* du/dy */
+            Dv[3] += -c * kx * kx * s;    /* dv/dx */
+            Dv[4] += -c * kx * ky * s;    /* dv/dy */
         }
         break;
     }

@@ -358,6 +358,58 @@ def fourier_speed_bound(modes):
                      np.sum(np.abs(m[:, 0]) * m[:, 1]) * math.pi))
 
 
+def wave_modes(nmodes, seed=DEFAULT_SEED, amp=0.4, kmin=math.pi, kmax=4 * math.pi, periodic=True):
+    """Random plane-wave stream-function modes (a, kx, ky, phase, n, chi) per row for the
+    WAVES2D field Psi = sum a sin(kx x + ky y + phase) cos(2 pi n t + chi): wave vectors of
+    uniform direction and length uniform in [kmin, kmax], a ~ N(0, (amp / sqrt(nmodes))^2)
+    (the field's typical speed does not grow with the number of modes), phase uniform in
+    [0, 2 pi); time-periodic fields (period 1) have n in {1, 2} and chi uniform in
+    [0, 2 pi), steady ones n = chi = 0."""
+    rng = np.random.default_rng(seed)
+    a = rng.normal(0.0, amp / math.sqrt(nmodes), nmodes)
+    ang = rng.uniform(0.0, 2 * math.pi, nmodes)
+    kk = rng.uniform(kmin, kmax, nmodes)
+    phase = rng.uniform(0.0, 2 * math.pi, nmodes)
+    if periodic:
+        nn = rng.integers(1, 3, nmodes).astype(np.float64)
+        chi = rng.uniform(0.0, 2 * math.pi, nmodes)
+    else:
+        nn = np.zeros(nmodes)
+        chi = np.zeros(nmodes)
+    return np.stack([a, kk * np.cos(ang), kk * np.sin(ang), phase, nn, chi], axis=1)
+
+
+def wave_velocity(modes, x, y, t):
+    """(u, v) of the WAVES2D field at points (x, y) (arrays) and time t, in FP64 (numpy);
+    for sampling the field's speed, not a reference of the method."""
+    m = np.asarray(modes)
+    u = np.zeros(np.broadcast(x, y).shape)
+    v = np.zeros_like(u)
+    for a, kx, ky, ph, n, chi in m:
+        c = a * math.cos(2 * math.pi * n * t + chi) * np.cos(kx * x + ky * y + ph)
+        u -= ky * c
+        v += kx * c
+    return u, v
+
+
+def wave_speed_sampled(modes, samples=129, times=12):
+    """max over [0,1]^2 and one period of max(|u|, |v|), sampled on a samples^2 grid at
+    `times` phases, times 1.1 (the CFL rule of the Fourier configurations, with margin)."""
+    xs = np.linspace(0.0, 1.0, samples)
+    X, Y = np.meshgrid(xs, xs)
+    best = 0.0
+    for k in range(times):
+        u, v = wave_velocity(modes, X, Y, k / times)
+        best = max(best, float(np.max(np.abs(u))), float(np.max(np.abs(v))))
+    return 1.1 * best
+
+
+def wave_speed_bound(modes):
+    """Upper bound of max |u|, |v| of the WAVES2D field: sum |a| |k| (the library's)."""
+    m = np.asarray(modes)
+    return float(np.sum(np.abs(m[:, 0]) * np.hypot(m[:, 1], m[:, 2])))
+
+
 def steps_for(T, h, vmax, cfl=1.0):
     """nsteps = ceil(T / dt_cfl) with dt_cfl = cfl h / vmax; dt = T / nsteps."""
     nsteps = int(math.ceil(T / (cfl * h / vmax) - 1e-9))

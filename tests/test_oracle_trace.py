@@ -14,6 +14,7 @@ FIELDS = [
     ("pseudo1d", 2, {}),
     ("rotation", 2, dict(omega=2 * math.pi, center=(0.5, 0.5))),
     ("fourier2d", 2, dict(modes=inputs.fourier_modes(16, seed=7, periodic=True))),
+    ("waves2d", 2, dict(modes=inputs.wave_modes(32, seed=7))),
 ]
 
 
@@ -218,3 +219,48 @@ def test_fourier_single_mode_hand_values():
     p2 = math.pi ** 2
     assert v == pytest.approx([-math.pi, math.pi / 2], abs=1e-14)
     assert np.allclose(D, [[-p2, 2 * p2], [-p2 / 2, p2]], atol=1e-13)
+
+
+def test_waves_single_mode_hand_values():
+    """One plane wave Psi = sin(pi x + 2 pi y) cos(2 pi t) (a = 1, k = (pi, 2 pi)):
+    at (1/4, 1/8) the phase is pi/2, so u = v = 0 and du/dx = kx ky = 2 pi^2,
+    du/dy = ky^2 = 4 pi^2, dv/dx = -kx^2 = -pi^2, dv/dy = -2 pi^2, times cos(2 pi t);
+    at the origin the phase is 0: u = -ky = -2 pi, v = kx = pi, Dv = 0."""
+    vel = oracle.velocity("waves2d", modes=np.array([[1.0, math.pi, 2 * math.pi, 0.0, 1.0, 0.0]]))
+    p2 = math.pi ** 2
+    v, D = oracle.vel_eval(vel, 2, (0.25, 0.125), 0.125)
+    c = math.cos(math.pi / 4)
+    assert v == pytest.approx([0.0, 0.0], abs=1e-14)
+    assert np.allclose(D, c * np.array([[2 * p2, 4 * p2], [-p2, -2 * p2]]), atol=1e-12)
+    v, D = oracle.vel_eval(vel, 2, (0.0, 0.0), 0.0)
+    assert v == pytest.approx([-2 * math.pi, math.pi], abs=1e-14)
+    assert np.allclose(D, 0.0, atol=1e-12)
+
+
+def test_waves_velocity_is_rotated_stream_function_gradient():
+    """v = (-dPsi/dy, dPsi/dx) by central differences of Psi written out again, and Dv
+    against central differences of v, for 64 random plane waves; trace(Dv) = 0."""
+    modes = inputs.wave_modes(64, seed=12)
+    vel = oracle.velocity("waves2d", modes=modes)
+
+    def psi(x, y, t):
+        return sum(a * math.sin(kx * x + ky * y + ph) * math.cos(2 * math.pi * n * t + chi)
+                   for a, kx, ky, ph, n, chi in modes)
+
+    rng = np.random.default_rng(13)
+    eps = 1e-6
+    for _ in range(8):
+        x, y, t = rng.uniform(0, 1), rng.uniform(0, 1), rng.uniform(0, 1)
+        v, D = oracle.vel_eval(vel, 2, (x, y), t)
+        u_ref = -(psi(x, y + eps, t) - psi(x, y - eps, t)) / (2 * eps)
+        w_ref = (psi(x + eps, y, t) - psi(x - eps, y, t)) / (2 * eps)
+        assert v == pytest.approx([u_ref, w_ref], abs=2e-7)
+        for j in range(2):
+            e = np.zeros(2)
+            e[j] = eps
+            vp, _ = oracle.vel_eval(vel, 2, np.array([x, y]) + e, t)
+            vm, _ = oracle.vel_eval(vel, 2, np.array([x, y]) - e, t)
+            assert np.allclose(D[:, j], (vp - vm) / (2 * eps), atol=1e-6 * max(1, np.abs(D).max()))
+        assert abs(np.trace(D)) < 1e-12
+    # the sampled speed used for the CFL rule lies below the library's analytic bound
+    assert inputs.wave_speed_sampled(modes) <= 1.1 * inputs.wave_speed_bound(modes)
