@@ -68,6 +68,15 @@ WORKLOADS = {
                                "3-128x4-6, BF16 tensor cores, trained on 32-sub-step RK4 "
                                "targets) with per-tile RK3 residual check and fallback, against "
                                "the plain RK3 trace"),
+    "waves2048": dict(dim=2, n=(2048, 2048), vel=dict(kind="waves2d"), vmax=None,
+                      surrogate=True, nwaves=256,
+                      desc="2D GALS 2048x2048 nodes on [0,1]^2, FP32, costly velocity: time-periodic "
+                           "(period 1) stream function of 256 plane waves of random direction, "
+                           "|k| in [pi, 4 pi] (seed 9053409; one sine and cosine per wave per "
+                           "evaluation), circle SDF r=0.15 at (0.5,0.75), CFL 1; learned flow-map "
+                           "trace (MLP 3-128x4-6, BF16 tensor cores, trained on 32-sub-step RK4 "
+                           "targets) with per-tile RK3 residual check, against the plain RK3 trace "
+                           "at the same step and at larger steps (equal interface error)"),
     # a smaller case of the same 3D kernel, for profiler captures (state still > L2)
     "deform256": dict(dim=3, n=(256, 256, 256), vel=dict(kind="deform3d", T=3.0), vmax=2.0,
                       desc="3D GALS 256^3 nodes on [0,1]^3, FP32, LeVeque deformation T=3, "
@@ -83,16 +92,21 @@ def bytes_per_node(dim, layout):
 
 def wl_modes(wl):
     from paper_0905_3409_gb300 import inputs
+    if wl.get("nwaves"):
+        return inputs.wave_modes(wl["nwaves"], seed=inputs.DEFAULT_SEED)
     if not wl.get("nmodes"):
         return None
     return inputs.fourier_modes(wl["nmodes"], seed=inputs.DEFAULT_SEED, periodic=True)
 
 
 def wl_dt(wl):
-    """CFL 1: dt = h / max|v_i| (the Fourier field's analytic speed bound)."""
+    """CFL 1: dt = h / max|v_i| (the Fourier field's analytic speed bound; for the plane
+    waves, whose sum bound is far above the field's speed, the sampled speed times 1.1)."""
     from paper_0905_3409_gb300 import inputs
     h = 1.0 / (wl["n"][0] - 1)
     modes = wl_modes(wl)
+    if wl.get("nwaves"):
+        return h / inputs.wave_speed_sampled(modes)
     return h / (inputs.fourier_speed_bound(modes) if modes is not None else wl["vmax"])
 
 
@@ -723,12 +737,13 @@ def run_surrogate(args, wl):
     h = 1.0 / (n[0] - 1)
     dt = wl_dt(wl)
     modes = wl_modes(wl)
+    kind = wl["vel"]["kind"]
     stream = torch.cuda.Stream()
-    plain = gals.Velocity("fourier2d", modes=modes, trace="rk3")
+    plain = gals.Velocity(kind, modes=modes, trace="rk3")
     S = gals.Surrogate(seed=7, stream=stream)
     rep = S.train(plain, dt, h, steps=args.train_steps, batch=16384, lr=2e-3, lr_min=1e-5)
     S.set_check(tol_x=args.tol, tol_J=args.tol, samples=4)
-    learned = gals.Velocity("fourier2d", modes=modes, trace="surrogate", surrogate=S)
+    learned = gals.Velocity(kind, modes=modes, trace="surrogate", surrogate=S)
     st_host = initial_state(wl)
     K = args.steps
 
@@ -758,6 +773,12 @@ def run_surrogate(args, wl):
     ms_sur = timed(learned, g_sur)
     clocks = sampler.stop() if rank == 0 else None
     tiles, falls = S.stats()
+    # the network alone: no residual check (and so no fallback)
+    S.set_check(tol_x=args.tol, tol_J=args.tol, samples=0)
+    g_nc = gals.Grid(n, stream=stream)
+    ms_nocheck = timed(learned, g_nc)
+    e_nocheck = None
+    S.set_check(tol_x=args.tol, tol_J=args.tol, samples=4)
     value = replicas.throughput(nodes * K, world, ms_sur * 1e-3)
     value_plain = replicas.throughput(nodes * K, world, ms_plain * 1e-3)
 
@@ -776,6 +797,48 @@ def run_surrogate(args, wl):
                      "emax_psi": d["emax_psi"],
                      "area_change": g.diagnostics(q=4)["measure_negative"] - area0}
     e_p, e_s = acc["plain_rk3"]["interface_symdiff"], acc["surrogate"]["interface_symdiff"]
+    e_nocheck = g_nc.diagnostics(q=4, reference=g_fine)["measure_symdiff"]
+    g_nc.close()
+
+    # equal interface error: the plain trace with steps c times longer reaches the same end
+    # time in K / c steps; each run's interface error against the same reference and its
+    # time to the end time (CUDA events; graph captured by an untimed first run)
+    sweep = []
+    for c in (1, 2, 4, 5, 8, 10, 16, 20, 25, 32, 40, 50, 64, 100):
+        if K % c or K // c < 4:
+            continue
+        gc = g_plain if c == 1 else gals.Grid(n, stream=stream)
+        if c == 1:
+            ms_c = ms_plain
+        else:
+            gc.set_state(st_host, t0=0.0, recon=True)
+            gc.step(plain, c * dt, K // c)
+            gc.set_state(st_host, t0=0.0, recon=True)
+            gc.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gc.step(plain, c * dt, K // c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_c = e0.elapsed_time(e1)
+        err = gc.diagnostics(q=4, reference=g_fine)["measure_symdiff"]
+        sweep.append({"step_multiple": c, "steps": K // c, "ms_to_end_time": ms_c,
+                      "interface_symdiff": err})
+        if c != 1:
+            gc.close()
+    # the cheapest plain run whose error is at most 1.1 x the learned run's
+    ok = [r for r in sweep if r["interface_symdiff"] <= 1.1 * e_s]
+    best = min(ok, key=lambda r: r["ms_to_end_time"]) if ok else None
+    equal_error = {
+        "learned": {"ms_to_end_time": ms_sur, "interface_symdiff": e_s},
+        "learned_without_check": {"ms_to_end_time": ms_nocheck, "interface_symdiff": e_nocheck},
+        "plain_rk3_sweep": sweep,
+        "plain_at_most_learned_error": best,
+        "time_ratio_learned_over_plain": (ms_sur / best["ms_to_end_time"]) if best else None,
+        "winner": (("plain_rk3" if best["ms_to_end_time"] < ms_sur else "learned") if best
+                   else "learned (no plain run reached its error)"),
+    }
 
     # roofline of the tensor-core MLP: one evaluation per node, device buffers > L2
     X = (torch.rand(nodes, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(1)) * 2 - 1)
@@ -834,7 +897,8 @@ def run_surrogate(args, wl):
                        "speedup_vs_plain": value / value_plain,
                        "fallback_tiles": falls, "tiles": tiles,
                        "accuracy_vs_rk3_dt_over_4": acc,
-                       "interface_error_ratio": (e_s / e_p) if e_p > 0 else None},
+                       "interface_error_ratio": (e_s / e_p) if e_p > 0 else None,
+                       "equal_error": equal_error},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                          "kernel": f"k_infer_points (the MLP tile code of the learned trace) over "

@@ -93,7 +93,11 @@ enum {
     GALS_VEL_DEFORM3D = 3,  /* u = 2 sin^2(pi x) sin(2 pi y) sin(2 pi z), v = -sin(2 pi x) sin^2(pi y) sin(2 pi z),
                                w = -sin(2 pi x) sin(2 pi y) sin^2(pi z), all times cos(pi t/T) (Sec. 6.2.4) */
     GALS_VEL_PSEUDO1D = 4,  /* eq. velocity_1 (Sec. 6.1.1) */
-    GALS_VEL_FOURIER2D = 5  /* v = (-Psi_y, Psi_x), Psi = sum_m a_m sin(k_m pi x) sin(l_m pi y) cos(2 pi n_m t + chi_m) */
+    GALS_VEL_FOURIER2D = 5, /* v = (-Psi_y, Psi_x), Psi = sum_m a_m sin(k_m pi x) sin(l_m pi y) cos(2 pi n_m t + chi_m) */
+    GALS_VEL_WAVES2D = 6    /* v = (-Psi_y, Psi_x), Psi = sum_m a_m sin(kx_m x + ky_m y + phase_m) cos(2 pi n_m t + chi_m):
+                               plane waves of any wave vector, a field with no separable form
+                               whose every evaluation costs one sine and cosine per mode (a costly
+                               velocity; not in the paper) */
 };
 
 /* Backward trace of one step. */
@@ -109,6 +113,7 @@ enum {
 typedef struct gals_surrogate gals_surrogate;   /* opaque, owned by the library */
 
 #define GALS_MAX_MODES 64
+#define GALS_MAX_WAVES 1024
 
 typedef struct {
     int kind;               /* GALS_VEL_* */
@@ -117,9 +122,10 @@ typedef struct {
     double omega;           /* ROTATION angular speed (counter-clockwise) */
     double center[3];       /* ROTATION center */
     double c[3];            /* CONST velocity */
-    int nmodes;             /* FOURIER2D: number of modes, 1..GALS_MAX_MODES */
+    int nmodes;             /* FOURIER2D: number of modes, 1..GALS_MAX_MODES; WAVES2D: 1..GALS_MAX_WAVES */
     const double *modes;    /* FOURIER2D: host array of nmodes rows (a, k, l, n, chi); k, l integers
-                               in 1..4, n >= 0.  Copied during the call. */
+                               in 1..4, n >= 0.  WAVES2D: rows (a, kx, ky, phase, n, chi), n >= 0.
+                               Copied during the call. */
     const gals_surrogate *surrogate;  /* GALS_TRACE_SURROGATE: the trained flow map (else NULL) */
 } gals_velocity;
 

@@ -71,6 +71,9 @@ struct gals_grid {
     cudaStream_t hs_in = nullptr, hs_out = nullptr;
     cudaEvent_t hs_enter = nullptr, hs_in_ev[kHostBands] = {}, hs_step_ev[kHostBands] = {};
     std::vector<GraphEntry> graphs;
+    WaveStore waves;              // WAVES2D: device copy of the field's modes
+    float *wamp = nullptr;        // WAVES2D: amplitudes of a call's steps [step][stage][mode]
+    int64_t wamp_cap = 0;
     int loop = GALS_LOOP_LAUNCHES; // time loop of multi-step calls (gals_set_time_loop)
     int *run_ctl = nullptr;       // persistent 2D loop: ticket, abort word, per-tile flags
     char err[256] = "";
@@ -397,6 +400,8 @@ gals_status gals_destroy_grid(gals_grid *g)
     cudaFree(g->diag_dev);
     cudaFree(g->diag_partials);
     cudaFree(g->run_ctl);
+    cudaFree(g->wamp);
+    g->waves.release();
     for (cudaStream_t hs : {g->hs_in, g->hs_out})
         if (hs) {
             cudaStreamSynchronize(hs);
@@ -471,10 +476,30 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     mlp::Check chk{};
     const void *sur = nullptr;
     float sur_key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    cudaError_t e;
+    if (v->kind == GALS_VEL_WAVES2D && nsteps > 0) {
+        // the modes in device memory, and room for the call's amplitude table
+        bool changed = false;
+        if ((e = g->waves.upload(v, g->stream, &changed)) != cudaSuccess) return cuda_fail(g, e, "wave table");
+        const int64_t need = (int64_t)nsteps * 3 * v->nmodes;
+        if (need > g->wamp_cap) {
+            if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
+            for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);  // they use the old table
+            g->graphs.clear();
+            cudaFree(g->wamp);
+            g->wamp = nullptr;
+            g->wamp_cap = 0;
+            if ((e = cudaMalloc(&g->wamp, sizeof(float) * (size_t)need)) != cudaSuccess)
+                return cuda_fail(g, e, "cudaMalloc(wave amplitudes)");
+            g->wamp_cap = need;
+        }
+        g->waves.bind(vp);
+        vp.wamp = g->wamp;
+    }
     if (v->trace == GALS_TRACE_SURROGATE) {
         if (g->dim != 2) return fail(g, GALS_ERR_UNSUPPORTED, "the surrogate trace is 2D");
         char msg[200];
-        st = surrogate_for_step(v->surrogate, vp, dt, g->h[0], g->h[1], ip, chk, msg, sizeof(msg));
+        st = surrogate_for_step(v->surrogate, v, vp, dt, g->h[0], g->h[1], ip, chk, msg, sizeof(msg));
         if (st != GALS_OK) return fail(g, st, "%s", msg);
         chk.err = g->err_dev;
         sur = v->surrogate;
@@ -485,7 +510,6 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     }
     if (nsteps == 0) return GALS_OK;
     const bool fe = g->cross_explicit;
-    cudaError_t e;
     if (sur && !g->trace_buf) {
         if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
         if ((e = cudaMalloc(&g->trace_buf, sizeof(float) * 6 * (size_t)g->geom.plane)) != cudaSuccess)
@@ -632,6 +656,8 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
     if (st != GALS_OK) return st;
     if (v->trace == GALS_TRACE_SURROGATE)
         return fail(g, GALS_ERR_UNSUPPORTED, "gals_step_host does not take the surrogate trace");
+    if (v->kind == GALS_VEL_WAVES2D)
+        return fail(g, GALS_ERR_UNSUPPORTED, "gals_step_host does not take the WAVES2D field");
     cudaError_t e = cudaSuccess;
     if (!g->hs_in) {
         e = cudaStreamCreateWithFlags(&g->hs_in, cudaStreamNonBlocking);

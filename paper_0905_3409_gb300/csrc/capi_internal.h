@@ -3,6 +3,8 @@
 
 #include <stddef.h>
 
+#include <vector>
+
 #include "../../include/gals.h"
 #include "gals_internal.h"
 #include "mlp_internal.h"
@@ -34,9 +36,22 @@ double speed_bound(const gals_velocity *v, int dim, const double lo[3], const do
 // blocks along y and z in 3D (n[1], n[2] <= 262140).  Returns false with a message.
 bool grid_size_ok(int dim, const int n[3], char *msg, size_t len);
 
-// Whether surrogate `s` serves a step with these parameters; fills the kernel views.
-gals_status surrogate_for_step(const gals_surrogate *s, const VelParams &vp, double dt, double h0,
-                               double h1, mlp::InferParams &ip, mlp::Check &chk, char *msg,
-                               size_t len);
+// Device copy of a WAVES2D mode table (per grid or surrogate): upload() copies the modes
+// of v (validated by velparams_from) when they differ from the copy held, after the stream
+// has finished earlier work (changed: whether it did); bind() points vp at it.
+struct WaveStore {
+    void *dev = nullptr;   // 3 M float4, then 3 M doubles (the layout of WaveTab / waves_d)
+    int cap = 0, count = 0;
+    std::vector<double> host;  // the rows held (6 per mode)
+    cudaError_t upload(const gals_velocity *v, cudaStream_t s, bool *changed);
+    void bind(VelParams &vp) const;
+    void release();
+};
+
+// Whether surrogate `s` serves a step with these parameters (v: the step's velocity);
+// fills the kernel views.
+gals_status surrogate_for_step(const gals_surrogate *s, const gals_velocity *v, const VelParams &vp,
+                               double dt, double h0, double h1, mlp::InferParams &ip, mlp::Check &chk,
+                               char *msg, size_t len);
 
 }  // namespace gals

@@ -31,6 +31,7 @@ struct gals_surrogate {
     // bound field
     bool bound = false;
     VelParams vp{};
+    WaveStore waves;  // WAVES2D: the bound field's modes on the device
     double dt = 0.0, h = 0.0;
     // residual check
     float tol_x = 0.05f, tol_J = 0.05f;
@@ -74,7 +75,7 @@ gals_status check_err(gals_surrogate *s)
     if (e != cudaSuccess) return scuda(s, e, "error word");
     if (code == 0) return GALS_OK;
     cudaMemset(s->err_dev, 0, sizeof(int));
-    return sfail(s, GALS_ERR_TIMEOUT, "a bounded wait of the inference kernel ran out (code %d)", code);
+    return sfail(s, GALS_ERR_TIMEOUT, "a bounded wait of a tensor-core kernel ran out (code %d)", code);
 }
 
 uint64_t splitmix64_host(uint64_t &state)
@@ -98,7 +99,7 @@ cudaError_t ensure_scratch(gals_surrogate *s, int n)
     if ((e = cudaMalloc(&s->T, sizeof(float) * OUT * (size_t)n)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&s->G0, sizeof(float) * HID * (size_t)n)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&s->G1, sizeof(float) * HID * (size_t)n)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s->split, sizeof(float) * 64 * HID * HID)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s->split, sizeof(float) * kMaxSplit * HID * HID)) != cudaSuccess) return e;
     for (int l = 0; l < NLAYER; ++l) {
         if ((e = cudaMalloc(&s->Z[l], sizeof(float) * lout(l) * (size_t)n)) != cudaSuccess) return e;
         if (l > 0 && (e = cudaMalloc(&s->A[l], sizeof(float) * HID * (size_t)n)) != cudaSuccess) return e;
@@ -112,8 +113,14 @@ gals_status check_field(gals_surrogate *s, const gals_velocity *vel, VelParams &
     char msg[200];
     gals_status st = velparams_from(2, vel, vp, msg, sizeof(msg));
     if (st != GALS_OK) return sfail(s, st, "%s", msg);
-    if (vel->kind != GALS_VEL_FOURIER2D)
-        return sfail(s, GALS_ERR_UNSUPPORTED, "the surrogate is built for FOURIER2D fields");
+    if (vel->kind != GALS_VEL_FOURIER2D && vel->kind != GALS_VEL_WAVES2D)
+        return sfail(s, GALS_ERR_UNSUPPORTED, "the surrogate is built for FOURIER2D and WAVES2D fields");
+    if (vel->kind == GALS_VEL_WAVES2D) {
+        bool changed = false;
+        cudaError_t e = s->waves.upload(vel, s->stream, &changed);
+        if (e != cudaSuccess) return scuda(s, e, "wave table");
+        s->waves.bind(vp);
+    }
     return GALS_OK;
 }
 
@@ -127,9 +134,9 @@ cudaError_t repack(gals_surrogate *s)
 namespace gals {
 
 // Used by gals_step: is `s` usable for this call?  On success fills the kernel-side views.
-gals_status surrogate_for_step(const gals_surrogate *s, const VelParams &vp, double dt, double h0,
-                               double h1, mlp::InferParams &ip, mlp::Check &chk, char *msg,
-                               size_t len)
+gals_status surrogate_for_step(const gals_surrogate *s, const gals_velocity *v, const VelParams &vp,
+                               double dt, double h0, double h1, mlp::InferParams &ip, mlp::Check &chk,
+                               char *msg, size_t len)
 {
     if (!s) { snprintf(msg, len, "GALS_TRACE_SURROGATE needs vel->surrogate"); return GALS_ERR_ARG; }
     if (!s->bound) { snprintf(msg, len, "the surrogate is not trained or bound"); return GALS_ERR_STATE; }
@@ -139,7 +146,13 @@ gals_status surrogate_for_step(const gals_surrogate *s, const VelParams &vp, dou
         snprintf(msg, len, "the surrogate was trained for dt = %.17g, h = %.17g", s->dt, s->h);
         return GALS_ERR_ARG;
     }
-    if (vp.kind != s->vp.kind || vp.nmodes != s->vp.nmodes ||
+    if (vp.kind == VK_WAVES2D) {
+        if (s->vp.kind != VK_WAVES2D || v->nmodes != s->waves.count ||
+            std::memcmp(v->modes, s->waves.host.data(), sizeof(double) * 6 * (size_t)v->nmodes)) {
+            snprintf(msg, len, "the velocity differs from the one the surrogate was trained for");
+            return GALS_ERR_ARG;
+        }
+    } else if (vp.kind != s->vp.kind || vp.nmodes != s->vp.nmodes ||
         std::memcmp(vp.mode_a, s->vp.mode_a, sizeof(float) * vp.nmodes) ||
         std::memcmp(vp.mode_kl, s->vp.mode_kl, sizeof(int) * vp.nmodes) ||
         std::memcmp(vp.mode_n, s->vp.mode_n, sizeof(double) * vp.nmodes) ||
@@ -225,6 +238,7 @@ gals_status gals_surrogate_destroy(gals_surrogate *s)
 {
     if (!s) return GALS_OK;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    s->waves.release();
     cudaFree(s->params); cudaFree(s->grad); cudaFree(s->m); cudaFree(s->v);
     cudaFree(s->ip.w); cudaFree(s->scale_dev); cudaFree(s->one);
     cudaFree(s->loss_dev); cudaFree(s->counters); cudaFree(s->err_dev);
@@ -276,9 +290,9 @@ gals_status gals_surrogate_train(gals_surrogate *s, const gals_velocity *vel, do
     for (int it = 0; it < o->steps; ++it) {
         if ((e = launch_samples(vp, s->Xn, s->T, n, (float)dt, (float)h, o->substeps, o->seed, (uint64_t)it + 1,
                                 s->scale_dev, s->stream)) != cudaSuccess ||
-            (e = forward_train(s->params, s->Xn, n, s->Z, s->A, s->stream)) != cudaSuccess ||
+            (e = forward_train(s->params, s->Xn, n, s->Z, s->A, s->err_dev, s->stream)) != cudaSuccess ||
             (e = backward_train(s->params, s->Xn, s->T, n, s->Z, s->A, s->G0, s->G1, s->grad, s->loss_dev,
-                                s->one, s->split, s->stream)) != cudaSuccess)
+                                s->one, s->split, s->err_dev, s->stream)) != cudaSuccess)
             return scuda(s, e, "training step");
         const double frac = o->steps > 1 ? (double)it / (o->steps - 1) : 0.0;
         const double lr = o->lr_min + 0.5 * (o->lr - o->lr_min) * (1.0 + std::cos(M_PI * frac));
@@ -296,6 +310,7 @@ gals_status gals_surrogate_train(gals_surrogate *s, const gals_velocity *vel, do
     }
     if ((e = repack(s)) != cudaSuccess || (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
         return scuda(s, e, "pack");
+    if ((st = check_err(s)) != GALS_OK) return st;  // a training product that timed out
     s->vp = vp;
     s->dt = dt;
     s->h = h;
@@ -409,13 +424,15 @@ gals_status gals_surrogate_gradient(gals_surrogate *s, const float *inputs, cons
     double l = 0.0;
     if ((e = cudaMemcpyAsync(s->Xn, inputs, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(s->T, targets, sizeof(float) * OUT * n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
-        (e = forward_train(s->params, s->Xn, n, s->Z, s->A, s->stream)) != cudaSuccess ||
+        (e = forward_train(s->params, s->Xn, n, s->Z, s->A, s->err_dev, s->stream)) != cudaSuccess ||
         (e = backward_train(s->params, s->Xn, s->T, n, s->Z, s->A, s->G0, s->G1, s->grad, s->loss_dev, s->one,
-                            s->split, s->stream)) != cudaSuccess ||
+                            s->split, s->err_dev, s->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(grad, s->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(&l, s->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
         return scuda(s, e, "gradient");
+    gals_status st = check_err(s);
+    if (st != GALS_OK) return st;
     if (loss) *loss = l;
     return GALS_OK;
 }
@@ -442,7 +459,6 @@ gals_status gals_surrogate_targets(gals_surrogate *s, const gals_velocity *vel, 
 
 namespace {
 const char kMagic[8] = {'G', 'A', 'L', 'S', 'M', 'L', 'P', 1};
-constexpr int32_t kVersion = 1;
 
 struct FileCloser {
     FILE *f;
@@ -465,12 +481,18 @@ gals_status gals_surrogate_save(const gals_surrogate *s, const char *path)
     if (st != GALS_OK) return st;
     FileCloser fc{fopen(path, "wb")};
     if (!fc.f) return sfail(ms, GALS_ERR_ARG, "cannot write %s", path);
-    const int32_t hdr[3] = {kVersion, (int32_t)NPARAM, (int32_t)OUT};
+    // version 2 where the bound field is WAVES2D (its rows follow), else version 1
+    const int32_t version = s->bound && s->vp.kind == VK_WAVES2D ? 2 : 1;
+    const int32_t hdr[3] = {version, (int32_t)NPARAM, (int32_t)OUT};
     const float tols[2] = {s->tol_x, s->tol_J};
     const int32_t samples = s->samples, bound = s->bound ? 1 : 0;
     bool ok = put(fc.f, kMagic, 8) && put(fc.f, hdr, 3) && put(fc.f, p.data(), NPARAM) && put(fc.f, sc, OUT) &&
               put(fc.f, tols, 2) && put(fc.f, &samples, 1) && put(fc.f, &bound, 1);
-    if (ok && bound) {
+    if (ok && bound && s->vp.kind == VK_WAVES2D) {
+        const double dh[2] = {s->dt, s->h};
+        const int32_t kn[2] = {s->vp.kind, s->waves.count};
+        ok = put(fc.f, dh, 2) && put(fc.f, kn, 2) && put(fc.f, s->waves.host.data(), s->waves.host.size());
+    } else if (ok && bound) {
         const double dh[2] = {s->dt, s->h};
         const int32_t kn[2] = {s->vp.kind, s->vp.nmodes};
         const size_t m = (size_t)s->vp.nmodes;
@@ -490,7 +512,7 @@ gals_status gals_surrogate_load(gals_surrogate *s, const char *path)
     int32_t hdr[3];
     if (!get(fc.f, magic, 8) || std::memcmp(magic, kMagic, 8) != 0)
         return sfail(s, GALS_ERR_ARG, "%s is not a surrogate file", path);
-    if (!get(fc.f, hdr, 3) || hdr[0] != kVersion || hdr[1] != (int32_t)NPARAM || hdr[2] != (int32_t)OUT)
+    if (!get(fc.f, hdr, 3) || (hdr[0] != 1 && hdr[0] != 2) || hdr[1] != (int32_t)NPARAM || hdr[2] != (int32_t)OUT)
         return sfail(s, GALS_ERR_ARG, "%s: unsupported version or network shape", path);
     std::vector<float> p(NPARAM);
     float sc[OUT], tols[2];
@@ -500,7 +522,27 @@ gals_status gals_surrogate_load(gals_surrogate *s, const char *path)
         return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
     VelParams vp{};
     double dh[2] = {0.0, 0.0};
-    if (bound) {
+    std::vector<double> rows;
+    if (bound && hdr[0] == 2) {
+        int32_t kn[2];
+        if (!get(fc.f, dh, 2) || !get(fc.f, kn, 2)) return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
+        if (kn[0] != VK_WAVES2D || kn[1] < 1 || kn[1] > GALS_MAX_WAVES || !(dh[0] > 0.0) || !(dh[1] > 0.0))
+            return sfail(s, GALS_ERR_ARG, "%s: invalid bound field", path);
+        rows.resize((size_t)6 * kn[1]);
+        if (!get(fc.f, rows.data(), rows.size())) return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
+        gals_velocity wv{};
+        wv.kind = GALS_VEL_WAVES2D;
+        wv.trace = GALS_TRACE_RK3;
+        wv.nmodes = kn[1];
+        wv.modes = rows.data();
+        char msg[200];
+        if (velparams_from(2, &wv, vp, msg, sizeof(msg)) != GALS_OK)
+            return sfail(s, GALS_ERR_ARG, "%s: invalid bound field (%s)", path, msg);
+        bool changed = false;
+        cudaError_t e = s->waves.upload(&wv, s->stream, &changed);
+        if (e != cudaSuccess) return scuda(s, e, "wave table");
+        s->waves.bind(vp);
+    } else if (bound) {
         int32_t kn[2];
         if (!get(fc.f, dh, 2) || !get(fc.f, kn, 2)) return sfail(s, GALS_ERR_ARG, "%s is truncated", path);
         if (kn[0] != VK_FOURIER2D || kn[1] < 1 || kn[1] > kMaxModes || !(dh[0] > 0.0) || !(dh[1] > 0.0))

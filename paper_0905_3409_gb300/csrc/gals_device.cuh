@@ -30,7 +30,7 @@ constexpr int kMaxModes = 64;
 constexpr float kPi = 3.14159265358979323846f;
 
 enum VelKind { VK_CONST = 0, VK_ROTATION = 1, VK_VORTEX2D = 2, VK_DEFORM3D = 3,
-               VK_PSEUDO1D = 4, VK_FOURIER2D = 5 };
+               VK_PSEUDO1D = 4, VK_FOURIER2D = 5, VK_WAVES2D = 6 };
 // GIVEN: precomputed (surrogate); HEUN: RK3 foot, gradients by Heun's method along the
 // characteristic (Sec. 4, CIR form)
 enum TraceKind { TR_EULER = 0, TR_RK3 = 1, TR_GIVEN = 2, TR_HEUN = 3 };
@@ -53,7 +53,24 @@ struct VelParams {
     double mode_chi[kMaxModes]; // phase / (2 pi)
     const float *given;         // TR_GIVEN: planes dx, dy, J00, J01, J10, J11 of the step
     int64_t given_plane;        //   (grid pitch layout) and their plane stride
+    // WAVES2D: device table of nwaves modes (see WaveTab) and the call's amplitude table
+    // (per step, per stage, per mode: a cos(2 pi n t_s + chi)), owned by the grid / surrogate
+    int nwaves;
+    const float4 *waves;
+    const double *waves_d;
+    float *wamp;
 };
+
+// WAVES2D device table of M modes: geo[m] = (kx, ky, phase, kx ky), sq[m] = (kx^2, ky^2, 0, 0),
+// tim[m] = (a, n, chi / (2 pi), 0) in FP32 at waves[0..3M), and (a, n, chi / (2 pi)) per
+// mode in FP64 at waves_d[0..3M).
+struct WaveTab {
+    const float4 *geo, *sq, *tim;
+};
+__host__ __device__ __forceinline__ WaveTab wave_tab(const float4 *w, int M)
+{
+    return WaveTab{w, w + M, w + 2 * M};
+}
 
 // Grid geometry for kernels.
 struct Geom {
@@ -110,6 +127,7 @@ __device__ __forceinline__ int64_t plane_extent(const Geom &g)
 struct StageCoef {
     float mod[3];               // cos(pi t_s / T)
     float pad;
+    const float *wamp;          // WAVES2D: this step's amplitudes [stage][mode]
     float A[3][16];             // A_kl
     float Al[3][16];            // A_kl * l pi
     float All[3][16];           // A_kl * (l pi)^2
@@ -127,6 +145,7 @@ __device__ inline void stage_coef_one(const VelParams &vp, double t, double dt, 
         sc.mod[s] = (float)cospi(ph);
     }
     sc.pad = 0.f;
+    sc.wamp = nullptr;
     if (vp.kind != VK_FOURIER2D) return;
     for (int s = 0; s < 3; ++s) {
         const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
@@ -195,6 +214,25 @@ __device__ __forceinline__ V2 vel2d(const VelParams &vp, const StageCoef &sc, in
         r.u = e * vp.d0; r.v = e * vp.d1;
         r.d00 = e * vp.d0 * vp.d0; r.d01 = e * vp.d0 * vp.d1;
         r.d10 = r.d01; r.d11 = e * vp.d1 * vp.d1;
+    } else if (VK == VK_WAVES2D) {
+        // Psi = sum C_m sin(theta_m), theta_m = kx x + ky y + phase, C_m the stage amplitude
+        const WaveTab T = wave_tab(vp.waves, vp.nwaves);
+        const float *amp = sc.wamp + stage * vp.nwaves;
+        float u = 0.f, v = 0.f, d00 = 0.f, d01 = 0.f, d10 = 0.f;
+#pragma unroll 4
+        for (int m = 0; m < vp.nwaves; ++m) {
+            const float4 g = __ldg(T.geo + m), q = __ldg(T.sq + m);
+            const float C = __ldg(amp + m);
+            float sn, cs;
+            __sincosf(__fmaf_rn(g.x, x, __fmaf_rn(g.y, y, g.z)), &sn, &cs);
+            const float cc = C * cs, cn = C * sn;
+            u = __fmaf_rn(-g.y, cc, u);
+            v = __fmaf_rn(g.x, cc, v);
+            d00 = __fmaf_rn(g.w, cn, d00);
+            d01 = __fmaf_rn(q.y, cn, d01);
+            d10 = __fmaf_rn(-q.x, cn, d10);
+        }
+        r.u = u; r.v = v; r.d00 = d00; r.d01 = d01; r.d10 = d10; r.d11 = -d00;
     } else {  // VK_FOURIER2D
         float s[5], c[5], sy_[5], cy_[5];
         sincospi_f(x, &s[1], &c[1]);
@@ -234,10 +272,11 @@ __device__ __forceinline__ V2 vel2d(const VelParams &vp, const StageCoef &sc, in
 
 // 2D trace from node position (x, y) at t+dt back to t: displacement (dx, dy) of the
 // foot and J[i][j] = d foot_i / d x_j (row-major J00, J01, J10, J11).
-template <int TR, int VK>
-__device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, const StageCoef &sc,
-                                             float x, float y, float dt, float &dx, float &dy,
-                                             float J[4])
+// The superconsistent trace with the velocity evaluated by vel(stage, x, y) -> V2 (stage 1
+// at time t, stage 2 at t + dt/2); a = v(x, t+dt) and its Jacobian from the caller.
+template <int TR, class Vel>
+__device__ __forceinline__ void trace2d_eval(const V2 &a, Vel vel, float x, float y, float dt,
+                                             float &dx, float &dy, float J[4])
 {
     // a = v(x, t+dt) and its Jacobian, supplied by the caller
     if (TR == TR_EULER) {
@@ -249,7 +288,7 @@ __device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, c
     // stage 1: x1 = x - dt v(x, t+dt), J1 = I - dt Dv(x, t+dt)
     float J1_00 = 1.f - dt * a.d00, J1_01 = -dt * a.d01;
     float J1_10 = -dt * a.d10, J1_11 = 1.f - dt * a.d11;
-    V2 b = vel2d<VK>(vp, sc, 1, x - dt * a.u, y - dt * a.v);  // v(x1, t)
+    V2 b = vel(1, x - dt * a.u, y - dt * a.v);  // v(x1, t)
     // M = Dv(x1, t) J1
     float M00 = b.d00 * J1_00 + b.d01 * J1_10, M01 = b.d00 * J1_01 + b.d01 * J1_11;
     float M10 = b.d10 * J1_00 + b.d11 * J1_10, M11 = b.d10 * J1_01 + b.d11 * J1_11;
@@ -257,7 +296,7 @@ __device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, c
     float q = 0.25f * dt;
     float J2_00 = 1.f - q * (a.d00 + M00), J2_01 = -q * (a.d01 + M01);
     float J2_10 = -q * (a.d10 + M10), J2_11 = 1.f - q * (a.d11 + M11);
-    V2 c = vel2d<VK>(vp, sc, 2, x - q * (a.u + b.u), y - q * (a.v + b.v));  // v(x2, t+dt/2)
+    V2 c = vel(2, x - q * (a.u + b.u), y - q * (a.v + b.v));  // v(x2, t+dt/2)
     float N00 = c.d00 * J2_00 + c.d01 * J2_10, N01 = c.d00 * J2_01 + c.d01 * J2_11;
     float N10 = c.d10 * J2_00 + c.d11 * J2_10, N11 = c.d10 * J2_01 + c.d11 * J2_11;
     // stage 3: foot = x - dt (v1/6 + v2/6 + 2 v3/3), written as w3 + (w1 + w2 - 2 w3)/6,
@@ -271,11 +310,64 @@ __device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, c
     J[3] = fmaf(m6, a.d11 + M11, fmaf(m23, N11, 1.f));
 }
 
+
+template <int TR, int VK>
+__device__ __forceinline__ void trace2d_from(const V2 &a, const VelParams &vp, const StageCoef &sc,
+                                             float x, float y, float dt, float &dx, float &dy,
+                                             float J[4])
+{
+    trace2d_eval<TR>(a, [&](int stage, float px, float py) { return vel2d<VK>(vp, sc, stage, px, py); },
+                     x, y, dt, dx, dy, J);
+}
+
 template <int TR, int VK>
 __device__ __forceinline__ void trace2d(const VelParams &vp, const StageCoef &sc, float x,
                                         float y, float dt, float &dx, float &dy, float J[4])
 {
     trace2d_from<TR, VK>(vel2d<VK>(vp, sc, 0, x, y), vp, sc, x, y, dt, dx, dy, J);
+}
+
+// WAVES2D velocity at one point evaluated by a whole warp (every lane passes the same
+// point): lane l sums modes l, l + 32, ..., then a butterfly reduction gives every lane the
+// totals.  The sums run in another order than vel2d's, so the last bits may differ.
+__device__ __forceinline__ V2 vel2d_waves_warp(const VelParams &vp, const StageCoef &sc, int stage,
+                                               float x, float y)
+{
+    const WaveTab T = wave_tab(vp.waves, vp.nwaves);
+    const float *amp = sc.wamp + stage * vp.nwaves;
+    float u = 0.f, v = 0.f, d00 = 0.f, d01 = 0.f, d10 = 0.f;
+    for (int m = threadIdx.x & 31; m < vp.nwaves; m += 32) {
+        const float4 g = __ldg(T.geo + m), q = __ldg(T.sq + m);
+        const float C = __ldg(amp + m);
+        float sn, cs;
+        __sincosf(__fmaf_rn(g.x, x, __fmaf_rn(g.y, y, g.z)), &sn, &cs);
+        const float cc = C * cs, cn = C * sn;
+        u = __fmaf_rn(-g.y, cc, u);
+        v = __fmaf_rn(g.x, cc, v);
+        d00 = __fmaf_rn(g.w, cn, d00);
+        d01 = __fmaf_rn(q.y, cn, d01);
+        d10 = __fmaf_rn(-q.x, cn, d10);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        d00 += __shfl_xor_sync(0xffffffffu, d00, o);
+        d01 += __shfl_xor_sync(0xffffffffu, d01, o);
+        d10 += __shfl_xor_sync(0xffffffffu, d10, o);
+    }
+    V2 r;
+    r.u = u; r.v = v; r.d00 = d00; r.d01 = d01; r.d10 = d10; r.d11 = -d00;
+    return r;
+}
+
+// The RK3 trace of one point by a whole warp (WAVES2D; all lanes get the result).
+__device__ __forceinline__ void trace2d_waves_warp(const VelParams &vp, const StageCoef &sc, float x,
+                                                   float y, float dt, float &dx, float &dy, float J[4])
+{
+    trace2d_eval<TR_RK3>(vel2d_waves_warp(vp, sc, 0, x, y),
+                         [&](int stage, float px, float py) { return vel2d_waves_warp(vp, sc, stage, px, py); },
+                         x, y, dt, dx, dy, J);
 }
 
 // ---------------------------------------------------------------- cell location

@@ -87,6 +87,27 @@ __device__ __forceinline__ V2p vel2d_pair(const VelParams &vp, const StageCoef &
         r.u = mul2(e, bc(vp.d0)); r.v = mul2(e, bc(vp.d1));
         r.d00 = mul2(e, bc(vp.d0 * vp.d0)); r.d01 = mul2(e, bc(vp.d0 * vp.d1));
         r.d10 = r.d01; r.d11 = mul2(e, bc(vp.d1 * vp.d1));
+    } else if (VK == VK_WAVES2D) {
+        // Psi = sum C_m sin(theta_m), theta_m = kx x + ky y + phase (the scalar vel2d, lane by lane)
+        const WaveTab T = wave_tab(vp.waves, vp.nwaves);
+        const float *amp = sc.wamp + stage * vp.nwaves;
+        F2 u = bc(0.f), v = bc(0.f), d00 = bc(0.f), d01 = bc(0.f), d10 = bc(0.f);
+#pragma unroll 4
+        for (int m = 0; m < vp.nwaves; ++m) {
+            const float4 g = __ldg(T.geo + m), q = __ldg(T.sq + m);
+            const F2 C = bc(__ldg(amp + m));
+            const F2 th = fma2(bc(g.x), x, fma2(bc(g.y), y, bc(g.z)));
+            F2 sn, cs;
+            __sincosf(th.x, &sn.x, &cs.x);
+            __sincosf(th.y, &sn.y, &cs.y);
+            const F2 cc = mul2(C, cs), cn = mul2(C, sn);
+            u = fma2(bc(-g.y), cc, u);
+            v = fma2(bc(g.x), cc, v);
+            d00 = fma2(bc(g.w), cn, d00);
+            d01 = fma2(bc(q.y), cn, d01);
+            d10 = fma2(bc(-q.x), cn, d10);
+        }
+        r.u = u; r.v = v; r.d00 = d00; r.d01 = d01; r.d10 = d10; r.d11 = neg2(d00);
     } else {  // VK_FOURIER2D: Psi = sum A_kl s_k(x) s_l(y), u = -Psi_y, v = Psi_x
         F2 s[5], c[5], sy_[5], cy_[5];
         sincospi2(x, s[1], c[1]);

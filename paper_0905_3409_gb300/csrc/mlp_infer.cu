@@ -17,10 +17,13 @@
 #include <cuda_fp16.h>
 
 #include "mlp_internal.h"
+#include "tc.cuh"
 #include "tma.cuh"
 
 namespace gals {
 namespace mlp {
+
+using namespace tc;
 
 namespace {
 
@@ -32,12 +35,6 @@ constexpr int ROWS = 128;            // points per tile (= M of the products, = 
 constexpr uint32_t TMEM_COLS = NWG <= 2 ? 256 : 512;  // power of two >= NWG * 128
 constexpr int kErrMmaTimeout = 2;
 
-// byte offset of element (r, k) of an R-row, K-major operand in the core-matrix layout
-__host__ __device__ constexpr uint32_t cm_off(int R, int r, int k)
-{
-    return (uint32_t)((k >> 3) * (R >> 3) * 128 + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
 struct Smem {
     __nv_bfloat16 w[W_TOTAL];            // packed operands (weights, bias slabs, ones block)
     __align__(1024) __nv_bfloat16 act[NWG][ROWS * HID];  // A operand of each group's tile
@@ -45,12 +42,6 @@ struct Smem {
     uint32_t tmem;                       // TMEM base address from tcgen05.alloc
     int fail[NWG];
 };
-
-// ---- tcgen05 / TMEM wrappers (PTX ISA, tcgen05 instructions) ----
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void wg_sync(int g)
 {
@@ -67,68 +58,6 @@ __device__ __forceinline__ int wg_sync_or(int g, int flag)
         : "r"(flag), "r"(1 + g), "n"(GT)
         : "memory");
     return r;
-}
-
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets,
-// descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(const void *p, uint32_t lbo, uint32_t sbo)
-{
-    const uint32_t a = smem_u32(p);
-    return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
-           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
-}
-
-// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-// 32 columns of this warp's 32 TMEM lanes (one accumulator row per thread), not yet waited
-// for: several loads share one tcgen05.wait::ld
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
-{
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&v);
 }
 
 // SiLU of two pre-activations given as h = z/2 (FP32): silu(z) = z (1 + tanh(z/2)) / 2
@@ -329,7 +258,9 @@ __device__ __forceinline__ uint32_t tile_hash(uint32_t a, uint32_t b)
     return h ^ (h >> 13);
 }
 
-// Surrogate trace of one step over the grid: tile = 128 consecutive nodes of a row.
+// Surrogate trace of one step over the grid: tile = 128 consecutive nodes of a row; VK
+// is the field of the exact trace the residual check and the fallback run.
+template <int VK>
 __global__ void __launch_bounds__(NT, 1)
 k_mlp_trace(InferParams ip, Geom g, VelParams vp, const StageCoef *__restrict__ coef,
             const double *__restrict__ t_dev, int kstep, double dt, float *__restrict__ trace,
@@ -368,12 +299,29 @@ k_mlp_trace(InferParams ip, Geom g, VelParams vp, const StageCoef *__restrict__ 
         wg_sync(w.g);
         // residual check of `samples` nodes of the tile against the exact RK3 trace
         const int width = min(ROWS, g.n0 - x0);
-        if (w.r < chk.samples) {
+        if (VK == VK_WAVES2D) {
+            // a costly field: each sampled node's trace by a whole warp of the group
+            // (modes split over the lanes), sample j on warp j mod 4
+            for (int jj = w.r >> 5; jj < chk.samples; jj += GT / 32) {
+                const int q = (int)(tile_hash((uint32_t)tile, (uint32_t)kstep + 977u * jj) % (uint32_t)width);
+                const float *yq = &outs[q * 8];
+                const float xq = g.lo0 + (float)(x0 + q) * g.h0, yy = g.lo1 + (float)j * g.h1;
+                float dr[2], Jr[4];
+                trace2d_waves_warp(vp, *coef, xq, yy, dtf, dr[0], dr[1], Jr);
+                const float ex = fmaxf(fabsf(yq[0] * ip.scale[0] * g.h0 - dr[0]) * g.ih0,
+                                       fabsf(yq[1] * ip.scale[1] * g.h1 - dr[1]) * g.ih1);
+                const float mJ[4] = {1.f + dtf * yq[2] * ip.scale[2], dtf * yq[3] * ip.scale[3],
+                                     dtf * yq[4] * ip.scale[4], 1.f + dtf * yq[5] * ip.scale[5]};
+                float eJ = 0.f;
+                for (int e = 0; e < 4; ++e) eJ = fmaxf(eJ, fabsf(mJ[e] - Jr[e]));
+                if ((w.r & 31) == 0 && (!(ex <= chk.tol_x) || !(eJ <= chk.tol_J))) atomicOr(&sm.fail[w.g], 1);
+            }
+        } else if (w.r < chk.samples) {
             const int q = (int)(tile_hash((uint32_t)tile, (uint32_t)kstep + 977u * w.r) % (uint32_t)width);
             const float *yq = &outs[q * 8];
             const float xq = g.lo0 + (float)(x0 + q) * g.h0, yy = g.lo1 + (float)j * g.h1;
             float dr[2], Jr[4];
-            trace2d<TR_RK3, VK_FOURIER2D>(vp, *coef, xq, yy, dtf, dr[0], dr[1], Jr);
+            trace2d<TR_RK3, VK>(vp, *coef, xq, yy, dtf, dr[0], dr[1], Jr);
             const float ex = fmaxf(fabsf(yq[0] * ip.scale[0] * g.h0 - dr[0]) * g.ih0,
                                    fabsf(yq[1] * ip.scale[1] * g.h1 - dr[1]) * g.ih1);
             const float mJ[4] = {1.f + dtf * yq[2] * ip.scale[2], dtf * yq[3] * ip.scale[3],
@@ -386,7 +334,7 @@ k_mlp_trace(InferParams ip, Geom g, VelParams vp, const StageCoef *__restrict__ 
         const bool fail = sm.fail[w.g] != 0;
         if (fail && i < g.n0) {
             const float x = g.lo0 + (float)i * g.h0, yy = g.lo1 + (float)j * g.h1;
-            trace2d<TR_RK3, VK_FOURIER2D>(vp, *coef, x, yy, dtf, d[0], d[1], J);
+            trace2d<TR_RK3, VK>(vp, *coef, x, yy, dtf, d[0], d[1], J);
         }
         if (i < g.n0) {
             const int64_t o = (int64_t)j * g.pitch + i;
@@ -488,14 +436,15 @@ cudaError_t launch_mlp_trace(const InferParams &ip, const Geom &g, const VelPara
 {
     static bool set = false;
     if (!set) {
-        cudaError_t e = set_smem(k_mlp_trace);
+        cudaError_t e = set_smem(k_mlp_trace<VK_FOURIER2D>);
+        if (e == cudaSuccess) e = set_smem(k_mlp_trace<VK_WAVES2D>);
         if (e != cudaSuccess) return e;
         set = true;
     }
     const int ntiles = ((g.n0 + ROWS - 1) / ROWS) * g.n1, sms = sm_count();
     const int blocks = (ntiles + NWG - 1) / NWG;
-    k_mlp_trace<<<blocks < sms ? blocks : sms, NT, sizeof(Smem), s>>>(ip, g, vp, coef, t_dev, kstep,
-                                                                     dt, trace, chk);
+    auto kern = vp.kind == VK_WAVES2D ? k_mlp_trace<VK_WAVES2D> : k_mlp_trace<VK_FOURIER2D>;
+    kern<<<blocks < sms ? blocks : sms, NT, sizeof(Smem), s>>>(ip, g, vp, coef, t_dev, kstep, dt, trace, chk);
     return cudaGetLastError();
 }
 

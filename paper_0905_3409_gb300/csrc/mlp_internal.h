@@ -44,11 +44,14 @@ cudaError_t launch_targets(const VelParams &vp, const float *X, float *T, int n,
 cudaError_t launch_samples(const VelParams &vp, float *Xn, float *T, int n, float dt, float h,
                            int substeps, uint64_t seed, uint64_t step, const float *scale,
                            cudaStream_t s);
+// Training products on the tensor cores; a product that does not complete in time sets *err.
 cudaError_t forward_train(const float *params, const float *X, int n, float *const *Z,
-                          float *const *A, cudaStream_t s);
+                          float *const *A, int *err, cudaStream_t s);
+// split: kMaxSplit * 128 * 128 floats of split-K partials
+constexpr int kMaxSplit = 128;
 cudaError_t backward_train(const float *params, const float *X, const float *T, int n,
                            float *const *Z, float *const *A, float *G0, float *G1, float *grad,
-                           double *loss, const float *one, float *split, cudaStream_t s);
+                           double *loss, const float *one, float *split, int *err, cudaStream_t s);
 cudaError_t adam_step(float *params, const float *grad, float *m, float *v, float lr, float b1,
                       float b2, float eps, int step, cudaStream_t s);
 // FP32 master parameters -> inference layout

@@ -1,6 +1,7 @@
 // mlp_train.cu -- training of the flow-map surrogate on the GPU: target generation by a
 // 32-sub-step RK4 backward flow map with its variational Jacobian, and the forward pass,
-// backward pass and Adam update of the MLP (BF16-rounded operands, FP32 accumulation).
+// backward pass and Adam update of the MLP: the products (forward, dX = dZ W, dW = dZ^T X)
+// on the tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM).
 //
 // Target generation follows the same backward flow the oracle integrates
 // (dX/ds = -v(X, t+dt-s), dJ/ds = -Dv(X, t+dt-s) J, J(0) = I), here with the displacement
@@ -8,9 +9,12 @@
 // (x, y, phase) come from a counter-based generator (SplitMix64, Steele, Lea and Flood,
 // OOPSLA 2014) keyed on (seed, step, sample), so a training run is reproducible.
 #include "mlp_internal.h"
+#include "tc.cuh"
 
 namespace gals {
 namespace mlp {
+
+using namespace tc;
 
 namespace {
 
@@ -50,11 +54,35 @@ __device__ void fourier_vdv(const VelParams &vp, float x, float y, float t, floa
     }
 }
 
+// Plane-wave stream-function field (WAVES2D): the same, from the device mode table.
+__device__ void waves_vdv(const VelParams &vp, float x, float y, float t, float v[2], float D[4])
+{
+    v[0] = v[1] = 0.f;
+    D[0] = D[1] = D[2] = D[3] = 0.f;
+    const WaveTab T = wave_tab(vp.waves, vp.nwaves);
+    for (int m = 0; m < vp.nwaves; ++m) {
+        const float4 g = __ldg(T.geo + m), q = __ldg(T.sq + m), w = __ldg(T.tim + m);
+        const float ph = w.y * t + w.z;  // in turns
+        const float C = w.x * __cosf(2.f * kPi * (ph - floorf(ph)));
+        float sn, cs;
+        __sincosf(g.x * x + g.y * y + g.z, &sn, &cs);
+        v[0] -= C * g.y * cs;
+        v[1] += C * g.x * cs;
+        D[0] += C * g.w * sn;
+        D[1] += C * q.y * sn;
+        D[2] -= C * q.x * sn;
+        D[3] -= C * g.w * sn;
+    }
+}
+
 __device__ void flow_rhs(const VelParams &vp, float x, float y, const float d[2], const float Jm[4],
                          float tau, float dd[2], float dJ[4])
 {
     float v[2], D[4];
-    fourier_vdv(vp, x + d[0], y + d[1], tau, v, D);
+    if (vp.kind == VK_WAVES2D)
+        waves_vdv(vp, x + d[0], y + d[1], tau, v, D);
+    else
+        fourier_vdv(vp, x + d[0], y + d[1], tau, v, D);
     dd[0] = -v[0];
     dd[1] = -v[1];
     dJ[0] = -(D[0] * Jm[0] + D[1] * Jm[2]);
@@ -134,43 +162,121 @@ __global__ void k_samples(const VelParams vp, float *__restrict__ Xn, float *__r
 }
 
 // C[m][n] (+)= sum_k A(m,k) B(k,n) (+ bias[n]) with A(m,k) = A[m*sam + k*sak],
-// B(k,n) = B[k*sbk + n*sbn]; operands rounded to BF16, FP32 accumulation.
+// B(k,n) = B[k*sbk + n*sbn] on the tensor cores: operands rounded to BF16, FP32
+// accumulation in TMEM.  A block owns 128 rows of C (one TMEM lane each) and TN columns
+// (16 or 128); the threads stage 64-wide K chunks of both operands from global memory into
+// shared memory (any strides: transposed operands cost nothing extra here) in the
+// core-matrix layout, and one thread issues the four K = 16 products of a chunk and
+// commits them to an mbarrier that the block waits on (bounded) before the next chunk.
 // Split-K: blockIdx.z covers K-range [z*kchunk, (z+1)*kchunk) and writes C + z*M*ldc.
-constexpr int GT = 64, GK = 16;
-__global__ void __launch_bounds__(256)
-k_gemm(int M, int N, int K, const float *__restrict__ A, int64_t sam, int64_t sak,
-       const float *__restrict__ B, int64_t sbk, int64_t sbn, float *__restrict__ C, int64_t ldc,
-       const float *__restrict__ bias, int kchunk)
+constexpr int TM = 128, TKC = 64;
+constexpr int kErrGemmTimeout = 4;
+
+template <int R>
+__device__ __forceinline__ void stage_operand(char *dst, const float *__restrict__ src, int rows,
+                                              int64_t srow, int64_t sk, int r0, int k0, int kend)
 {
-    __shared__ float As[GK][GT + 1], Bs[GK][GT + 1];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    // task (r, q): 8 consecutive K values of row r as one 16-byte core-matrix row
+    for (int e = threadIdx.x; e < R * (TKC / 8); e += TM) {
+        const int r = e % R, q = e / R;
+        const int gr = r0 + r, gk = k0 + 8 * q;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            v[j] = (gr < rows && gk + j < kend) ? src[(int64_t)gr * srow + (int64_t)(gk + j) * sk] : 0.f;
+        *reinterpret_cast<uint4 *>(dst + cm_off(R, r, 8 * q)) =
+            make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    }
+}
+
+template <int TN>
+__global__ void __launch_bounds__(TM)
+k_tc_gemm(int M, int N, int K, const float *__restrict__ A, int64_t sam, int64_t sak,
+          const float *__restrict__ B, int64_t sbk, int64_t sbn, float *__restrict__ C, int64_t ldc,
+          const float *__restrict__ bias, int kchunk, int *__restrict__ err)
+{
+    __shared__ __align__(1024) char As[TM * TKC * 2];
+    __shared__ __align__(1024) char Bs[TN * TKC * 2];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    constexpr uint32_t TCOLS = TN < 32 ? 32 : TN;  // TMEM allocations are powers of two >= 32
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
     const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
     C += (int64_t)blockIdx.z * M * ldc;
-    float acc[4][4] = {};
-    for (int k0 = kbeg; k0 < kend; k0 += GK) {
-        for (int e = threadIdx.x; e < GK * GT; e += 256) {
-            const int kk = e / GT, r = e % GT;
-            const int gm = m0 + r, gn = n0 + r, gk = k0 + kk;
-            As[kk][r] = (gm < M && gk < kend) ? bf16r(A[gm * sam + gk * sak]) : 0.f;
-            Bs[kk][r] = (gn < N && gk < kend) ? bf16r(B[gk * sbk + gn * sbn]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk)
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(As[kk][ty * 4 + a], Bs[kk][tx * 4 + b], acc[a][b]);
-        __syncthreads();
+    if (tid == 0) mbar_init(&bar, 1);
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "n"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+    uint32_t phase = 0;
+    bool ok = true, any = false;
+    for (int k0 = kbeg; k0 < kend; k0 += TKC) {
+        stage_operand<TM>(As, A, M, sam, sak, m0, k0, kend);
+        stage_operand<TN>(Bs, B, N, sbn, sbk, n0, k0, kend);
+        fence_async_smem();  // generic-proxy writes, read by the tensor core (async proxy)
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int gm = m0 + ty * 4 + a, gn = n0 + tx * 4 + b;
-            if (gm < M && gn < N) C[(int64_t)gm * ldc + gn] = acc[a][b] + (bias ? bias[gn] : 0.f);
+            for (int q = 0; q < TKC / 16; ++q)
+                umma(tbase, sdesc(As + q * 2 * TM * 16, TM * 16, 128), sdesc(Bs + q * 2 * TN * 16, TN * 16, 128),
+                     idesc_bf16(TM, TN), (any || q > 0) ? 1u : 0u);
+            umma_commit(&bar);
         }
+        any = true;
+        // the chunk is overwritten next: wait for its products (one warp polls)
+        const bool done = tid < 32 ? mbar_wait_bounded(&bar, phase) : true;
+        phase ^= 1u;
+        if (__syncthreads_or(!done)) {
+            ok = false;
+            if (tid == 0) {
+                atomicExch(err, kErrGemmTimeout);
+                mbar_wait_bounded(&bar, phase ^ 1u);  // let the late products land
+            }
+            break;
+        }
+        tc_fence_after();
+    }
+    // epilogue: thread r holds row m0 + r (TMEM lane r); 8 columns per load
+    const int gm = m0 + tid;
+    const uint32_t ta = tbase + ((uint32_t)(tid & ~31) << 16);
+    if (ok) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 8) {
+            uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (any) tmem_ld8(ta + (uint32_t)c0, v);
+            if (gm < M)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int gn = n0 + c0 + j;
+                    if (gn < N) C[(int64_t)gm * ldc + gn] = __uint_as_float(v[j]) + (bias ? bias[gn] : 0.f);
+                }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(TCOLS) : "memory");
+}
+
+// Column sums of G (n rows x no columns, row-major) over row blocks: P[z*no + o] = sum of
+// rows [z*rows, (z+1)*rows) (the bias gradients' split-K partials; a fixed order).
+__global__ void k_colsum(const float *__restrict__ G, int n, int no, int rows, float *__restrict__ P)
+{
+    const int o = threadIdx.x, z = blockIdx.x;
+    if (o >= no) return;
+    float acc = 0.f;
+    const int r1 = min(n, (z + 1) * rows);
+    for (int r = z * rows; r < r1; ++r) acc += G[(int64_t)r * no + o];
+    P[(int64_t)z * no + o] = acc;
 }
 
 __global__ void k_silu(const float *__restrict__ Z, float *__restrict__ A, int64_t n)
@@ -227,20 +333,21 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
 
 inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// C (M x N, row stride N) = A B (+ bias); K split into `nsplit` chunks reduced through
-// `split` (nsplit*M*N floats) when nsplit > 1.
+// C (M x N, row stride N) = A B (+ bias) on the tensor cores; K split into `nsplit`
+// chunks reduced through `split` (nsplit*M*N floats) when nsplit > 1.
 void gemm(int M, int N, int K, const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk,
-          int64_t sbn, float *C, const float *bias, int nsplit, float *split, cudaStream_t s)
+          int64_t sbn, float *C, const float *bias, int nsplit, float *split, int *err, cudaStream_t s)
 {
-    if (nsplit <= 1) {
-        k_gemm<<<dim3(nb(N, GT), nb(M, GT), 1), 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, N,
-                                                              bias, K);
-        return;
-    }
     const int kchunk = (K + nsplit - 1) / nsplit;
-    k_gemm<<<dim3(nb(N, GT), nb(M, GT), nsplit), 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn,
-                                                               split, N, nullptr, kchunk);
-    k_sum_splits<<<nb((int64_t)M * N, 256), 256, 0, s>>>(split, nsplit, (int64_t)M * N, C);
+    float *dst = nsplit > 1 ? split : C;
+    const float *bb = nsplit > 1 ? nullptr : bias;
+    if (N > 16)
+        k_tc_gemm<128><<<dim3(nb(N, 128), nb(M, TM), nsplit), TM, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn,
+                                                                          dst, N, bb, kchunk, err);
+    else
+        k_tc_gemm<16><<<dim3(nb(N, 16), nb(M, TM), nsplit), TM, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn,
+                                                                        dst, N, bb, kchunk, err);
+    if (nsplit > 1) k_sum_splits<<<nb((int64_t)M * N, 256), 256, 0, s>>>(split, nsplit, (int64_t)M * N, C);
 }
 
 }  // namespace
@@ -262,13 +369,13 @@ cudaError_t launch_samples(const VelParams &vp, float *Xn, float *T, int n, floa
 
 // Forward pass keeping pre-activations Z[l] (n x out_l) and activations A[l] (A[0] = X).
 cudaError_t forward_train(const float *params, const float *X, int n, float *const *Z,
-                          float *const *A, cudaStream_t s)
+                          float *const *A, int *err, cudaStream_t s)
 {
     const float *in = X;
     for (int l = 0; l < NLAYER; ++l) {
         const int ni = lin(l), no = lout(l);
         // Z = in (n x ni) * W^T (ni x no) + b ; W(k=i, n=o) = W[o*ni + i]
-        gemm(n, no, ni, in, ni, 1, params + woff(l), 1, ni, Z[l], params + boff(l), 1, nullptr, s);
+        gemm(n, no, ni, in, ni, 1, params + woff(l), 1, ni, Z[l], params + boff(l), 1, nullptr, err, s);
         if (l < NLAYER - 1) {
             k_silu<<<nb((int64_t)n * no, 256), 256, 0, s>>>(Z[l], A[l + 1], (int64_t)n * no);
             in = A[l + 1];
@@ -280,9 +387,11 @@ cudaError_t forward_train(const float *params, const float *X, int n, float *con
 // Backward pass of the mean squared error against T: grad (flat, like params) and the loss.
 cudaError_t backward_train(const float *params, const float *X, const float *T, int n,
                            float *const *Z, float *const *A, float *G0, float *G1, float *grad,
-                           double *loss, const float *one, float *split, cudaStream_t s)
+                           double *loss, const float *one, float *split, int *err, cudaStream_t s)
 {
-    const int nsplit = n >= 4096 ? 64 : 1;
+    (void)one;
+    // K = n split into chunks of at least 128 samples, at most kMaxSplit of them
+    const int nsplit = (n + 127) / 128 < kMaxSplit ? (n + 127) / 128 : kMaxSplit;
     const int64_t nout = (int64_t)n * OUT;
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
@@ -292,12 +401,14 @@ cudaError_t backward_train(const float *params, const float *X, const float *T, 
         const int ni = lin(l), no = lout(l);
         const float *Ain = l == 0 ? X : A[l];
         // dW (no x ni) = G^T (no x n) * Ain (n x ni): A(m=o,k=b) = G[b*no + o], B(k=b,n=i) = Ain[b*ni + i]
-        gemm(no, ni, n, G, 1, no, Ain, ni, 1, grad + woff(l), nullptr, nsplit, split, s);
-        // db (no) = G^T * ones
-        gemm(no, 1, n, G, 1, no, one, 0, 0, grad + boff(l), nullptr, nsplit, split, s);
+        gemm(no, ni, n, G, 1, no, Ain, ni, 1, grad + woff(l), nullptr, nsplit, split, err, s);
+        // db (no) = column sums of G
+        const int rows = (n + nsplit - 1) / nsplit;
+        k_colsum<<<nsplit, HID, 0, s>>>(G, n, no, rows, split);
+        k_sum_splits<<<nb(no, 256), 256, 0, s>>>(split, nsplit, no, grad + boff(l));
         if (l > 0) {
             // dA (n x ni) = G (n x no) * W (no x ni)
-            gemm(n, ni, no, G, no, 1, params + woff(l), ni, 1, Gn, nullptr, 1, nullptr, s);
+            gemm(n, ni, no, G, no, 1, params + woff(l), ni, 1, Gn, nullptr, 1, nullptr, err, s);
             k_act_bwd<<<nb((int64_t)n * ni, 256), 256, 0, s>>>(Gn, Z[l - 1], Gn, (int64_t)n * ni);
             float *tmp = G;
             G = Gn;

@@ -27,12 +27,35 @@ __global__ void k_coef_table(StageCoef *table, VelParams vp, const double *t_dev
     if (k >= nsteps) return;
     const double t = t_dev[0] + (double)k * dt;
     stage_coef_one(vp, t, dt, table[k]);
+    if (vp.kind == VK_WAVES2D) table[k].wamp = vp.wamp + (size_t)k * 3 * vp.nwaves;
+}
+
+// WAVES2D amplitudes of the call's steps: wamp[(k 3 + s) M + m] = a_m cos(2 pi (n_m t_s + chi_m'))
+// at the stage times t_s (t + dt, t, t + dt/2) of step k, the phase reduced in FP64.
+__global__ void k_wave_amp(VelParams vp, const double *t_dev, double dt, int nsteps)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int M = vp.nwaves;
+    if (e >= (int64_t)nsteps * 3 * M) return;
+    const int m = (int)(e % M), s = (int)((e / M) % 3), k = (int)(e / (3 * M));
+    const double t = t_dev[0] + (double)k * dt;
+    const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
+    const double a = vp.waves_d[3 * m], n = vp.waves_d[3 * m + 1], chi = vp.waves_d[3 * m + 2];
+    double ph = 2.0 * (n * ts + chi);  // in units of pi
+    ph = ph - 2.0 * floor(0.5 * ph);
+    vp.wamp[e] = (float)(a * cospi(ph));
 }
 }  // namespace
 
 cudaError_t launch_coef_table(StageCoef *table, const VelParams &vp, const double *t_dev,
                               double dt, int nsteps, cudaStream_t s)
 {
+    if (vp.kind == VK_WAVES2D) {
+        const int64_t n = (int64_t)nsteps * 3 * vp.nwaves;
+        k_wave_amp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vp, t_dev, dt, nsteps);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_coef_table<<<(nsteps + 63) / 64, 64, 0, s>>>(table, vp, t_dev, dt, nsteps);
     return cudaGetLastError();
 }
@@ -82,7 +105,7 @@ bool vel_supported(int dim, int kind)
 {
     if (dim == 2)
         return kind == VK_CONST || kind == VK_ROTATION || kind == VK_VORTEX2D ||
-               kind == VK_PSEUDO1D || kind == VK_FOURIER2D;
+               kind == VK_PSEUDO1D || kind == VK_FOURIER2D || kind == VK_WAVES2D;
     return kind == VK_CONST || kind == VK_ROTATION || kind == VK_DEFORM3D;
 }
 

@@ -201,6 +201,7 @@ cudaError_t launch_step2d(const StepLaunch &a, cudaStream_t s)
     case VK_VORTEX2D: return launch_tr<VK_VORTEX2D>(a, s);
     case VK_PSEUDO1D: return launch_tr<VK_PSEUDO1D>(a, s);
     case VK_FOURIER2D: return launch_tr<VK_FOURIER2D>(a, s);
+    case VK_WAVES2D: return launch_tr<VK_WAVES2D>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -250,6 +251,7 @@ cudaError_t launch_step2d_run(const RunLaunch &a, cudaStream_t s)
     case VK_VORTEX2D: return launch_run_tr<VK_VORTEX2D>(a, s);
     case VK_PSEUDO1D: return launch_run_tr<VK_PSEUDO1D>(a, s);
     case VK_FOURIER2D: return launch_run_tr<VK_FOURIER2D>(a, s);
+    case VK_WAVES2D: return launch_run_tr<VK_WAVES2D>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "capi_internal.h"
 
@@ -50,6 +51,18 @@ gals_status velparams_from(int dim, const gals_velocity *v, VelParams &vp, char 
         if (!(v->T > 0.0)) return vfail(msg, len, GALS_ERR_ARG, "modulation period T must be > 0");
         vp.invT = 1.0 / v->T;
     }
+    if (v->kind == GALS_VEL_WAVES2D) {
+        // the mode table itself goes to device memory of the caller (grid or surrogate):
+        // upload_waves
+        if (v->nmodes < 1 || v->nmodes > GALS_MAX_WAVES || !v->modes)
+            return vfail(msg, len, GALS_ERR_ARG, "WAVES2D needs 1..%d modes", GALS_MAX_WAVES);
+        for (int m = 0; m < v->nmodes; ++m) {
+            const double *md = v->modes + 6 * m;
+            if (!finite3(md, 6)) return vfail(msg, len, GALS_ERR_ARG, "non-finite wave %d", m);
+            if (md[4] < 0) return vfail(msg, len, GALS_ERR_ARG, "wave %d: n must be >= 0", m);
+        }
+        vp.nwaves = v->nmodes;
+    }
     if (v->kind == GALS_VEL_FOURIER2D) {
         if (v->nmodes < 1 || v->nmodes > GALS_MAX_MODES || !v->modes)
             return vfail(msg, len, GALS_ERR_ARG, "FOURIER2D needs 1..%d modes", GALS_MAX_MODES);
@@ -87,6 +100,14 @@ double speed_bound(const gals_velocity *v, int dim, const double lo[3], const do
         const double nrm = std::sqrt(2.0 + M_PI), d0 = std::sqrt(2.0) / nrm, d1 = std::sqrt(M_PI) / nrm;
         return std::exp(d0 * std::fmax(lo[0], hi[0]) + d1 * std::fmax(lo[1], hi[1]));
     }
+    case GALS_VEL_WAVES2D: {  // |u|, |v| <= sum |a| |k|
+        double b = 0.0;
+        for (int m = 0; m < v->nmodes; ++m) {
+            const double *md = v->modes + 6 * m;
+            b += std::fabs(md[0]) * std::hypot(md[1], md[2]);
+        }
+        return b;
+    }
     case GALS_VEL_FOURIER2D: {  // |u| <= pi sum |a| l, |v| <= pi sum |a| k
         double b = 0.0;
         for (int m = 0; m < v->nmodes; ++m) {
@@ -98,6 +119,64 @@ double speed_bound(const gals_velocity *v, int dim, const double lo[3], const do
     default:
         return INFINITY;
     }
+}
+
+cudaError_t WaveStore::upload(const gals_velocity *v, cudaStream_t s, bool *changed)
+{
+    *changed = false;
+    const int M = v->nmodes;
+    const size_t nd = (size_t)6 * M;
+    if (M == count && std::memcmp(host.data(), v->modes, sizeof(double) * nd) == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s);  // earlier work may still read the table
+    if (e != cudaSuccess) return e;
+    if (M > cap) {
+        cudaFree(dev);
+        dev = nullptr;
+        cap = 0;
+        if ((e = cudaMalloc(&dev, (sizeof(float4) * 3 + sizeof(double) * 3) * (size_t)M)) != cudaSuccess) {
+            count = 0;
+            return e;
+        }
+        cap = M;
+    }
+    std::vector<float4> f((size_t)3 * M);
+    std::vector<double> d((size_t)3 * M);
+    for (int m = 0; m < M; ++m) {
+        const double *md = v->modes + 6 * m;
+        const float kx = (float)md[1], ky = (float)md[2];
+        f[m] = make_float4(kx, ky, (float)md[3], kx * ky);
+        f[M + m] = make_float4(kx * kx, ky * ky, 0.f, 0.f);
+        const double chi = md[5] / (2.0 * M_PI);
+        f[2 * M + m] = make_float4((float)md[0], (float)md[4], (float)chi, 0.f);
+        d[3 * m] = md[0];
+        d[3 * m + 1] = md[4];
+        d[3 * m + 2] = chi;
+    }
+    if ((e = cudaMemcpy(dev, f.data(), sizeof(float4) * f.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(reinterpret_cast<char *>(dev) + sizeof(float4) * f.size(), d.data(),
+                        sizeof(double) * d.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        count = 0;
+        return e;
+    }
+    host.assign(v->modes, v->modes + nd);
+    count = M;
+    *changed = true;
+    return cudaSuccess;
+}
+
+void WaveStore::bind(VelParams &vp) const
+{
+    vp.waves = reinterpret_cast<const float4 *>(dev);
+    vp.waves_d = reinterpret_cast<const double *>(reinterpret_cast<const char *>(dev) +
+                                                  sizeof(float4) * 3 * (size_t)count);
+}
+
+void WaveStore::release()
+{
+    cudaFree(dev);
+    dev = nullptr;
+    cap = count = 0;
+    host.clear();
 }
 
 bool grid_size_ok(int dim, const int n[3], char *msg, size_t len)

@@ -22,10 +22,12 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE, ERR_UNS
     0, -1, -2, -3, -4, -5, -6, -7
 MEM_HOST, MEM_DEVICE = 0, 1
 LAYOUT_FULL, LAYOUT_COMPACT = 0, 1
-VEL = {"const": 0, "rotation": 1, "vortex2d": 2, "deform3d": 3, "pseudo1d": 4, "fourier2d": 5}
+VEL = {"const": 0, "rotation": 1, "vortex2d": 2, "deform3d": 3, "pseudo1d": 4, "fourier2d": 5,
+       "waves2d": 6}
 TRACE = {"euler": 0, "rk3": 1, "surrogate": 2, "heun_psi": 3}
 SET_RECON_CROSS = 1
 MAX_MODES = 64
+MAX_WAVES = 1024
 
 # every symbol include/gals.h declares
 EXPORTS = [
@@ -208,7 +210,7 @@ class Velocity:
             d.center[i] = float(self.center[i]) if i < len(self.center) else 0.0
             d.c[i] = float(self.c[i]) if i < len(self.c) else 0.0
         if self.modes is not None:
-            m = np.ascontiguousarray(self.modes, dtype=np.float64).reshape(-1, 5)
+            m = np.ascontiguousarray(self.modes, dtype=np.float64).reshape(-1, 6 if self.kind == "waves2d" else 5)
             d._keep = m
             d.nmodes = m.shape[0]
             d.modes = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
