@@ -200,9 +200,10 @@ class ClockSampler:
 
 
 SPIN_CYCLES = 200_000  # ~0.1 ms at 2 GHz: covers the host's graph submission
+TIMING_S = 1.0         # timed load per measurement (--timing-s)
 
 
-def time_windows(step_k, stream, R, min_s=1.0, min_windows=5, max_windows=4000):
+def time_windows(step_k, stream, R, min_s=None, min_windows=5, max_windows=4000):
     """CUDA-event times (ms) of repeated windows of K steps on `stream`.  Each window is
     bracketed by a barrier and a device synchronise on both sides; a short spin kernel
     queued on the stream ahead of the first event keeps the host's submission of the
@@ -211,6 +212,8 @@ def time_windows(step_k, stream, R, min_s=1.0, min_windows=5, max_windows=4000):
     same number, from the slowest rank's first window."""
     import torch
     from paper_0905_3409_gb300 import replicas
+    if min_s is None:
+        min_s = TIMING_S
 
     def one():
         replicas.barrier(R)
@@ -236,6 +239,73 @@ def window_summary(wins):
     w = np.asarray(wins)
     return {"count": int(w.size), "median_ms": float(np.median(w)), "min_ms": float(w.min()),
             "max_ms": float(w.max()), "timed_s": float(w.sum() / 1e3)}
+
+
+def gpu_numa_node(index):
+    """Host NUMA node nearest to GPU `index` (its PCI device's numa_node), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={index}", "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True, timeout=20).stdout
+        bdf = out.strip().splitlines()[0].strip().lower()
+        dom, rest = bdf.split(":", 1)
+        bdf = f"{int(dom, 16):04x}:{rest}"
+        with open(f"/sys/bus/pci/devices/{bdf}/numa_node") as f:
+            node = int(f.read().strip())
+        return node if node >= 0 else None
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return None
+
+
+def node_cpus(node):
+    """CPU ids of a NUMA node (from sysfs), or None."""
+    try:
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            spec = f.read().strip()
+    except OSError:
+        return None
+    cpus = set()
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus or None
+
+
+def pinned_near_gpu(local, arrays):
+    """Page-locked copies of `arrays`, allocated by this thread while it runs on the CPUs of
+    the GPU's nearest NUMA node (pages are placed where they are first touched), and the
+    measured host-to-device and device-to-host copy rates of the first one (GB/s, CUDA
+    events, 3 copies each way)."""
+    import torch
+    node = gpu_numa_node(local)
+    cpus = node_cpus(node) if node is not None else None
+    old = os.sched_getaffinity(0)
+    if cpus:
+        os.sched_setaffinity(0, cpus)
+    try:
+        pins = [torch.from_numpy(a).pin_memory() for a in arrays]
+        pins.append(torch.empty_like(pins[0]).pin_memory())
+    finally:
+        os.sched_setaffinity(0, old)
+    dev = torch.empty(pins[0].shape, dtype=pins[0].dtype, device="cuda")
+    rates = {}
+    for name, dst, src in (("h2d_gbs", dev, pins[0]), ("d2h_gbs", pins[-1], dev)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        rates[name] = 3 * src.numel() * src.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev
+    info = {"numa_node": node, "cpu_affinity_for_allocation": f"node {node}" if cpus else "unchanged",
+            **rates}
+    return pins, info
 
 
 # the sources that define each benchmarked kernel: a recorded DRAM traffic figure is
@@ -580,8 +650,7 @@ def run_ours(args, wl):
     # gals_step_host call (copies overlapped with the step in bands); COMPACT:
     # gals_set_state + gals_step + gals_read_state.
     nplanes = 4 if dim == 2 else 8
-    pin_in = torch.from_numpy(st_host).pin_memory()
-    pin_out = torch.empty_like(pin_in).pin_memory()
+    (pin_in, pin_out), host_buffers = pinned_near_gpu(local, [st_host])
     e2e_steps = max(1, min(args.steps, 20))
     g2 = gals.Grid(n, layout=args.layout, stream=stream, cross=args.cross)
     banded = args.layout == "full" and not cell
@@ -626,7 +695,8 @@ def run_ours(args, wl):
                                     else f"gals step ({launches_per_step} launch(es) per step)")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes,
-                    "api": "gals_step_host" if banded else "gals_set_state + gals_step + gals_read_state"},
+                    "api": "gals_step_host" if banded else "gals_set_state + gals_step + gals_read_state",
+                    "host_buffers": host_buffers},
             # + stage-coefficient table and clock advance kernels
             "gpu_launches": (1 if persistent else args.steps * launches_per_step) + 2,
             "clocks": clocks,
@@ -936,6 +1006,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--loop", default="launches", choices=["launches", "persistent"],
                     help="single-grid workloads: time loop of the K-step call")
+    ap.add_argument("--timing-s", type=float, default=1.0,
+                    help="seconds of timed load per measurement (repeated K-step windows, at least 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="default workload: skip the 512^3 3D line timed in the same run")
@@ -943,6 +1015,8 @@ def main():
     ap.add_argument("--tol", type=float, default=0.05,
                     help="learned trace: residual-check tolerance (cells and Jacobian entries)")
     args = ap.parse_args()
+    global TIMING_S
+    TIMING_S = max(0.0, args.timing_s)
     if args.warmup < 3:
         args.warmup = 3
     wl = WORKLOADS[args.workload]

@@ -310,16 +310,22 @@ gals_status gals_batch_read_state(gals_batch *batch, int index, float *const *fi
 
 gals_status gals_batch_synchronize(gals_batch *batch);
 
-/* Launch shape of the batched step kernel. */
+/* Launch shape and time loop of the batched step. */
 typedef struct {
     int variant;          /* 0: tiles of 128 x 8 nodes, 1: 128 x 16 */
     int blocks;           /* blocks per launch; 0 = one per tile, else persistent blocks */
     double ms_per_step;   /* measured by gals_batch_autotune (0 if set by hand) */
+    int loop;             /* GALS_LOOP_LAUNCHES: one launch per step (graph replay);
+                             GALS_LOOP_PERSISTENT: all steps of a call in one launch, a tile of
+                             step s waiting for the 3 x 3 tiles of its problem around it to finish
+                             step s - 1 (used where every problem's feet stay within the tile
+                             height minus 2 rows of their node; else one launch per step) */
 } gals_batch_tuning;
 
-/* Time every candidate launch shape (tile variant x {one block per tile, persistent
- * grids of 1..occupancy blocks per SM}) for trial_steps steps on the current states
- * (which are left unchanged) and keep the fastest; out (optional) receives it.
+/* Time every candidate (tile variant x {one block per tile, persistent grids of
+ * 1..occupancy blocks per SM} one launch per step, and per tile variant the persistent
+ * multi-step loop over trial_steps + 1 steps from a copy of the states) on the current
+ * states (which are left unchanged) and keep the fastest; out (optional) receives it.
  * Synchronises.  Errors as gals_batch_step. */
 gals_status gals_batch_autotune(gals_batch *batch, const gals_velocity *vels, const double *dt,
                                 int trial_steps, gals_batch_tuning *out);

@@ -4,6 +4,9 @@ Each ``csrc/*.cu`` file is compiled by nvcc in parallel into ``_build/*.o`` and 
 objects are linked into ``paper_0905_3409_gb300/libgals.so``.  Only the files whose
 sources (or the shared headers) changed are recompiled.
 
+A stamp in each build directory records the machine, the nvcc version and the flags; a
+build whose stamp differs starts from no objects (``clean=True`` forces that).
+
 ``build_checked()`` builds the same sources with ``-DGALS_CHECKED`` into
 ``libgals_checked.so`` (objects in ``_build_checked``): the step kernels test their
 data-dependent indexes and report a violation through the grid's error word.
@@ -13,6 +16,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -46,6 +50,29 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _stamp_text(extra) -> str:
+    """What the objects of a build directory depend on besides their sources: the host
+    (objects of another machine are never reused), the compiler and every flag."""
+    try:
+        ver = subprocess.run([nvcc(), "--version"], capture_output=True, text=True).stdout.strip().splitlines()[-1]
+    except (OSError, IndexError):
+        ver = "unknown"
+    return "\n".join([platform.machine(), ver] + ARCH + NVCC_FLAGS + list(extra)) + "\n"
+
+
+def _check_stamp(build_dir: str, extra, clean: bool) -> None:
+    """Empty the build directory when asked to, or when its stamp (machine, nvcc, flags)
+    differs from this build's; then write the stamp."""
+    stamp = os.path.join(build_dir, "STAMP")
+    want = _stamp_text(extra)
+    have = open(stamp).read() if os.path.exists(stamp) else None
+    if clean or have != want:
+        for fn in glob.glob(os.path.join(build_dir, "*.o")):
+            os.remove(fn)
+    with open(stamp, "w") as f:
+        f.write(want)
+
+
 def _compile(src: str, extra, build_dir: str = BUILD) -> str:
     obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     if _stale(obj, [src] + _headers()):
@@ -57,8 +84,13 @@ def _compile(src: str, extra, build_dir: str = BUILD) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=(), build_dir: str = BUILD, lib: str = LIB) -> str:
+def build(verbose: bool = False, extra=(), build_dir: str = BUILD, lib: str = LIB, clean: bool = False) -> str:
+    """Compile what changed (every object when `clean`, or when the machine, the compiler
+    or the flags differ from the last build in build_dir) and link the library."""
     os.makedirs(build_dir, exist_ok=True)
+    _check_stamp(build_dir, extra, clean)
+    if clean and os.path.exists(lib):
+        os.remove(lib)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
@@ -73,11 +105,12 @@ def build(verbose: bool = False, extra=(), build_dir: str = BUILD, lib: str = LI
     return lib
 
 
-def build_checked(verbose: bool = False) -> str:
+def build_checked(verbose: bool = False, clean: bool = False) -> str:
     """The checked build: libgals_checked.so (see the module docstring)."""
     return build(verbose, extra=("-DGALS_CHECKED",), build_dir=os.path.join(HERE, "_build_checked"),
-                 lib=os.path.join(HERE, "libgals_checked.so"))
+                 lib=os.path.join(HERE, "libgals_checked.so"), clean=clean)
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = [a for a in sys.argv[1:] if a != "--clean"]
+    build(verbose=True, extra=args, clean="--clean" in sys.argv[1:])

@@ -33,7 +33,25 @@ struct BatchLaunch {
     int *err;
 };
 
+// Persistent multi-step launch (all nsteps steps of a call): ctl holds 4 + nitems ints, zero
+// before the launch; nbr the 9 neighbour item indices of every item (-1: none).  Feet must
+// stay within batch_tile_rows(variant) - 2 rows and 126 columns of their node.
+struct BatchRunLaunch {
+    float *buf[2];
+    int cur;
+    const BatchProb *probs;
+    const VelParams *vps;
+    const StageCoef *coef;       // coefficients of the launch's steps [step][problem]
+    const CUtensorMap *maps[2];  // per-problem TMA maps of buf[0], buf[1]
+    const BatchItem *items;
+    const int *nbr;
+    int nitems, nprob, nsteps;
+    int variant, kind, compact;
+    int *err, *ctl;
+};
+
 bool batch_kind_supported(int kind);
+cudaError_t launch_batch2d_run(const BatchRunLaunch &a, cudaStream_t s);
 int batch_tile_rows(int variant);
 void batch_tile_box(int variant, int np, uint32_t box[3]);
 int batch_max_blocks_per_sm(int variant, int kind, int compact);

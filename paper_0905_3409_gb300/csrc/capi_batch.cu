@@ -25,7 +25,7 @@ namespace {
 char g_batch_create_err[256] = "";
 
 struct BatchGraph {
-    int nsteps, cur, variant, blocks;
+    int nsteps, cur, variant, blocks, loop;
     std::vector<VelParams> vps;
     std::vector<double> dts;
     cudaGraphExec_t exec;
@@ -48,14 +48,17 @@ struct gals_batch {
     std::vector<int64_t> steps;
     CUtensorMap *maps_dev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [variant][buffer]
     BatchItem *items_dev[2] = {nullptr, nullptr};                             // per variant
+    int *nbr_dev[2] = {nullptr, nullptr};  // per variant: 9 neighbour items of every item
     int nitems[2] = {0, 0};
+    int *run_ctl = nullptr;                // persistent loop: ticket, abort word, item flags
+    std::vector<double> reach;             // per problem: the feet's reach in cells (last step call)
     StageCoef *coef = nullptr;
     int64_t coef_cap = 0;
     int *err_dev = nullptr;
     int cur = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    gals_batch_tuning tuning{1, 0, 0.0};
+    gals_batch_tuning tuning{1, 0, 0.0, GALS_LOOP_LAUNCHES};
     std::vector<BatchGraph> graphs;
     char err[256] = "";
 };
@@ -108,7 +111,26 @@ gals_status prepare(gals_batch *b, const gals_velocity *vels, const double *dt,
     if (!batch_kind_supported(vels[0].kind))
         return bfail(b, GALS_ERR_UNSUPPORTED, "velocity kind %d not available in the batched mode",
                      vels[0].kind);
+    // how far the feet reach, in cells of the problem's finer axis (the persistent loop's
+    // dependences hold while it stays small)
+    b->reach.assign(b->count, 0.0);
+    for (int p = 0; p < b->count; ++p) {
+        const gals_grid_desc &d = b->descs[p];
+        const double lo[3] = {d.lo[0], d.lo[1], 0.0}, hi[3] = {d.hi[0], d.hi[1], 1.0};
+        const double h = std::min((d.hi[0] - d.lo[0]) / (d.n[0] - 1), (d.hi[1] - d.lo[1]) / (d.n[1] - 1));
+        b->reach[p] = dt[p] * speed_bound(&vels[p], 2, lo, hi) / h;
+    }
     return GALS_OK;
+}
+
+// Whether the persistent loop serves tile variant v: every problem's feet within the rows
+// of the launch's dependences.
+bool run_ok(const gals_batch *b, int v)
+{
+    const double lim = std::min(batch_tile_rows(v) - 2, 126);
+    for (double r : b->reach)
+        if (!(r <= lim)) return false;
+    return b->run_ctl != nullptr;
 }
 
 // Upload per-problem dt (into the descriptors) and velocity parameters.
@@ -161,11 +183,48 @@ BatchLaunch make_launch(gals_batch *b, int src, int variant, int blocks, int ste
     return a;
 }
 
+// Persistent launches of all steps (in chunks of fewer than 2^31 - 2^20 work items).
+cudaError_t issue_run(gals_batch *b, int kind, int variant, int nsteps, int src)
+{
+    const int nit = b->nitems[variant];
+    const int chunk = (int)((INT32_MAX - (1 << 20)) / nit);
+    cudaError_t e = cudaSuccess;
+    for (int s0 = 0; s0 < nsteps && e == cudaSuccess; s0 += chunk) {
+        BatchRunLaunch r{};
+        r.buf[0] = b->buf[0];
+        r.buf[1] = b->buf[1];
+        r.cur = src;
+        r.probs = b->probs_dev;
+        r.vps = b->vps_dev;
+        r.coef = b->coef + (int64_t)s0 * b->count;
+        r.maps[0] = b->maps_dev[variant][0];
+        r.maps[1] = b->maps_dev[variant][1];
+        r.items = b->items_dev[variant];
+        r.nbr = b->nbr_dev[variant];
+        r.nitems = nit;
+        r.nprob = b->count;
+        r.nsteps = std::min(chunk, nsteps - s0);
+        r.variant = variant;
+        r.kind = kind;
+        r.compact = b->layout == GALS_LAYOUT_COMPACT;
+        r.err = b->err_dev;
+        r.ctl = b->run_ctl;
+        if ((e = cudaMemsetAsync(b->run_ctl, 0, sizeof(int) * (4 + (size_t)nit), b->stream)) == cudaSuccess)
+            e = launch_batch2d_run(r, b->stream);
+        if (r.nsteps & 1) src ^= 1;
+    }
+    return e;
+}
+
 cudaError_t issue(gals_batch *b, int kind, int nsteps)
 {
     cudaError_t e = launch_batch_coef(b->coef, b->vps_dev, b->t_dev, b->probs_dev, b->count, nsteps,
                                       b->stream);
     if (e != cudaSuccess) return e;
+    if (b->tuning.loop == GALS_LOOP_PERSISTENT && nsteps > 1 && run_ok(b, b->tuning.variant)) {
+        if ((e = issue_run(b, kind, b->tuning.variant, nsteps, b->cur)) != cudaSuccess) return e;
+        return launch_batch_advance(b->t_dev, b->probs_dev, b->count, nsteps, b->stream);
+    }
     int src = b->cur;
     for (int s = 0; s < nsteps; ++s) {
         e = launch_batch2d(make_launch(b, src, b->tuning.variant, b->tuning.blocks, s, kind), b->stream);
@@ -295,6 +354,29 @@ gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch
             for (int y0 = 0; y0 < descs[p].n[1]; y0 += ty)
                 for (int x0 = 0; x0 < descs[p].n[0]; x0 += 128) items.push_back(BatchItem{p, x0, y0});
         b->nitems[v] = (int)items.size();
+        // neighbour lists: the item of each tile of a problem, then its 3 x 3 neighbourhood
+        std::vector<std::vector<int>> at(count);
+        std::vector<int> ntx(count);
+        for (int p = 0; p < count; ++p) {
+            ntx[p] = (descs[p].n[0] + 127) / 128;
+            at[p].assign((size_t)ntx[p] * ((descs[p].n[1] + ty - 1) / ty), -1);
+        }
+        for (int i = 0; i < (int)items.size(); ++i)
+            at[items[i].prob][(size_t)(items[i].y0 / ty) * ntx[items[i].prob] + items[i].x0 / 128] = i;
+        std::vector<int> nbr(items.size() * 9, -1);
+        for (int i = 0; i < (int)items.size(); ++i) {
+            const int p = items[i].prob, bx = items[i].x0 / 128, by = items[i].y0 / ty;
+            const int nty = (int)(at[p].size() / ntx[p]);
+            for (int q = 0; q < 9; ++q) {
+                const int nx = bx + q % 3 - 1, ny = by + q / 3 - 1;
+                if (nx >= 0 && nx < ntx[p] && ny >= 0 && ny < nty) nbr[(size_t)i * 9 + q] = at[p][(size_t)ny * ntx[p] + nx];
+            }
+        }
+        if ((e = cudaMalloc(&b->nbr_dev[v], sizeof(int) * nbr.size())) != cudaSuccess)
+            return bail(e, "cudaMalloc(neighbour lists)");
+        if ((e = cudaMemcpy(b->nbr_dev[v], nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return bail(e, "neighbour list upload");
         if ((e = cudaMalloc(&b->items_dev[v], sizeof(BatchItem) * items.size())) != cudaSuccess)
             return bail(e, "cudaMalloc(work list)");
         if ((e = cudaMemcpy(b->items_dev[v], items.data(), sizeof(BatchItem) * items.size(),
@@ -318,6 +400,9 @@ gals_status gals_create_batch(const gals_grid_desc *descs, int count, gals_batch
                 return bail(e, "map upload");
         }
     }
+    if ((e = cudaMalloc(&b->run_ctl, sizeof(int) * (4 + (size_t)std::max(b->nitems[0], b->nitems[1])))) !=
+        cudaSuccess)
+        return bail(e, "cudaMalloc(time-loop control)");
     if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bail(e, "create sync");
     *out = b;
     return GALS_OK;
@@ -331,8 +416,10 @@ gals_status gals_destroy_batch(gals_batch *b)
     for (int s = 0; s < 2; ++s) cudaFree(b->buf[s]);
     for (int v = 0; v < 2; ++v) {
         cudaFree(b->items_dev[v]);
+        cudaFree(b->nbr_dev[v]);
         for (int s = 0; s < 2; ++s) cudaFree(b->maps_dev[v][s]);
     }
+    cudaFree(b->run_ctl);
     cudaFree(b->probs_dev);
     cudaFree(b->vps_dev);
     cudaFree(b->t_dev);
@@ -390,7 +477,7 @@ gals_status gals_batch_step(gals_batch *b, const gals_velocity *vels, const doub
     BatchGraph *hit = nullptr;
     for (auto &g : b->graphs)
         if (g.nsteps == nsteps && g.cur == b->cur && g.variant == b->tuning.variant &&
-            g.blocks == b->tuning.blocks && g.dts == dts &&
+            g.blocks == b->tuning.blocks && g.loop == b->tuning.loop && g.dts == dts &&
             std::memcmp(g.vps.data(), vps.data(), sizeof(VelParams) * b->count) == 0) {
             hit = &g;
             break;
@@ -416,6 +503,7 @@ gals_status gals_batch_step(gals_batch *b, const gals_velocity *vels, const doub
         }
         BatchGraph bg;
         bg.nsteps = nsteps; bg.cur = b->cur; bg.variant = b->tuning.variant; bg.blocks = b->tuning.blocks;
+        bg.loop = b->tuning.loop;
         bg.vps = vps; bg.dts = dts; bg.exec = exec;
         b->graphs.push_back(std::move(bg));
         hit = &b->graphs.back();
@@ -468,7 +556,9 @@ gals_status gals_batch_read_state(gals_batch *b, int index, float *const *fields
 gals_status gals_batch_set_tuning(gals_batch *b, const gals_batch_tuning *t)
 {
     if (!b || !t) return bfail(b, GALS_ERR_ARG, "NULL argument");
-    if (t->variant < 0 || t->variant > 1 || t->blocks < 0) return bfail(b, GALS_ERR_ARG, "bad tuning");
+    if (t->variant < 0 || t->variant > 1 || t->blocks < 0 ||
+        (t->loop != GALS_LOOP_LAUNCHES && t->loop != GALS_LOOP_PERSISTENT))
+        return bfail(b, GALS_ERR_ARG, "bad tuning");
     b->tuning = *t;
     return GALS_OK;
 }
@@ -507,14 +597,14 @@ gals_status gals_batch_autotune(gals_batch *b, const gals_velocity *vels, const 
         // query needs
         if ((e = launch_batch2d(make_launch(b, b->cur, v, 0, 0, kind), b->stream)) != cudaSuccess)
             return bcuda(b, e, "autotune launch");
-        cands.push_back({v, 0, 0.0});
+        cands.push_back({v, 0, 0.0, GALS_LOOP_LAUNCHES});
         const int occ = std::max(1, batch_max_blocks_per_sm(v, kind, compact));
-        for (int k = 1; k <= occ; ++k) cands.push_back({v, k * sms, 0.0});
+        for (int k = 1; k <= occ; ++k) cands.push_back({v, k * sms, 0.0, GALS_LOOP_LAUNCHES});
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    gals_batch_tuning best{1, 0, 1e30};
+    gals_batch_tuning best{1, 0, 1e30, GALS_LOOP_LAUNCHES};
     for (auto &c : cands) {
         // one untimed launch (first-use attributes, cold caches), then the timed trials
         BatchLaunch a = make_launch(b, b->cur, c.variant, c.blocks, 0, kind);
@@ -528,6 +618,41 @@ gals_status gals_batch_autotune(gals_batch *b, const gals_velocity *vels, const 
         cudaEventElapsedTime(&ms, e0, e1);
         c.ms_per_step = ms / trial_steps;
         if (c.ms_per_step < best.ms_per_step) best = c;
+    }
+    // the persistent loop (all steps of a call in one launch): trial_steps + 1 steps from a
+    // copy of the current states, which are put back after each trial
+    const int K = trial_steps + 1;
+    float *saved = nullptr;
+    if (e == cudaSuccess && (run_ok(b, 0) || run_ok(b, 1)) &&
+        (e = ensure_coef(b, K)) == cudaSuccess &&
+        (e = launch_batch_coef(b->coef, b->vps_dev, b->t_dev, b->probs_dev, b->count, K, b->stream)) == cudaSuccess) {
+        if (cudaMalloc(&saved, sizeof(float) * (size_t)b->total_floats) != cudaSuccess) {
+            cudaGetLastError();  // no room for the copy: no persistent candidates
+            saved = nullptr;
+        }
+        const size_t bytes = sizeof(float) * (size_t)b->total_floats;
+        for (int v = 0; v < 2 && saved && e == cudaSuccess; ++v) {
+            if (!run_ok(b, v)) continue;
+            gals_batch_tuning c{v, 0, 0.0, GALS_LOOP_PERSISTENT};
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // untimed, then timed
+                if ((e = cudaMemcpyAsync(saved, b->buf[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream)) != cudaSuccess)
+                    break;
+                cudaEventRecord(e0, b->stream);
+                e = issue_run(b, kind, v, K, b->cur);
+                cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(b->buf[b->cur], saved, bytes, cudaMemcpyDeviceToDevice, b->stream);
+                if (e == cudaSuccess && (e = cudaEventSynchronize(e1)) == cudaSuccess)
+                    cudaEventElapsedTime(&ms, e0, e1);
+            }
+            c.ms_per_step = ms / K;
+            if (e == cudaSuccess && c.ms_per_step < best.ms_per_step) best = c;
+        }
+        if (saved) {
+            cudaStreamSynchronize(b->stream);
+            cudaFree(saved);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -48,7 +48,8 @@ EXPORTS = [
 
 
 class BatchTuning(ctypes.Structure):
-    _fields_ = [("variant", ctypes.c_int), ("blocks", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+    _fields_ = [("variant", ctypes.c_int), ("blocks", ctypes.c_int), ("ms_per_step", ctypes.c_double),
+                ("loop", ctypes.c_int)]
 
 
 class GalsError(RuntimeError):
@@ -459,10 +460,11 @@ class Batch:
         descs, dt, keep = self._vels(vels, dts)
         t = BatchTuning()
         _bcheck(lib().gals_batch_autotune(self._h, descs, dt, int(trial_steps), ctypes.byref(t)), self._h)
-        return {"variant": t.variant, "blocks": t.blocks, "ms_per_step": t.ms_per_step}
+        return {"variant": t.variant, "blocks": t.blocks, "ms_per_step": t.ms_per_step,
+                "loop": "persistent" if t.loop == 1 else "launches"}
 
-    def set_tuning(self, variant, blocks):
-        t = BatchTuning(int(variant), int(blocks), 0.0)
+    def set_tuning(self, variant, blocks, loop="launches"):
+        t = BatchTuning(int(variant), int(blocks), 0.0, {"launches": 0, "persistent": 1}[loop])
         _bcheck(lib().gals_batch_set_tuning(self._h, ctypes.byref(t)), self._h)
 
     def read_state(self, index, nfields=4):

@@ -1,6 +1,7 @@
 """Batched 2D mode: every problem of a batch evolves bit for bit as the same problem on
-its own grid (the per-tile code is shared), for every launch shape the autotuner can
-pick; one problem is also checked against the FP64 oracle."""
+its own grid (the per-tile code is shared), for every launch shape and time loop (one
+launch per step, or all steps in one persistent launch) the autotuner can pick; one
+problem is also checked against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -50,15 +51,16 @@ def test_batch_equals_single_grids(G, layout, sizes):
         g.step(v, dt, 3)
         singles.append(g.read_state())
         g.close()
-    for variant, blocks in ((0, 0), (1, 0), (1, 152), (0, 304)):
+    for variant, blocks, loop in ((0, 0, "launches"), (1, 0, "launches"), (1, 152, "launches"),
+                                  (0, 304, "launches"), (0, 0, "persistent"), (1, 0, "persistent")):
         b = G.Batch(sizes, layout=layout)
         for p, st in enumerate(states):
             b.set_state(p, st, t0=0.25, recon=True)
-        b.set_tuning(variant, blocks)
+        b.set_tuning(variant, blocks, loop)
         b.step(vels, dts, 2)
         b.step(vels, dts, 1)
         for p in range(len(sizes)):
-            assert np.array_equal(b.read_state(p), singles[p]), (variant, blocks, p)
+            assert np.array_equal(b.read_state(p), singles[p]), (variant, blocks, loop, p)
         b.close()
 
 
@@ -71,6 +73,7 @@ def test_batch_autotune_leaves_state(G):
     before = [b.read_state(p) for p in range(len(sizes))]
     t = b.autotune(vels, dts, trial_steps=2)
     assert t["variant"] in (0, 1) and t["blocks"] >= 0 and t["ms_per_step"] > 0
+    assert t["loop"] in ("launches", "persistent")
     for p in range(len(sizes)):
         assert np.array_equal(b.read_state(p), before[p])
     assert b.nodes == sum(nx * ny for nx, ny in sizes)

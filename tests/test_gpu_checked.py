@@ -70,6 +70,15 @@ def run_cases():
     for p in range(len(sizes)):
         out[f"batch{p}"] = b.read_state(p)
     b.close()
+    b = G.Batch(sizes)  # the persistent multi-step loop
+    b.set_tuning(0, 0, "persistent")
+    for p, ((nx, ny), pr) in enumerate(zip(sizes, probs)):
+        b.set_state(p, inputs.ellipse_sdf((nx, ny), pr.center, pr.a, pr.b, pr.angle, iters=60).astype(np.float32),
+                    recon=True)
+    b.step(vels, dts, 3)
+    for p in range(len(sizes)):
+        out[f"batchp{p}"] = b.read_state(p)
+    b.close()
     for c, (n, vel, cells) in enumerate((((150, 200), dict(kind="vortex2d", T=8.0), 0.8),
                                          ((24, 20, 37), dict(kind="deform3d", T=3.0), 0.4))):
         st = (inputs.circle_sdf(n, center=(0.45, 0.55), r=0.3) if len(n) == 2 else
