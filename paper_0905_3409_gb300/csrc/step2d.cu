@@ -13,6 +13,9 @@
 #ifndef GALS_2D_HY
 #define GALS_2D_HY 1
 #endif
+#ifndef GALS_2D_OV
+#define GALS_2D_OV 1
+#endif
 
 namespace gals {
 
@@ -21,7 +24,12 @@ namespace {
 using namespace t2;
 constexpr int TY = GALS_2D_TY;  // output tile rows (even)
 constexpr int HYT = GALS_2D_HY; // staged halo rows above and below the tile
-using GT = Geo<TY, HYT>;
+constexpr bool OVX = GALS_2D_OV; // overlapped tiles where phi_xy is written (see tile_step2d)
+constexpr int TWS = OVX ? TW + 4 : TW;  // staged columns of the single-grid kernels
+using GT = Geo<TY, HYT, TWS>;
+
+template <int WC> constexpr bool overlapped() { return OVX && WC; }
+template <int WC> constexpr int tile_stride() { return overlapped<WC>() ? TX - 2 : TX; }
 
 template <int TR, int VK, int CR, int WC>
 __global__ void __launch_bounds__(TX, GALS_2D_MINB)
@@ -33,8 +41,8 @@ k_step2d(const float *__restrict__ in, float *__restrict__ out, Geom g, VelParam
     __shared__ __align__(16) Smem<TY, WC> sm;
     if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
     __syncthreads();
-    tile_step2d<TY, TR, VK, CR, WC, HYT>(in, out, g, vp, coef, dt, &tmap, err, blockIdx.x * TX,
-                                    (blockIdx.y + yt0) * TY, tile, sm, 0);
+    tile_step2d<TY, TR, VK, CR, WC, HYT, false, TWS, overlapped<WC>()>(
+        in, out, g, vp, coef, dt, &tmap, err, blockIdx.x * tile_stride<WC>(), (blockIdx.y + yt0) * TY, tile, sm, 0);
 }
 
 // ---------------------------------------------------------------- persistent time loop
@@ -119,7 +127,7 @@ k_step2d_run(float *__restrict__ buf0, float *__restrict__ buf1, Geom g, VelPara
             // generic proxy (acquired above, ordered before this thread by the barrier)
             asm volatile("fence.proxy.async.global;" ::: "memory");
         }
-        const bool ok = tile_step2d<TY, TR, VK, CROSS_PLANE, 1, HYT, true>(
+        const bool ok = tile_step2d<TY, TR, VK, CROSS_PLANE, 1, HYT, true, TWS>(
             b ? buf1 : buf0, b ? buf0 : buf1, g, vp, coef + st, dt, b ? &tmap1 : &tmap0, err,
             bx * TX, by * TY, tile, sm, parity, [&]() { next = atomicAdd(ticket, 1); });
         parity ^= 1u;
@@ -165,7 +173,7 @@ cudaError_t launch_t(const StepLaunch &a, cudaStream_t s)
     const int yt0 = a.band_lo / TY;
     const int yt1 = ((a.band_hi > 0 ? a.band_hi : a.geom.n1) + TY - 1) / TY;
     if (yt1 <= yt0) return cudaSuccess;
-    dim3 grid((a.geom.n0 + TX - 1) / TX, yt1 - yt0);
+    dim3 grid((a.geom.n0 + tile_stride<WC>() - 1) / tile_stride<WC>(), yt1 - yt0);
     const CUtensorMap &map = NP == 4 ? *a.tmap4 : *a.tmap3;
     k_step2d<TR, VK, CR, WC><<<grid, TX, GT::bytes(NP), s>>>(a.in, a.out, a.geom, a.vp, a.coef,
                                                             (float)a.dt, map, a.err, yt0);
@@ -260,7 +268,7 @@ int band_unit(int dim) { return dim == 2 ? TY : 4; }
 
 void tile_box2d(int np, uint32_t box[3])
 {
-    box[0] = TW;
+    box[0] = TWS;
     box[1] = GT::TH;
     box[2] = (uint32_t)np;
 }

@@ -12,7 +12,9 @@
 // batched ones) is staged into shared memory by one TMA copy;
 // feet whose cell leaves the staged tile read global memory instead.  With WC the new
 // psi_y of the tile plus one halo column on each side (2 extra node updates per 128 per
-// row) stays in shared memory and phi_xy+ is written by the same kernel.
+// row) stays in shared memory and phi_xy+ is written by the same kernel: the halo columns
+// are traced after the tile's own, or (overlapped tiles, the single-grid kernel) tiles of
+// 126 columns overlap by one column on each side and the halo is traced with the rest.
 #pragma once
 
 #include "gals_internal.h"
@@ -26,9 +28,9 @@ constexpr int TX = 128;               // output tile columns (one thread each)
 constexpr int HX = 4, HY = 2;         // input halo (x rounded to 16 bytes for TMA)
 constexpr int TW = TX + 2 * HX;
 
-template <int TY, int HYV = HY> struct Geo {
+template <int TY, int HYV = HY, int W = TW> struct Geo {
     static constexpr int TH = TY + 2 * HYV;
-    static constexpr int PS = TW * TH;  // floats per staged plane
+    static constexpr int PS = W * TH;  // floats per staged plane (W columns a row)
     static constexpr int bytes(int np) { return np * PS * 4; }
 };
 
@@ -177,34 +179,35 @@ __device__ __forceinline__ float ld_state(const float *p)
 
 // The 4 corners x 4 data of the cell (k, l) for one node, from the staged tile when the
 // cell (and, for COMPACT, its psi_y window k-1..k+2) lies inside it, else from global
-// memory (feet farther than the halo: CFL well above 1).
-template <int TY, int CR, int HYV = HY, bool COH = false>
+// memory (feet farther than the halo: CFL well above 1).  The staged tile is W columns
+// wide from column x0 - HX (SX: from column x0), TY + 2 HYV rows from row y0 - HYV.
+template <int TY, int CR, int HYV = HY, bool COH = false, int W = TW, bool SX = false>
 __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const Geom &g,
                                             const float *__restrict__ tile, int x0, int y0, int k,
                                             int l, float c[4][4])
 {
-    constexpr int TH = Geo<TY, HYV>::TH, PS = Geo<TY, HYV>::PS;
-    const int tx = k - x0 + HX, ty = l - y0 + HYV;
-    if (tx >= 1 && tx <= TW - 3 && ty >= 0 && ty <= TH - 2) {
+    constexpr int TH = Geo<TY, HYV, W>::TH, PS = Geo<TY, HYV, W>::PS;
+    const int tx = SX ? k - x0 : k - x0 + HX, ty = l - y0 + HYV;
+    if (tx >= 1 && tx <= W - 3 && ty >= 0 && ty <= TH - 2) {
 #ifdef GALS_CHECKED
-        // every read below is t[o + a PS] with -1 <= o <= TW + 2, a < 4
-        const float *t = tile + GALS_CHK(g, ty * TW + tx, PS - TW - 2);
+        // every read below is t[o + a PS] with -1 <= o <= W + 2, a < 4
+        const float *t = tile + GALS_CHK(g, ty * W + tx, PS - W - 2);
 #else
-        const float *t = tile + ty * TW + tx;
+        const float *t = tile + ty * W + tx;
 #endif
 #pragma unroll
         for (int B = 0; B < 2; ++B) {
 #pragma unroll
             for (int A = 0; A < 2; ++A) {
-                const int v = A + 2 * B, o = B * TW + A;
+                const int v = A + 2 * B, o = B * W + A;
                 c[v][0] = t[o];
                 c[v][1] = t[PS + o];
                 c[v][2] = t[2 * PS + o];
                 if (CR == CROSS_PLANE) c[v][3] = t[3 * PS + o];
             }
             if (CR == CROSS_RECON) {
-                const float w[4] = {t[2 * PS + B * TW - 1], c[2 * B][2], c[2 * B + 1][2],
-                                    t[2 * PS + B * TW + 2]};
+                const float w[4] = {t[2 * PS + B * W - 1], c[2 * B][2], c[2 * B + 1][2],
+                                    t[2 * PS + B * W + 2]};
                 c[2 * B][3] = cross_from_window<0>(w, k, g.n0, g.i2h0);
                 c[2 * B + 1][3] = cross_from_window<1>(w, k + 1, g.n0, g.i2h0);
             }
@@ -242,8 +245,8 @@ __device__ __forceinline__ void gather_lane(const float *__restrict__ in, const 
 }
 
 // Update of two nodes (i0, j0) and (i1, j1): phi+, psi_x+, psi_y+ per lane; the staged
-// tile has HYV halo rows.
-template <int TY, int TR, int VK, int CR, int HYV = HY, bool COH = false>
+// tile (W columns from column x0 - HX; SX: from column x0) has HYV halo rows.
+template <int TY, int TR, int VK, int CR, int HYV = HY, bool COH = false, int W = TW, bool SX = false>
 __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const Geom &g,
                                             const float *__restrict__ tile, int x0, int y0,
                                             const VelParams &vp, const StageCoef &sc,
@@ -275,8 +278,8 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
     locate_pair(j0, j1, mul2(dy, bc(g.ih1)), g.n1, l0, l1, eta);
 
     float c0[4][4], c1[4][4];
-    gather_lane<TY, CR, HYV, COH>(in, g, tile, x0, y0, k0, l0, c0);
-    gather_lane<TY, CR, HYV, COH>(in, g, tile, x0, y0, k1, l1, c1);
+    gather_lane<TY, CR, HYV, COH, W, SX>(in, g, tile, x0, y0, k0, l0, c0);
+    gather_lane<TY, CR, HYV, COH, W, SX>(in, g, tile, x0, y0, k1, l1, c1);
     F2 c[4][4];
 #pragma unroll
     for (int v = 0; v < 4; ++v)
@@ -301,16 +304,33 @@ __device__ __forceinline__ void node2d_pair(const float *__restrict__ in, const 
 }
 
 // One tile step: origin (x0, y0).  `tile` is the dynamic shared buffer for the staged
-// input, `sm` the static part; the barrier sm.bar must be initialised (count 1) and
-// `parity` is the phase this tile's copy completes.  COH: global-memory gathers go
+// input (W columns), `sm` the static part; the barrier sm.bar must be initialised (count 1)
+// and `parity` is the phase this tile's copy completes.  COH: global-memory gathers go
 // through L2 (see ld_state).  after_issue() runs on thread 0 right after it issued the copy.  Returns false (after recording
 // kErrTmaTimeout) if the staged copy did not arrive within the wait limit.
 // Must be called by all TX threads of the block.
+//
+// OV (overlapped tiles, WC only): the block owns the TX - 2 columns x0 .. x0 + TX - 3 and
+// its threads walk the columns x0 - 1 .. x0 + TX - 2, so that the two halo columns of the
+// phi_xy stencil are traced in the main loop by the first and last thread instead of in a
+// separate pass after it (those two also store their phi+, psi+, identical to the
+// neighbouring tiles' own, see st_out; they write no phi_xy+).  The staged tile then starts
+// at the 16-byte boundary at or below x0 - 1 - HX, and W = TW + 4 keeps at least HX staged
+// columns on both sides of the walked ones.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <int TY, int TR, int VK, int CR, int WC, int HYV = HY, bool COH = false, class Hook = NoHook>
+// Output store of the overlapped tiles: the halo lanes store the same bits as the lanes of
+// the neighbouring tile that own the column, so every output store is a strong (relaxed,
+// GPU-scope) one and the duplicates do not race.
+__device__ __forceinline__ void st_out(float *p, float v)
+{
+    asm("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+
+template <int TY, int TR, int VK, int CR, int WC, int HYV = HY, bool COH = false, int W = TW,
+          bool OV = false, class Hook = NoHook>
 __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float *__restrict__ out,
                                             const Geom &g, const VelParams &vp,
                                             const StageCoef *__restrict__ coef, float dt,
@@ -318,10 +338,14 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
                                             int x0, int y0, float *tile, Smem<TY, WC> &sm,
                                             uint32_t parity, Hook after_issue = Hook())
 {
+    static_assert(!OV || (WC && W >= TW + 4), "overlapped tiles carry the phi_xy halo");
     auto &psy = sm.psy;
     auto &scp_s = sm.scp;
     const int tid = threadIdx.x;
     constexpr int NP = CR == CROSS_PLANE ? 4 : 3;
+    // first staged column (a multiple of 4: TMA rows start on 16-byte boundaries)
+    const int sx0 = OV ? ((x0 - 1 - HX) & ~3) : x0 - HX;
+    const int gx0 = OV ? sx0 : x0;  // gathers index the staged tile from sx0 (OV) or x0 - HX
 
     // stage the input tile (all planes, halo HX x HY) with one TMA copy
 #ifdef GALS_CHECKED
@@ -331,8 +355,8 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
     constexpr uint32_t polls = kWaitLimit;
     if (tid == 0) {
 #endif
-        mbar_arrive_expect_tx(&sm.bar, Geo<TY, HYV>::bytes(NP));
-        tma_load_3d(tile, tmap, x0 - HX, y0 - HYV, 0, &sm.bar);
+        mbar_arrive_expect_tx(&sm.bar, Geo<TY, HYV, W>::bytes(NP));
+        tma_load_3d(tile, tmap, sx0, y0 - HYV, 0, &sm.bar);
         after_issue();  // thread 0's own work while the copy is in flight
     }
     const StageCoef &sc = *coef;
@@ -362,7 +386,9 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
         }
     }
 
-    const int i = x0 + tid;
+    const int i = OV ? x0 - 1 + tid : x0 + tid;
+    const bool own = !OV || (tid >= 1 && tid <= TX - 2);  // a column of this tile's output
+    constexpr int PQ = OV ? 1 : 2;                          // psy index of column i: i - x0 + 2
     const int rows = min(TY, g.n1 - y0);
     const float xs = g.lo0 + (float)i * g.h0;
     const F2 x = bc(xs);
@@ -379,7 +405,7 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
         return false;
     }
 
-    if (i < g.n0) {
+    if ((!OV || i >= 0) && i < g.n0) {
         for (int r = 0; r < rows; r += 2) {
             const int j0 = y0 + r, j1 = min(j0 + 1, g.n1 - 1);
             const F2 y = make_float2(g.lo1 + (float)j0 * g.h1, g.lo1 + (float)j1 * g.h1);
@@ -387,35 +413,47 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             F2 phi, px, py;
             if (VK == VK_FOURIER2D && TR != TR_GIVEN) {
                 const V2p a1 = fourier_stage1_pair<TY>(fcol, sm.fsum, r);
-                node2d_pair<TY, TR, VK, CR, HYV, COH>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
-                                            cx, ry, phi, px, py, &a1);
+                node2d_pair<TY, TR, VK, CR, HYV, COH, W, OV>(in, g, tile, gx0, y0, vp, sc, scp, dt, i, j0, i,
+                                                   j1, x, y, cx, ry, phi, px, py, &a1);
             } else {
-                node2d_pair<TY, TR, VK, CR, HYV, COH>(in, g, tile, x0, y0, vp, sc, scp, dt, i, j0, i, j1, x, y,
-                                            cx, ry, phi, px, py);
+                node2d_pair<TY, TR, VK, CR, HYV, COH, W, OV>(in, g, tile, gx0, y0, vp, sc, scp, dt, i, j0, i,
+                                                   j1, x, y, cx, ry, phi, px, py);
             }
             const int o = GALS_CHK(g, j0 * g.pitch + i, plane_extent(g));
-            out[o] = phi.x;
-            out[g.plane + o] = px.x;
-            out[2 * g.plane + o] = py.x;
-            if (WC) psy[WC ? r : 0][tid + 2] = py.x;
+            if (OV) {
+                st_out(out + o, phi.x);
+                st_out(out + g.plane + o, px.x);
+                st_out(out + 2 * g.plane + o, py.x);
+            } else {
+                out[o] = phi.x;
+                out[g.plane + o] = px.x;
+                out[2 * g.plane + o] = py.x;
+            }
+            if (WC) psy[WC ? r : 0][tid + PQ] = py.x;
             if (r + 1 < rows) {
                 const int o1 = GALS_CHK(g, o + g.pitch, plane_extent(g));
-                out[o1] = phi.y;
-                out[g.plane + o1] = px.y;
-                out[2 * g.plane + o1] = py.y;
-                if (WC) psy[WC ? r + 1 : 0][tid + 2] = py.y;
+                if (OV) {
+                    st_out(out + o1, phi.y);
+                    st_out(out + g.plane + o1, px.y);
+                    st_out(out + 2 * g.plane + o1, py.y);
+                } else {
+                    out[o1] = phi.y;
+                    out[g.plane + o1] = px.y;
+                    out[2 * g.plane + o1] = py.y;
+                }
+                if (WC) psy[WC ? r + 1 : 0][tid + PQ] = py.y;
             }
         }
     }
     if (WC) {
         // halo columns of psi_y+: x0-1 and x0+TX (x0-2 too when the tile is one column
         // wide, for the one-sided stencil of the last node); two rows per task
-        const int width = min(TX, g.n0 - x0);
+        const int width = min(OV ? TX - 2 : TX, g.n0 - x0);
         const int npairs = (rows + 1) / 2;
         for (int hh = tid; hh < 3 * npairs; hh += TX) {
             const int rp = hh / 3, which = hh % 3;
             const int ih = which == 0 ? x0 - 2 : (which == 1 ? x0 - 1 : x0 + TX);
-            const bool need = which == 0 ? (width == 1 && ih >= 0) : (ih >= 0 && ih < g.n0);
+            const bool need = which == 0 ? (width == 1 && ih >= 0) : (!OV && ih >= 0 && ih < g.n0);
             if (!need) continue;
             const int r = 2 * rp, j0 = y0 + r, j1 = min(j0 + 1, g.n1 - 1);
             const F2 xh = bc(g.lo0 + (float)ih * g.h0);
@@ -423,13 +461,13 @@ __device__ __forceinline__ bool tile_step2d(const float *__restrict__ in, float 
             const VCol cxh = (VK == VK_VORTEX2D) ? vortex_col(xh.x, sc.mod[0]) : VCol{0.f, 0.f, 0.f, 0.f, 0.f};
             const Sep2 ry = (VK == VK_VORTEX2D) ? sep_factors2(y) : Sep2{bc(0.f), bc(0.f), bc(0.f)};
             F2 phi, px, py;
-            node2d_pair<TY, TR, VK, CR, HYV, COH>(in, g, tile, x0, y0, vp, sc, scp, dt, ih, j0, ih, j1, xh, y, cxh,
-                                    ry, phi, px, py);
+            node2d_pair<TY, TR, VK, CR, HYV, COH, W, OV>(in, g, tile, gx0, y0, vp, sc, scp, dt, ih, j0, ih, j1,
+                                               xh, y, cxh, ry, phi, px, py);
             psy[WC ? r : 0][GALS_CHK(g, ih - x0 + 2, TX + 3)] = py.x;
             if (r + 1 < rows) psy[WC ? r + 1 : 0][GALS_CHK(g, ih - x0 + 2, TX + 3)] = py.y;
         }
         __syncthreads();
-        if (i < g.n0) {
+        if (own && i < g.n0) {
             for (int r = 0; r < rows; ++r) {
                 const float *line = psy[WC ? r : 0];
                 const float v = dline(i, g.n0, g.i2h0, [&](int q) { return line[q - x0 + 2]; });
