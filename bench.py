@@ -633,10 +633,11 @@ def run_ours(args, wl):
     ms = replicas.max_over_ranks(R, float(np.median(wins)), device="cuda")
     value = replicas.throughput(nodes * args.steps, world, ms * 1e-3)
 
-    # roofline of the step kernel: launches per step (FULL: step + reconstruction kernels);
-    # with --loop persistent a 2D FULL approach-A call is one launch (CFL 1 here)
+    # roofline of the step: its kernel launches as the library counts them for one K-step
+    # call (2D: one per row band of a step; 3D FULL: step + reconstruction; with --loop
+    # persistent a 2D FULL approach-A call is one launch), plus coefficient and clock kernels
     cell = args.cross == "cell"
-    launches_per_step = 2 if (args.layout == "full" and dim == 3 and not cell) else 1
+    call_launches = g.last_step_launches()
     persistent = args.loop == "persistent" and dim == 2 and args.layout == "full" and not cell
     # approach B stores no mixed derivatives: the step moves phi and psi only
     bpn = bytes_per_node(dim, "compact" if cell else args.layout)
@@ -692,13 +693,14 @@ def run_ours(args, wl):
                          "traffic": recorded_traffic(args.workload, args.layout) if default_path else None,
                          "peak_source": peak_kind,
                          "kernel": ("k_step2d_run (persistent: the K steps in one launch)" if persistent
-                                    else f"gals step ({launches_per_step} launch(es) per step)")},
+                                    else f"gals step ({call_launches} kernel launches per "
+                                         f"{args.steps}-step call)")},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes,
                     "api": "gals_step_host" if banded else "gals_set_state + gals_step + gals_read_state",
                     "host_buffers": host_buffers},
-            # + stage-coefficient table and clock advance kernels
-            "gpu_launches": (1 if persistent else args.steps * launches_per_step) + 2,
+            # per timed window (one K-step call), coefficient-table and clock kernels included
+            "gpu_launches": call_launches,
             "clocks": clocks,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -159,7 +159,11 @@ gals_status gals_set_state(gals_grid *grid, const float *const *fields, int nfie
  * the stage times of the step from t0 + s*dt.  Feet outside the box are clamped into it
  * (outflow or tangential boundaries need no data, Sec. 4.1).  nsteps > 1 is replayed
  * from a cached CUDA graph (of one launch per step, or of one persistent launch, see
- * gals_set_time_loop).  Asynchronous on the grid stream.
+ * gals_set_time_loop).  In 2D the graph splits each step into up to 4 bands of whole tile
+ * rows, at least 2 tiles and the velocity's reach plus 4 rows high; a band of step s
+ * depends only on itself and its two neighbouring bands at step s - 1, so the next step's
+ * bands start while the current one drains (same results bit for bit).  Asynchronous on
+ * the grid stream.
  * Errors: GALS_ERR_ARG (dt <= 0 or non-finite, nsteps < 0, bad velocity descriptor),
  * GALS_ERR_STATE (no state loaded), GALS_ERR_UNSUPPORTED (velocity kind not available in
  * this dimension), GALS_ERR_CUDA (launch failure). */
@@ -173,15 +177,20 @@ gals_status gals_step(gals_grid *grid, const gals_velocity *vel, double dt, int 
  *               (step, tile) items in order and a tile of step s starts once the 3 x 3 tiles
  *               around it have finished step s - 1, so no step waits for the last tiles of
  *               the previous one to drain; elsewhere one launch per step.  On a GB300 it
- *               runs 8 % slower than LAUNCHES on the 4096^2 single vortex (0.148 against
- *               0.137 ms per step): the per-tile flag fence and acquire cost more than the
- *               drained tails it saves.
+ *               runs slower than LAUNCHES on the 4096^2 single vortex (0.148 ms per step
+ *               against 0.128 ms for the banded graph): the per-tile flag fence and acquire
+ *               cost more than the drained tails it saves.
  * Both give the same results bit for bit. */
 enum { GALS_LOOP_LAUNCHES = 0, GALS_LOOP_PERSISTENT = 1 };
 
 /* Select the time loop of later gals_step calls (default LAUNCHES); synchronises when it
  * changes.  Errors: GALS_ERR_ARG. */
 gals_status gals_set_time_loop(gals_grid *grid, int mode);
+
+/* The number of kernel launches the last gals_step call on the grid issued (its step
+ * kernels, per band where the step is banded, and its coefficient-table and clock
+ * kernels; 0 after nsteps = 0), for profiling.  Errors: GALS_ERR_ARG (NULL pointer). */
+gals_status gals_last_step_launches(const gals_grid *grid, int64_t *launches);
 
 /* Copy the current state out (all planes, or the first nfields).  In the COMPACT layout
  * the mixed derivatives are rebuilt first.  Synchronises the grid stream.

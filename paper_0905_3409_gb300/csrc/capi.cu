@@ -33,12 +33,17 @@ struct GraphEntry {
     float sur_key[9];
     // value
     cudaGraphExec_t exec;
+    int64_t launches;     // kernel launches the graph holds
 };
 
 }  // namespace
 
 // at most this many bands in gals_step_host (rows in 2D, z-levels in 3D)
 constexpr int kHostBands = 16;
+#ifndef GALS_STEP_BANDS
+#define GALS_STEP_BANDS 4
+#endif
+constexpr int kStepBands = GALS_STEP_BANDS;  // row bands of a captured multi-step 2D call
 
 struct gals_grid {
     int dim = 0;
@@ -71,6 +76,11 @@ struct gals_grid {
     cudaStream_t hs_in = nullptr, hs_out = nullptr;
     cudaEvent_t hs_enter = nullptr, hs_in_ev[kHostBands] = {}, hs_step_ev[kHostBands] = {};
     std::vector<GraphEntry> graphs;
+    // captured multi-step 2D calls: one stream per row band (they carry no work outside a
+    // capture) and two generations of per-band events
+    cudaStream_t band_s[kStepBands] = {};
+    cudaEvent_t band_fork = nullptr, band_ev[2][kStepBands] = {};
+    int64_t last_launches = 0;    // kernel launches of the last gals_step call
     WaveStore waves;              // WAVES2D: device copy of the field's modes
     float *wamp = nullptr;        // WAVES2D: amplitudes of a call's steps [step][stage][mode]
     int64_t wamp_cap = 0;
@@ -165,13 +175,97 @@ bool use_run(const gals_grid *g, int trace, int nsteps, const double reach[2])
            reach[0] <= run2d_max_cells(0) && reach[1] <= run2d_max_cells(1);
 }
 
+// Row bands of a captured multi-step 2D call.  Step s of band b reads the rows of step
+// s - 1 that its feet reach (plus the staged tile's halo row and the cubic cell) and
+// overwrites rows that step s - 1 of the neighbouring bands read, so with bands at least
+// reach + 4 rows high it depends on bands b - 1, b, b + 1 of step s - 1 only: in the graph a
+// band starts as soon as those three are done, and the next step's first bands fill the
+// tail of the current one.  Whole tile rows per band; n < 2 means one launch per step.
+struct StepBands {
+    int n = 0;
+    int row[kStepBands + 1] = {};
+};
+
+StepBands step_bands(const gals_grid *g, int trace, int nsteps, const double reach[2])
+{
+    StepBands sb;
+    if (g->dim != 2 || nsteps < 2 || trace == GALS_TRACE_SURROGATE || !(reach[1] < 1e6)) return sb;
+    const int unit = band_unit(2);
+    const int tile_rows = (g->geom.n1 + unit - 1) / unit;
+    const int min_rows = (int)std::ceil(reach[1]) + 4;
+    const int min_tiles = std::max(2, (min_rows + unit - 1) / unit);
+    const int n = std::min(kStepBands, tile_rows / min_tiles);
+    if (n < 2) return sb;
+    sb.n = n;
+    for (int b = 0; b <= n; ++b) sb.row[b] = std::min(g->geom.n1, (int)((int64_t)b * tile_rows / n) * unit);
+    sb.row[n] = g->geom.n1;
+    return sb;
+}
+
+// The band streams and events, made once per grid (all or none).
+cudaError_t make_band_streams(gals_grid *g)
+{
+    if (g->band_fork) return cudaSuccess;
+    cudaStream_t st[kStepBands] = {};
+    cudaEvent_t ev[2][kStepBands] = {}, fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int b = 0; b < kStepBands && e == cudaSuccess; ++b) {
+        e = cudaStreamCreateWithFlags(&st[b], cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k][b], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        for (int b = 0; b < kStepBands; ++b) {
+            if (st[b]) cudaStreamDestroy(st[b]);
+            for (int k = 0; k < 2; ++k)
+                if (ev[k][b]) cudaEventDestroy(ev[k][b]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        return e;
+    }
+    std::memcpy(g->band_s, st, sizeof(st));
+    std::memcpy(g->band_ev, ev, sizeof(ev));
+    g->band_fork = fork;
+    return cudaSuccess;
+}
+
+// The kernels of one gals_step call on the grid stream; `launches` counts them (the
+// coefficient table and clock kernels included).
 cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt, int nsteps,
-                        bool first_explicit, const mlp::InferParams *ip = nullptr,
-                        const mlp::Check *chk = nullptr, bool run = false)
+                        bool first_explicit, int64_t &launches, const mlp::InferParams *ip = nullptr,
+                        const mlp::Check *chk = nullptr, bool run = false, const StepBands *bands = nullptr)
 {
     int cur = g->cur;
+    launches = (vp.kind == VK_WAVES2D ? 2 : 1) + 1;  // coefficients (+ wave amplitudes), clock
     cudaError_t ce = launch_coef_table(g->coef, vp, g->t_dev, dt, nsteps, g->stream);
     if (ce != cudaSuccess) return ce;
+    if (bands && bands->n >= 2) {
+        // fork the band streams off the grid stream, chain each band on its two neighbours'
+        // previous step, join them back before the clock advances
+        const int nb = bands->n;
+        if ((ce = cudaEventRecord(g->band_fork, g->stream)) != cudaSuccess) return ce;
+        for (int b = 0; b < nb; ++b)
+            if ((ce = cudaStreamWaitEvent(g->band_s[b], g->band_fork, 0)) != cudaSuccess) return ce;
+        for (int s = 0; s < nsteps; ++s) {
+            for (int b = 0; b < nb; ++b) {
+                cudaStream_t bs = g->band_s[b];
+                if (s > 0) {
+                    const cudaEvent_t *prev = g->band_ev[(s - 1) & 1];
+                    if (b > 0 && (ce = cudaStreamWaitEvent(bs, prev[b - 1], 0)) != cudaSuccess) return ce;
+                    if (b + 1 < nb && (ce = cudaStreamWaitEvent(bs, prev[b + 1], 0)) != cudaSuccess) return ce;
+                }
+                StepLaunch a = step_launch(g, vp, trace, dt, s, cur, first_explicit);
+                a.band_lo = bands->row[b];
+                a.band_hi = bands->row[b + 1];
+                if ((ce = launch_step2d(a, bs)) != cudaSuccess) return ce;
+                if ((ce = cudaEventRecord(g->band_ev[s & 1][b], bs)) != cudaSuccess) return ce;
+            }
+            cur ^= 1;
+        }
+        for (int b = 0; b < nb; ++b)
+            if ((ce = cudaStreamWaitEvent(g->stream, g->band_ev[(nsteps - 1) & 1][b], 0)) != cudaSuccess) return ce;
+        launches += (int64_t)nsteps * nb;
+        return launch_advance_time(g->t_dev, nsteps, dt, g->stream);
+    }
     if (run) {
         // persistent launches of fewer than 2^31 - 2^20 work items (tiles x steps) each:
         // the ticket counter also counts one final draw per block
@@ -196,6 +290,7 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
             if ((ce = cudaMemsetAsync(g->run_ctl, 0, sizeof(int) * (4 + (size_t)tiles), g->stream)) != cudaSuccess ||
                 (ce = launch_step2d_run(r, g->stream)) != cudaSuccess)
                 return ce;
+            ++launches;
             if (r.nsteps & 1) cur ^= 1;
         }
         return launch_advance_time(g->t_dev, nsteps, dt, g->stream);
@@ -209,9 +304,11 @@ cudaError_t issue_steps(gals_grid *g, const VelParams &vp, int trace, double dt,
             if (ce != cudaSuccess) return ce;
             a.vp.given = g->trace_buf;
             a.vp.given_plane = g->geom.plane;
+            ++launches;
         }
         cudaError_t e = g->dim == 2 ? launch_step2d(a, g->stream) : launch_step3d(a, g->stream);
         if (e != cudaSuccess) return e;
+        launches += (g->dim == 3 && a.write_cross) ? 2 : 1;  // 3D FULL: step + reconstruction
         cur ^= 1;
     }
     return launch_advance_time(g->t_dev, nsteps, dt, g->stream);
@@ -241,6 +338,13 @@ gals_status gals_set_time_loop(gals_grid *g, int mode)
         g->graphs.clear();
         g->loop = mode;
     }
+    return GALS_OK;
+}
+
+gals_status gals_last_step_launches(const gals_grid *g, int64_t *launches)
+{
+    if (!g || !launches) return fail(nullptr, GALS_ERR_ARG, "grid or output is NULL");
+    *launches = g->last_launches;
     return GALS_OK;
 }
 
@@ -412,6 +516,12 @@ gals_status gals_destroy_grid(gals_grid *g)
         if (g->hs_in_ev[b]) cudaEventDestroy(g->hs_in_ev[b]);
         if (g->hs_step_ev[b]) cudaEventDestroy(g->hs_step_ev[b]);
     }
+    for (int b = 0; b < kStepBands; ++b) {
+        if (g->band_s[b]) cudaStreamDestroy(g->band_s[b]);
+        for (int k = 0; k < 2; ++k)
+            if (g->band_ev[k][b]) cudaEventDestroy(g->band_ev[k][b]);
+    }
+    if (g->band_fork) cudaEventDestroy(g->band_fork);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
     return GALS_OK;
@@ -508,7 +618,10 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
         sur_key[7] = chk.tol_J;
         sur_key[8] = (float)chk.samples;
     }
-    if (nsteps == 0) return GALS_OK;
+    if (nsteps == 0) {
+        g->last_launches = 0;
+        return GALS_OK;
+    }
     const bool fe = g->cross_explicit;
     if (sur && !g->trace_buf) {
         if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
@@ -537,17 +650,22 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
             return cuda_fail(g, e, "cudaMalloc(time-loop control)");
     }
     if (nsteps == 1) {
-        if ((e = issue_steps(g, vp, v->trace, dt, 1, fe, &ip, &chk)) != cudaSuccess)
+        int64_t nl = 0;
+        if ((e = issue_steps(g, vp, v->trace, dt, 1, fe, nl, &ip, &chk)) != cudaSuccess)
             return cuda_fail(g, e, "step launch");
+        g->last_launches = nl;
     } else {
         GraphEntry *hit = nullptr;
         for (auto &ge : g->graphs)
             if (same_key(ge, nsteps, g->cur, fe, v->trace, g->layout, dt, vp, sur, sur_key)) { hit = &ge; break; }
         if (!hit) {
+            const StepBands bands = run ? StepBands{} : step_bands(g, v->trace, nsteps, reach);
+            if (bands.n >= 2 && (e = make_band_streams(g)) != cudaSuccess) return cuda_fail(g, e, "band streams");
             cudaGraph_t graph;
             if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(g, e, "begin capture");
-            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe, &ip, &chk, run);
+            int64_t nl = 0;
+            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe, nl, &ip, &chk, run, &bands);
             e = cudaStreamEndCapture(g->stream, &graph);
             if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
             if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
@@ -563,11 +681,13 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
             ge.nsteps = nsteps; ge.cur = g->cur; ge.first_explicit = fe; ge.trace = v->trace;
             ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
             ge.sur = sur;
+            ge.launches = nl;
             std::memcpy(ge.sur_key, sur_key, sizeof(sur_key));
             g->graphs.push_back(ge);
             hit = &g->graphs.back();
         }
         if ((e = cudaGraphLaunch(hit->exec, g->stream)) != cudaSuccess) return cuda_fail(g, e, "graph launch");
+        g->last_launches = hit->launches;
     }
     if (nsteps & 1) g->cur ^= 1;
     g->t = g->t + (double)nsteps * dt;

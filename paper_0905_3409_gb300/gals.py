@@ -38,7 +38,7 @@ EXPORTS = [
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
     "gals_batch_set_tuning", "gals_batch_get_tuning", "gals_batch_nodes", "gals_batch_last_error",
     "gals_diagnostics_noalloc", "gals_noalloc_max_nodes", "gals_noalloc_last_error",
-    "gals_checked_wait_test", "gals_set_time_loop",
+    "gals_checked_wait_test", "gals_set_time_loop", "gals_last_step_launches",
     "gals_surrogate_create", "gals_surrogate_destroy", "gals_surrogate_train",
     "gals_surrogate_set_check", "gals_surrogate_stats", "gals_surrogate_get_params",
     "gals_surrogate_set_params", "gals_surrogate_bind", "gals_surrogate_forward",
@@ -156,6 +156,7 @@ def lib() -> ctypes.CDLL:
         L.gals_noalloc_max_nodes.restype = ctypes.c_int64
         L.gals_noalloc_last_error.restype = ctypes.c_char_p
         L.gals_checked_wait_test.argtypes = [ctypes.c_uint32, ctypes.c_int]
+        L.gals_last_step_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         fp = ctypes.POINTER(ctypes.c_float)
         L.gals_surrogate_create.argtypes = [ctypes.POINTER(MlpDesc), ctypes.POINTER(vp)]
         L.gals_surrogate_destroy.argtypes = [vp]
@@ -300,6 +301,13 @@ class Grid:
         """"launches" (one launch per step, the default) or "persistent" (one launch per
         multi-step call where it applies)."""
         _check(lib().gals_set_time_loop(self._h, {"launches": 0, "persistent": 1}[mode]), self._h)
+
+    def last_step_launches(self) -> int:
+        """Kernel launches of the last step() call (step kernels per band, coefficient and
+        clock kernels)."""
+        n = ctypes.c_int64(0)
+        _check(lib().gals_last_step_launches(self._h, ctypes.byref(n)), self._h)
+        return n.value
 
     def read_state(self, out=None, nfields=None):
         """Copy the state into ``out`` (numpy or torch CUDA tensor of self.shape);
