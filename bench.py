@@ -311,7 +311,7 @@ def pinned_near_gpu(local, arrays):
 # the sources that define each benchmarked kernel: a recorded DRAM traffic figure is
 # reported only while these files are unchanged
 KERNEL_SOURCES = {
-    2: ["step2d.cu", "step2d_tile.cuh", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
+    2: ["step2d.cu", "step2d_tile.cuh", "gals_pair.cuh", "gals_device.cuh", "tma.cuh", "capi.cu"],
     3: ["step3d.cu", "step3d_common.cuh", "gals_pair.cuh", "gals_device.cuh", "tma.cuh"],
 }
 
