@@ -65,7 +65,7 @@ WORKLOADS = {
                           desc="2D GALS 2048x2048 nodes on [0,1]^2, FP32, time-periodic (period 1) "
                                "stream-function field of 16 Fourier modes (seed 9053409), circle "
                                "SDF r=0.15 at (0.5,0.75), CFL 1; learned flow-map trace (MLP "
-                               "3-128x4-6, BF16 tensor cores, trained on 32-sub-step RK4 "
+                               "3-128x4-6 on the tensor cores, FP16 inference, trained on 32-sub-step RK4 "
                                "targets) with per-tile RK3 residual check and fallback, against "
                                "the plain RK3 trace"),
     "waves2048": dict(dim=2, n=(2048, 2048), vel=dict(kind="waves2d"), vmax=None,
@@ -74,7 +74,7 @@ WORKLOADS = {
                            "(period 1) stream function of 256 plane waves of random direction, "
                            "|k| in [pi, 4 pi] (seed 9053409; one sine and cosine per wave per "
                            "evaluation), circle SDF r=0.15 at (0.5,0.75), CFL 1; learned flow-map "
-                           "trace (MLP 3-128x4-6, BF16 tensor cores, trained on 32-sub-step RK4 "
+                           "trace (MLP 3-128x4-6 on the tensor cores, FP16 inference, trained on 32-sub-step RK4 "
                            "targets) with per-tile RK3 residual check, against the plain RK3 trace "
                            "at the same step and at larger steps (equal interface error)"),
     # a smaller case of the same 3D kernel, for profiler captures (state still > L2)
@@ -929,7 +929,7 @@ def run_surrogate(args, wl):
     torch.cuda.synchronize()
     ms_mlp = e0.elapsed_time(e1) / reps
     achieved = MLP_FLOP_PER_POINT * nodes / (ms_mlp * 1e-3) / 1e12
-    peak, peak_kind = measured_peaks("bf16")
+    peak, peak_kind = measured_peaks("bf16")  # FP16 operands: the same dense rate as BF16
 
     # e2e through the C ABI with host buffers: per step, pinned host -> device state, one
     # learned step, device -> pinned host state
@@ -956,7 +956,7 @@ def run_surrogate(args, wl):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_sur / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 mlp / f32 step",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16 mlp / f32 step",
             "data": "synthetic",
             "config": {"workload": wl["desc"], "layout": "full", "nodes": nodes, "dt": dt,
                        "l2": "working set per step (2 state buffers 134 MB + trace planes 101 MB) "

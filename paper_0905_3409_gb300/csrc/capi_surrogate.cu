@@ -198,7 +198,7 @@ gals_status gals_surrogate_create(const gals_mlp_desc *desc, gals_surrogate **ou
     const size_t pb = sizeof(float) * NPARAM;
     if ((e = cudaMalloc(&s->params, pb)) != cudaSuccess || (e = cudaMalloc(&s->grad, pb)) != cudaSuccess ||
         (e = cudaMalloc(&s->m, pb)) != cudaSuccess || (e = cudaMalloc(&s->v, pb)) != cudaSuccess ||
-        (e = cudaMalloc(&s->ip.w, sizeof(__nv_bfloat16) * W_TOTAL)) != cudaSuccess ||
+        (e = cudaMalloc(&s->ip.w, sizeof(uint16_t) * W_TOTAL)) != cudaSuccess ||
         (e = cudaMalloc(&s->scale_dev, sizeof(float) * OUT)) != cudaSuccess ||
         (e = cudaMalloc(&s->one, sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&s->loss_dev, sizeof(double))) != cudaSuccess ||

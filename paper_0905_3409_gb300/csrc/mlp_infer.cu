@@ -1,15 +1,16 @@
 // mlp_infer.cu -- tensor-core (tcgen05 + TMEM) inference of the flow-map surrogate and the
 // surrogate trace of one GALS step.
 //
-// A block holds all BF16 weights (120 KB with the bias slabs) in shared memory and runs
+// A block holds all 16-bit weights (120 KB with the bias slabs) in shared memory and runs
 // NWG = 3 groups of 4 warps, each with its own 128-point tile in flight, so that one tile's
 // epilogue overlaps another tile's matrix products.  Per layer and group, one elected
 // thread issues tcgen05.mma (M = 128 points, N = 128 units (16 for the output layer),
-// K = 16 per instruction, BF16 operands from shared memory, FP32 accumulator in TMEM, 128
+// K = 16 per instruction, FP16 operands from shared memory, FP32 accumulator in TMEM, 128
 // columns per group) and commits them to the group's mbarrier; after a bounded wait each
 // thread reads its accumulator row back with tcgen05.ld (the bias is one more K-slab of the
-// product), applies SiLU (FP32, tanh on FP16 pairs) and stores the BF16 activations as the
-// next layer's A operand.  Operands use the no-swizzle K-major core-matrix layout: 8 rows
+// product), applies SiLU on FP16 pairs and stores the FP16 activations as the next layer's
+// A operand.  (GALS_MLP_F16=0 builds the former BF16 operands, SiLU in FP32 with tanh on
+// FP16 pairs.)  Operands use the no-swizzle K-major core-matrix layout: 8 rows
 // x 16 bytes per core matrix, core matrices adjacent in K `lbo` bytes apart and adjacent
 // in M/N 128 bytes apart.  The trace kernel turns the outputs into the foot displacement
 // and the Jacobian of the backward map, checks a few nodes of every tile against the exact
@@ -20,12 +21,25 @@
 #include "tc.cuh"
 #include "tma.cuh"
 
+#ifndef GALS_MLP_F16
+#define GALS_MLP_F16 1
+#endif
+
 namespace gals {
 namespace mlp {
 
 using namespace tc;
 
 namespace {
+
+constexpr bool kF16 = GALS_MLP_F16;  // operand type of every inference product
+
+__device__ __forceinline__ uint16_t to_op(float v)
+{
+    return kF16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16(v));
+}
+__device__ __forceinline__ uint32_t pack_op(float a, float b) { return kF16 ? pack_f16(a, b) : pack_bf16(a, b); }
+__host__ __device__ constexpr uint32_t idesc_op(int M, int N) { return kF16 ? idesc_f16(M, N) : idesc_bf16(M, N); }
 
 constexpr int NWG = 3;               // tile groups (tiles in flight) per block
 constexpr int GT = 128;              // threads per tile group: one per accumulator row
@@ -36,8 +50,8 @@ constexpr uint32_t TMEM_COLS = NWG <= 2 ? 256 : 512;  // power of two >= NWG * 1
 constexpr int kErrMmaTimeout = 2;
 
 struct Smem {
-    __nv_bfloat16 w[W_TOTAL];            // packed operands (weights, bias slabs, ones block)
-    __align__(1024) __nv_bfloat16 act[NWG][ROWS * HID];  // A operand of each group's tile
+    uint16_t w[W_TOTAL];                 // packed operands (weights, bias slabs, ones block)
+    __align__(1024) uint16_t act[NWG][ROWS * HID];  // A operand of each group's tile
     uint64_t bar[NWG];
     uint32_t tmem;                       // TMEM base address from tcgen05.alloc
     int fail[NWG];
@@ -61,14 +75,20 @@ __device__ __forceinline__ int wg_sync_or(int g, int flag)
 }
 
 // SiLU of two pre-activations given as h = z/2 (FP32): silu(z) = z (1 + tanh(z/2)) / 2
-// = h + h tanh(h).  tanh runs on packed FP16 pairs (one MUFU operation for two values,
-// relative error about 1e-3, below the BF16 rounding of the result); the rest in FP32.
-// Returns the two results as a BF16 pair.
-__device__ __forceinline__ uint32_t silu2_bf16(float2 h)
+// = h + h tanh(h), returned as an operand pair.  FP16 operands: h rounded to FP16, tanh on
+// the FP16 pair (one MUFU operation for two values, relative error about 1e-3) and one
+// FP16 fused multiply-add, whose result is the next layer's operand pair as it stands
+// (FP16 carries 3 more mantissa bits than BF16).  BF16 operands: the multiply-add in FP32
+// and the result rounded to BF16.
+__device__ __forceinline__ uint32_t silu2_op(float2 h)
 {
     const __half2 hh = __floats2half2_rn(h.x, h.y);
     uint32_t tr;
     asm("tanh.approx.f16x2 %0, %1;" : "=r"(tr) : "r"(*reinterpret_cast<const uint32_t *>(&hh)));
+    if (kF16) {
+        const __half2 y = __hfma2(hh, *reinterpret_cast<const __half2 *>(&tr), hh);
+        return *reinterpret_cast<const uint32_t *>(&y);
+    }
     const float2 t = __half22float2(*reinterpret_cast<const __half2 *>(&tr));
     const float2 y = __ffma2_rn(h, t, h);
     return pack_bf16(y.x, y.y);
@@ -136,7 +156,7 @@ __device__ __forceinline__ Wg make_wg(const Smem &sm)
 __device__ __forceinline__ void stage_input(Smem &sm, const Wg &w, float a, float b, float c)
 {
     char *base = reinterpret_cast<char *>(sm.act[w.g]) + (w.r >> 3) * 128 + (w.r & 7) * 16;
-    *reinterpret_cast<uint4 *>(base) = make_uint4(pack_bf16(a, b), pack_bf16(c, 1.f), 0u, 0u);
+    *reinterpret_cast<uint4 *>(base) = make_uint4(pack_op(a, b), pack_op(c, 1.f), 0u, 0u);
     *reinterpret_cast<uint4 *>(base + 2048) = make_uint4(0u, 0u, 0u, 0u);
     fence_async_smem();
     wg_sync(w.g);
@@ -155,22 +175,22 @@ __device__ bool run_tile(Smem &sm, Wg &w, int *err, float out[8])
             tc_fence_after();
             if (L == 0) {
                 umma(w.tcol, sdesc(act, 2048, 128), sdesc(wts + 2 * W1_OFF, 2048, 128),
-                     idesc_bf16(128, 128), 0u);
+                     idesc_op(128, 128), 0u);
             } else if (L < NLAYER - 1) {
                 const char *W = wts + 2 * (W2_OFF + (int64_t)(L - 1) * 128 * 128);
 #pragma unroll
                 for (int s = 0; s < 8; ++s)
                     umma(w.tcol, sdesc(act + s * 4096, 2048, 128), sdesc(W + s * 4096, 2048, 128),
-                         idesc_bf16(128, 128), s > 0 ? 1u : 0u);
+                         idesc_op(128, 128), s > 0 ? 1u : 0u);
                 umma(w.tcol, sdesc(wts + 2 * ONES_OFF, 2048, 128),
-                     sdesc(wts + 2 * (WB_OFF + (int64_t)(L - 1) * 128 * 16), 2048, 128), idesc_bf16(128, 128), 1u);
+                     sdesc(wts + 2 * (WB_OFF + (int64_t)(L - 1) * 128 * 16), 2048, 128), idesc_op(128, 128), 1u);
             } else {
 #pragma unroll
                 for (int s = 0; s < 8; ++s)
                     umma(w.tcol, sdesc(act + s * 4096, 2048, 128), sdesc(wts + 2 * W5_OFF + s * 512, 256, 128),
-                         idesc_bf16(128, 16), s > 0 ? 1u : 0u);
+                         idesc_op(128, 16), s > 0 ? 1u : 0u);
                 umma(w.tcol, sdesc(wts + 2 * ONES_OFF, 2048, 128), sdesc(wts + 2 * W5B_OFF, 256, 128),
-                     idesc_bf16(128, 16), 1u);
+                     idesc_op(128, 16), 1u);
             }
             umma_commit(&sm.bar[g]);
         }
@@ -201,7 +221,7 @@ __device__ bool run_tile(Smem &sm, Wg &w, int *err, float out[8])
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int k = 8 * q + 2 * e;
-                            p[e] = silu2_bf16(make_float2(__uint_as_float(v[u][k]), __uint_as_float(v[u][k + 1])));
+                            p[e] = silu2_op(make_float2(__uint_as_float(v[u][k]), __uint_as_float(v[u][k + 1])));
                         }
                         *reinterpret_cast<uint4 *>(arow + (4 * (c + u) + q) * 2048) =
                             make_uint4(p[0], p[1], p[2], p[3]);
@@ -355,36 +375,36 @@ k_mlp_trace(InferParams ip, Geom g, VelParams vp, const StageCoef *__restrict__ 
     block_teardown(sm);
 }
 
-// FP32 master parameters -> packed BF16 operands in the core-matrix layout (see
+// FP32 master parameters -> packed 16-bit operands in the core-matrix layout (see
 // mlp_internal.h): hidden layers and their biases halved, biases as K-slab columns.
-__global__ void k_pack(const float *__restrict__ p, __nv_bfloat16 *__restrict__ w)
+__global__ void k_pack(const float *__restrict__ p, uint16_t *__restrict__ w)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < 128 * 16) {  // W1/2 (inputs 0..2), b1/2 (column 3), zeros
         const int r = e / 16, c = e % 16;
         const float v = c < IN ? p[woff(0) + r * IN + c] : (c == IN ? p[boff(0) + r] : 0.f);
-        w[W1_OFF + cm_off(128, r, c) / 2] = __float2bfloat16(0.5f * v);
+        w[W1_OFF + cm_off(128, r, c) / 2] = to_op(0.5f * v);
     }
     if (e < 3 * 128 * 128) {  // W2/2..W4/2: 128 x 128
         const int L = e / (128 * 128), rem = e % (128 * 128), r = rem / 128, c = rem % 128;
-        w[W2_OFF + (int64_t)L * 128 * 128 + cm_off(128, r, c) / 2] = __float2bfloat16(0.5f * p[woff(1 + L) + rem]);
+        w[W2_OFF + (int64_t)L * 128 * 128 + cm_off(128, r, c) / 2] = to_op(0.5f * p[woff(1 + L) + rem]);
     }
     if (e < 16 * 128) {  // W5: 16 x 128, rows 6..15 zero
         const int r = e / 128, c = e % 128;
-        w[W5_OFF + cm_off(16, r, c) / 2] = __float2bfloat16(r < OUT ? p[woff(4) + r * 128 + c] : 0.f);
+        w[W5_OFF + cm_off(16, r, c) / 2] = to_op(r < OUT ? p[woff(4) + r * 128 + c] : 0.f);
     }
     if (e < 3 * 128 * 16) {  // hidden bias slabs: b/2 in column 0
         const int L = e / (128 * 16), rem = e % (128 * 16), r = rem / 16, c = rem % 16;
         w[WB_OFF + (int64_t)L * 128 * 16 + cm_off(128, r, c) / 2] =
-            __float2bfloat16(c == 0 ? 0.5f * p[boff(1 + L) + r] : 0.f);
+            to_op(c == 0 ? 0.5f * p[boff(1 + L) + r] : 0.f);
     }
     if (e < 16 * 16) {  // output bias slab: b5 in column 0
         const int r = e / 16, c = e % 16;
-        w[W5B_OFF + cm_off(16, r, c) / 2] = __float2bfloat16(c == 0 && r < OUT ? p[boff(4) + r] : 0.f);
+        w[W5B_OFF + cm_off(16, r, c) / 2] = to_op(c == 0 && r < OUT ? p[boff(4) + r] : 0.f);
     }
     if (e < 128 * 16) {  // ones block
         const int r = e / 16, c = e % 16;
-        w[ONES_OFF + cm_off(128, r, c) / 2] = __float2bfloat16(c == 0 ? 1.f : 0.f);
+        w[ONES_OFF + cm_off(128, r, c) / 2] = to_op(c == 0 ? 1.f : 0.f);
     }
 }
 

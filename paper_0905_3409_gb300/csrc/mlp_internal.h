@@ -7,15 +7,15 @@
 namespace gals {
 namespace mlp {
 
-// Inference weights: BF16 copies laid out for the tensor-core kernel, FP32 biases and
-// the output de-normalisation.
+// Inference weights: 16-bit copies (FP16; BF16 in a build with GALS_MLP_F16=0) laid out
+// for the tensor-core kernel, and the output de-normalisation.
 // Each weight matrix (N units x K inputs) is stored as the tensor core's K-major operand
-// in the no-swizzle core-matrix layout (8 x 8 BF16 blocks of 128 bytes).  Biases enter the
+// in the no-swizzle core-matrix layout (8 x 8 16-bit blocks of 128 bytes).  Biases enter the
 // products as one more K-slab: bias column k = 0 of a 16-wide slab times a constant block
 // whose column 0 is 1 (layer 1 uses input column 3 = 1 instead).  Hidden layers (weights
-// and biases) are pre-scaled by 1/2, exact in BF16, so their accumulators hold z/2.
+// and biases) are pre-scaled by 1/2, exact in FP16 and BF16, so their accumulators hold z/2.
 struct InferParams {
-    __nv_bfloat16 *w;   // packed operands, W_TOTAL elements (offsets below)
+    uint16_t *w;        // packed 16-bit operands, W_TOTAL elements (offsets below)
     float scale[OUT];   // output k of the network times scale[k] is the physical target
 };
 constexpr int64_t W1_OFF = 0,                          // 128 x 16: W1/2 (inputs 0..2), b1/2 (column 3)
