@@ -54,6 +54,11 @@ WORKLOADS = {
                             "(r=0.15 at (0.5,0.75,0.5), slot width 0.05, depth 0.25) in rigid "
                             "rotation about the z-axis through (0.5,0.5) (omega=2pi), RK3 "
                             "trace, CFL 1"),
+    "fourier4096": dict(dim=2, n=(4096, 4096), vel=dict(kind="fourier2d"), vmax=None, nmodes=16,
+                        desc="2D GALS 4096x4096 nodes on [0,1]^2, FP32, time-periodic (period 1) "
+                             "stream-function field of 16 Fourier modes (seed 9053409), circle SDF "
+                             "r=0.15 at (0.5,0.75), RK3 trace, CFL 1 (the batched mode's field "
+                             "kind on one grid larger than L2, for profiling its tile code)"),
     "batch256": dict(dim=2, n=None, batch=256, vel=dict(kind="fourier2d"), vmax=None,
                      desc="Batched 2D GALS, FP32: 256 independent problems, side lengths uniform "
                           "in [128,1024] (seed 9053409), each an ellipse SDF advected by its own "
@@ -612,8 +617,9 @@ def run_ours(args, wl):
     dim = wl["dim"]
     nodes = int(np.prod(n))
     h = 1.0 / (n[0] - 1)
-    dt = h / wl["vmax"]
-    vel = gals.Velocity(trace=args.trace, **wl["vel"])
+    modes = wl_modes(wl)
+    dt = wl_dt(wl) if modes is not None else h / wl["vmax"]
+    vel = gals.Velocity(trace=args.trace, modes=modes, **wl["vel"])
     st_host = initial_state(wl)
     stream = torch.cuda.Stream()
     g = gals.Grid(n, layout=args.layout, stream=stream, cross=args.cross)
