@@ -158,8 +158,9 @@ gals_status gals_set_state(gals_grid *grid, const float *const *fields, int nfie
  * superconsistent form of Sec. 5.1; M = P A of Sec. 5.2).  Step s uses the velocity at
  * the stage times of the step from t0 + s*dt.  Feet outside the box are clamped into it
  * (outflow or tangential boundaries need no data, Sec. 4.1).  nsteps > 1 is replayed
- * from a cached CUDA graph (of one launch per step, or of one persistent launch, see
- * gals_set_time_loop).  In 2D the graph splits each step into up to 4 bands of whole tile
+ * from cached CUDA graphs of at most 256 steps each (of one launch per step, or of one
+ * persistent launch, see gals_set_time_loop); each graph reads the grid clock on the
+ * device and advances it, so longer calls replay the same graph.  In 2D the graph splits each step into up to 4 bands of whole tile
  * rows, at least 2 tiles and the velocity's reach plus 4 rows high; a band of step s
  * depends only on itself and its two neighbouring bands at step s - 1, so the next step's
  * bands start while the current one drains (same results bit for bit).  Asynchronous on

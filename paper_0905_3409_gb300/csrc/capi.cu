@@ -7,6 +7,7 @@
 // replayed.  The grid time lives on the device too, so a cached graph is valid for any
 // start time: step s of a call reads t = t_dev + s*dt, and the graph ends by advancing
 // t_dev.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,6 +45,9 @@ constexpr int kHostBands = 16;
 #define GALS_STEP_BANDS 4
 #endif
 constexpr int kStepBands = GALS_STEP_BANDS;  // row bands of a captured multi-step 2D call
+// Longest run of steps one cached graph holds (even: a whole graph leaves the ping-pong
+// buffers as it found them); longer calls replay it.
+constexpr int kGraphSteps = 256;
 
 struct gals_grid {
     int dim = 0;
@@ -591,7 +595,7 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
         // the modes in device memory, and room for the call's amplitude table
         bool changed = false;
         if ((e = g->waves.upload(v, g->stream, &changed)) != cudaSuccess) return cuda_fail(g, e, "wave table");
-        const int64_t need = (int64_t)nsteps * 3 * v->nmodes;
+        const int64_t need = (int64_t)std::min(nsteps, kGraphSteps) * 3 * v->nmodes;
         if (need > g->wamp_cap) {
             if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
             for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);  // they use the old table
@@ -628,7 +632,7 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
         if ((e = cudaMalloc(&g->trace_buf, sizeof(float) * 6 * (size_t)g->geom.plane)) != cudaSuccess)
             return cuda_fail(g, e, "cudaMalloc(trace buffer)");
     }
-    if (nsteps > g->coef_cap) {
+    if (std::min(nsteps, kGraphSteps) > g->coef_cap) {
         // grow the coefficient table; cached graphs refer to the old one
         if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
         for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
@@ -636,60 +640,70 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
         cudaFree(g->coef);
         g->coef = nullptr;
         g->coef_cap = 0;
-        const int cap = nsteps < 64 ? 64 : nsteps;
+        const int cap = std::max(64, std::min(nsteps, kGraphSteps));
         if ((e = cudaMalloc(&g->coef, sizeof(StageCoef) * (size_t)cap)) != cudaSuccess)
             return cuda_fail(g, e, "cudaMalloc(coefficient table)");
         g->coef_cap = cap;
     }
     const double vmax = speed_bound(v, g->dim, g->lo, g->hi);
     const double reach[2] = {dt * vmax / g->h[0], dt * vmax / g->h[1]};
-    const bool run = use_run(g, v->trace, nsteps, reach);
+    const bool run = use_run(g, v->trace, std::min(nsteps, kGraphSteps), reach);
     if (run && !g->run_ctl) {
         if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_fail(g, e, "sync");
         if ((e = cudaMalloc(&g->run_ctl, sizeof(int) * (4 + (size_t)run2d_tiles(g->geom)))) != cudaSuccess)
             return cuda_fail(g, e, "cudaMalloc(time-loop control)");
     }
-    if (nsteps == 1) {
-        int64_t nl = 0;
-        if ((e = issue_steps(g, vp, v->trace, dt, 1, fe, nl, &ip, &chk)) != cudaSuccess)
-            return cuda_fail(g, e, "step launch");
-        g->last_launches = nl;
-    } else {
-        GraphEntry *hit = nullptr;
-        for (auto &ge : g->graphs)
-            if (same_key(ge, nsteps, g->cur, fe, v->trace, g->layout, dt, vp, sur, sur_key)) { hit = &ge; break; }
-        if (!hit) {
-            const StepBands bands = run ? StepBands{} : step_bands(g, v->trace, nsteps, reach);
-            if (bands.n >= 2 && (e = make_band_streams(g)) != cudaSuccess) return cuda_fail(g, e, "band streams");
-            cudaGraph_t graph;
-            if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-                return cuda_fail(g, e, "begin capture");
+    // runs of up to kGraphSteps steps: one step as launches, more from a cached graph; each
+    // graph computes its coefficients from the device clock and advances it, so the graph of
+    // one run serves every run of the same length, buffer parity and first-step layout
+    int64_t total = 0;
+    for (int s0 = 0; s0 < nsteps;) {
+        const int cs = std::min(kGraphSteps, nsteps - s0);
+        const bool fe_c = fe && s0 == 0;
+        if (cs == 1) {
             int64_t nl = 0;
-            cudaError_t le = issue_steps(g, vp, v->trace, dt, nsteps, fe, nl, &ip, &chk, run, &bands);
-            e = cudaStreamEndCapture(g->stream, &graph);
-            if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
-            if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
-            cudaGraphExec_t exec;
-            e = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
-            if (g->graphs.size() >= 8) {
-                cudaGraphExecDestroy(g->graphs.front().exec);
-                g->graphs.erase(g->graphs.begin());
+            if ((e = issue_steps(g, vp, v->trace, dt, 1, fe_c, nl, &ip, &chk)) != cudaSuccess)
+                return cuda_fail(g, e, "step launch");
+            total += nl;
+        } else {
+            GraphEntry *hit = nullptr;
+            for (auto &ge : g->graphs)
+                if (same_key(ge, cs, g->cur, fe_c, v->trace, g->layout, dt, vp, sur, sur_key)) { hit = &ge; break; }
+            if (!hit) {
+                const StepBands bands = run ? StepBands{} : step_bands(g, v->trace, cs, reach);
+                if (bands.n >= 2 && (e = make_band_streams(g)) != cudaSuccess) return cuda_fail(g, e, "band streams");
+                cudaGraph_t graph;
+                if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                    return cuda_fail(g, e, "begin capture");
+                int64_t nl = 0;
+                cudaError_t le = issue_steps(g, vp, v->trace, dt, cs, fe_c, nl, &ip, &chk, run, &bands);
+                e = cudaStreamEndCapture(g->stream, &graph);
+                if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
+                if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
+                cudaGraphExec_t exec;
+                e = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+                if (g->graphs.size() >= 8) {
+                    cudaGraphExecDestroy(g->graphs.front().exec);
+                    g->graphs.erase(g->graphs.begin());
+                }
+                GraphEntry ge;
+                ge.nsteps = cs; ge.cur = g->cur; ge.first_explicit = fe_c; ge.trace = v->trace;
+                ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
+                ge.sur = sur;
+                ge.launches = nl;
+                std::memcpy(ge.sur_key, sur_key, sizeof(sur_key));
+                g->graphs.push_back(ge);
+                hit = &g->graphs.back();
             }
-            GraphEntry ge;
-            ge.nsteps = nsteps; ge.cur = g->cur; ge.first_explicit = fe; ge.trace = v->trace;
-            ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
-            ge.sur = sur;
-            ge.launches = nl;
-            std::memcpy(ge.sur_key, sur_key, sizeof(sur_key));
-            g->graphs.push_back(ge);
-            hit = &g->graphs.back();
+            if ((e = cudaGraphLaunch(hit->exec, g->stream)) != cudaSuccess) return cuda_fail(g, e, "graph launch");
+            total += hit->launches;
         }
-        if ((e = cudaGraphLaunch(hit->exec, g->stream)) != cudaSuccess) return cuda_fail(g, e, "graph launch");
-        g->last_launches = hit->launches;
+        if (cs & 1) g->cur ^= 1;
+        s0 += cs;
     }
-    if (nsteps & 1) g->cur ^= 1;
+    g->last_launches = total;
     g->t = g->t + (double)nsteps * dt;
     g->steps += nsteps;
     g->cross_explicit = false;

@@ -92,3 +92,23 @@ def test_band_launch_counts(G):
         assert g.last_step_launches() == 5 * nb + 2, (n, cfl, nb, g.last_step_launches())
         g.step(vel, dt, 0)
         assert g.last_step_launches() == 0
+
+
+def test_long_call_replays_bounded_graphs(G):
+    """A call of more steps than one graph holds (256) replays graphs of 256 steps and one of
+    the rest: the same result as one launch per step, bit for bit, for an odd total (the
+    last graph flips the ping-pong buffers), and the launch count of every replay."""
+    n, nsteps = (128, 100), 601
+    vel = G.Velocity("rotation", omega=2 * math.pi)
+    dt = 0.5 / (max(n) - 1)
+    st = inputs.circle_sdf(n).astype(np.float32)
+    a, b = G.Grid(n), G.Grid(n)
+    for g in (a, b):
+        g.set_state(st, recon=True)
+    a.step(vel, dt, nsteps)
+    for _ in range(nsteps):
+        b.step(vel, dt, 1)
+    nb = expected_bands(n[1], dt * 2 * math.pi * 0.5 * (n[1] - 1))
+    assert a.last_step_launches() == 2 * (256 * nb + 2) + (89 * nb + 2)
+    assert np.array_equal(a.read_state(), b.read_state())
+    assert a.time == pytest.approx(b.time, rel=0, abs=1e-12)
