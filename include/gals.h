@@ -174,7 +174,8 @@ gals_status gals_step(gals_grid *grid, const gals_velocity *vel, double dt, int 
  *   LAUNCHES    one launch per step, replayed from a cached CUDA graph (the default).
  *   PERSISTENT  where it applies (2D, FULL layout, approach A, the Euler / RK3 / Heun-psi
  *               traces, and feet at most 126 columns and 12 rows from their node by the
- *               velocity's speed bound) the whole call is one persistent launch: blocks take
+ *               velocity's speed bound) each run of up to 256 steps of a call (see
+ *               gals_step) is one persistent launch: blocks take
  *               (step, tile) items in order and a tile of step s starts once the 3 x 3 tiles
  *               around it have finished step s - 1, so no step waits for the last tiles of
  *               the previous one to drain; elsewhere one launch per step.  On a GB300 it
