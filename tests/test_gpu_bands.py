@@ -112,3 +112,24 @@ def test_long_call_replays_bounded_graphs(G):
     assert a.last_step_launches() == 2 * (256 * nb + 2) + (89 * nb + 2)
     assert np.array_equal(a.read_state(), b.read_state())
     assert a.time == pytest.approx(b.time, rel=0, abs=1e-12)
+
+
+def test_bench_configuration_bands_equal_single_steps(G):
+    """The benchmark's launch configuration: the 4096^2 single vortex at CFL 1, stepped as
+    the bench times it (a multi-step call: four bands of 73 and 74 tile rows per step),
+    equals one whole-grid launch per step bit for bit."""
+    n = (4096, 4096)
+    st = inputs.circle_sdf(n).astype(np.float32)
+    vel = G.Velocity("vortex2d", T=8.0)
+    dt = 1.0 / (n[0] - 1)
+    a, b = G.Grid(n), G.Grid(n)
+    for g in (a, b):
+        g.set_state(st, recon=True)
+    a.step(vel, dt, 4)
+    assert a.last_step_launches() == 4 * 4 + 2
+    for _ in range(4):
+        b.step(vel, dt, 1)
+    ra, rb = a.read_state(), b.read_state()
+    assert np.array_equal(ra, rb)
+    a.close()
+    b.close()
