@@ -207,14 +207,17 @@ __device__ bool run_tile(Smem &sm, Wg &w, int *err, float out[8])
             // SiLU of h = z/2 (the accumulator), BF16 activations of row r as the next
             // layer's A operand (K = 128)
             char *arow = reinterpret_cast<char *>(sm.act[g]) + (w.r >> 3) * 128 + (w.r & 7) * 16;
+            // one 32-column TMEM load per wait: two per wait held 64 accumulator values live
+            // and pushed the trace kernel past its 168-register cap (spills)
+            constexpr int NU = 1;
 #pragma unroll 1
-            for (int c = 0; c < 4; c += 2) {
-                uint32_t v[2][32];
-                tmem_ld32_nowait(ta + 32 * c, v[0]);
-                tmem_ld32_nowait(ta + 32 * c + 32, v[1]);
+            for (int c = 0; c < 4; c += NU) {
+                uint32_t v[NU][32];
+#pragma unroll
+                for (int u = 0; u < NU; ++u) tmem_ld32_nowait(ta + 32 * (c + u), v[u]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 2; ++u)
+                for (int u = 0; u < NU; ++u)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         uint32_t p[4];
