@@ -657,51 +657,72 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     // graph computes its coefficients from the device clock and advances it, so the graph of
     // one run serves every run of the same length, buffer parity and first-step layout
     int64_t total = 0;
-    for (int s0 = 0; s0 < nsteps;) {
-        const int cs = std::min(kGraphSteps, nsteps - s0);
-        const bool fe_c = fe && s0 == 0;
+    const char *what = "";
+    auto run_one = [&](int cs, bool fe_c) -> cudaError_t {
+        cudaError_t ce;
         if (cs == 1) {
             int64_t nl = 0;
-            if ((e = issue_steps(g, vp, v->trace, dt, 1, fe_c, nl, &ip, &chk)) != cudaSuccess)
-                return cuda_fail(g, e, "step launch");
-            total += nl;
-        } else {
-            GraphEntry *hit = nullptr;
-            for (auto &ge : g->graphs)
-                if (same_key(ge, cs, g->cur, fe_c, v->trace, g->layout, dt, vp, sur, sur_key)) { hit = &ge; break; }
-            if (!hit) {
-                const StepBands bands = run ? StepBands{} : step_bands(g, v->trace, cs, reach);
-                if (bands.n >= 2 && (e = make_band_streams(g)) != cudaSuccess) return cuda_fail(g, e, "band streams");
-                cudaGraph_t graph;
-                if ((e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-                    return cuda_fail(g, e, "begin capture");
-                int64_t nl = 0;
-                cudaError_t le = issue_steps(g, vp, v->trace, dt, cs, fe_c, nl, &ip, &chk, run, &bands);
-                e = cudaStreamEndCapture(g->stream, &graph);
-                if (le != cudaSuccess) { if (e == cudaSuccess) cudaGraphDestroy(graph); return cuda_fail(g, le, "capture launch"); }
-                if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
-                cudaGraphExec_t exec;
-                e = cudaGraphInstantiate(&exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
-                if (g->graphs.size() >= 8) {
-                    cudaGraphExecDestroy(g->graphs.front().exec);
-                    g->graphs.erase(g->graphs.begin());
-                }
-                GraphEntry ge;
-                ge.nsteps = cs; ge.cur = g->cur; ge.first_explicit = fe_c; ge.trace = v->trace;
-                ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
-                ge.sur = sur;
-                ge.launches = nl;
-                std::memcpy(ge.sur_key, sur_key, sizeof(sur_key));
-                g->graphs.push_back(ge);
-                hit = &g->graphs.back();
+            if ((ce = issue_steps(g, vp, v->trace, dt, 1, fe_c, nl, &ip, &chk)) != cudaSuccess) {
+                what = "step launch";
+                return ce;
             }
-            if ((e = cudaGraphLaunch(hit->exec, g->stream)) != cudaSuccess) return cuda_fail(g, e, "graph launch");
-            total += hit->launches;
+            total += nl;
+            return cudaSuccess;
+        }
+        GraphEntry *hit = nullptr;
+        for (auto &ge : g->graphs)
+            if (same_key(ge, cs, g->cur, fe_c, v->trace, g->layout, dt, vp, sur, sur_key)) { hit = &ge; break; }
+        if (!hit) {
+            const StepBands bands = run ? StepBands{} : step_bands(g, v->trace, cs, reach);
+            if (bands.n >= 2 && (ce = make_band_streams(g)) != cudaSuccess) { what = "band streams"; return ce; }
+            cudaGraph_t graph;
+            if ((ce = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+                what = "begin capture";
+                return ce;
+            }
+            int64_t nl = 0;
+            const cudaError_t le = issue_steps(g, vp, v->trace, dt, cs, fe_c, nl, &ip, &chk, run, &bands);
+            ce = cudaStreamEndCapture(g->stream, &graph);
+            if (le != cudaSuccess) {
+                if (ce == cudaSuccess) cudaGraphDestroy(graph);
+                what = "capture launch";
+                return le;
+            }
+            if (ce != cudaSuccess) { what = "end capture"; return ce; }
+            cudaGraphExec_t exec;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) { what = "graph instantiate"; return ce; }
+            if (g->graphs.size() >= 8) {
+                cudaGraphExecDestroy(g->graphs.front().exec);
+                g->graphs.erase(g->graphs.begin());
+            }
+            GraphEntry ge;
+            ge.nsteps = cs; ge.cur = g->cur; ge.first_explicit = fe_c; ge.trace = v->trace;
+            ge.layout = g->layout; ge.dt = dt; ge.vp = vp; ge.exec = exec;
+            ge.sur = sur;
+            ge.launches = nl;
+            std::memcpy(ge.sur_key, sur_key, sizeof(sur_key));
+            g->graphs.push_back(ge);
+            hit = &g->graphs.back();
+        }
+        if ((ce = cudaGraphLaunch(hit->exec, g->stream)) != cudaSuccess) { what = "graph launch"; return ce; }
+        total += hit->launches;
+        return cudaSuccess;
+    };
+    int done = 0;  // steps of the runs already issued
+    while (done < nsteps) {
+        const int cs = std::min(kGraphSteps, nsteps - done);
+        if ((e = run_one(cs, fe && done == 0)) != cudaSuccess) {
+            // the runs issued before stand: the host clock follows the device's
+            g->last_launches = total;
+            g->t = g->t + (double)done * dt;
+            g->steps += done;
+            if (done > 0) g->cross_explicit = false;
+            return cuda_fail(g, e, what);
         }
         if (cs & 1) g->cur ^= 1;
-        s0 += cs;
+        done += cs;
     }
     g->last_launches = total;
     g->t = g->t + (double)nsteps * dt;
