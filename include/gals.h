@@ -243,6 +243,18 @@ gals_status gals_diagnostics(gals_grid *grid, const gals_diag_request *req, gals
 gals_status gals_step_host(gals_grid *grid, const gals_velocity *vel, double dt, double t0,
                            const float *const *in, float *const *out);
 
+/* gals_step_host without the final wait: returns once the copies and the step are queued,
+ * for callers that step a host-resident field repeatedly.  in[p] must stay valid and
+ * unchanged, and out[p] must not be read, until gals_synchronize (or a synchronous host
+ * step) returns.  Consecutive calls overlap: the copy-in of a band of the next call waits
+ * only for the copy-out of the same band of this one, so out may be the next call's in (a
+ * host-side time loop).  Other calls on the grid (gals_step, gals_set_state,
+ * gals_read_state, ...) wait for the pending copies before they touch the state.  Errors
+ * of the queued work surface at gals_synchronize.  Bit-identical to gals_step_host.
+ * Errors: as gals_step_host. */
+gals_status gals_step_host_async(gals_grid *grid, const gals_velocity *vel, double dt, double t0,
+                                 const float *const *in, float *const *out);
+
 /* Value, unit normal and curvature of the current state's interpolant at npoints points
  * (Sec. 3.4: every first and second derivative inside a cell from the p-cubic interpolant
  * of that cell; eq. surface_normal n = grad H / |grad H|; eq. curvature in 2D,
@@ -258,7 +270,8 @@ gals_status gals_step_host(gals_grid *grid, const gals_velocity *vel, double dt,
 gals_status gals_eval_points(gals_grid *grid, const double *points, int64_t npoints, int memspace,
                              float *H, float *normal, float *kappa);
 
-/* Wait for the grid's stream; returns the first asynchronous error, if any. */
+/* Wait for the grid's stream and any pending host-step copies; returns the first
+ * asynchronous error, if any. */
 gals_status gals_synchronize(gals_grid *grid);
 
 /* Current grid time (host copy; advanced by gals_step at issue). */

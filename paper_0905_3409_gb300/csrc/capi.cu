@@ -79,6 +79,9 @@ struct gals_grid {
     // gals_step_host: copy-in and copy-out streams, one event per band and direction
     cudaStream_t hs_in = nullptr, hs_out = nullptr;
     cudaEvent_t hs_enter = nullptr, hs_in_ev[kHostBands] = {}, hs_step_ev[kHostBands] = {};
+    cudaEvent_t hs_out_ev[kHostBands] = {};  // copy-out of each band, of the last host step
+    cudaEvent_t hs_done = nullptr;           // its last copy-out
+    bool hs_pending = false;      // an asynchronous host step's copies may still run
     std::vector<GraphEntry> graphs;
     // captured multi-step 2D calls: one stream per row band (they carry no work outside a
     // capture) and two generations of per-band events
@@ -118,6 +121,15 @@ gals_status cuda_fail(gals_grid *g, cudaError_t e, const char *what)
     cudaGetLastError();
     return fail(g, e == cudaErrorMemoryAllocation ? GALS_ERR_NOMEM : GALS_ERR_CUDA, "%s: %s", what,
                 cudaGetErrorString(e));
+}
+
+// After gals_step_host_async: the grid stream waits for its last copy-out before any other
+// call touches the state buffers (the host streams run on their own until then).
+cudaError_t join_host_steps(gals_grid *g)
+{
+    if (!g->hs_pending) return cudaSuccess;
+    g->hs_pending = false;
+    return cudaStreamWaitEvent(g->stream, g->hs_done, 0);
 }
 
 int full_planes(int dim) { return dim == 2 ? 4 : 8; }
@@ -519,7 +531,9 @@ gals_status gals_destroy_grid(gals_grid *g)
     for (int b = 0; b < kHostBands; ++b) {
         if (g->hs_in_ev[b]) cudaEventDestroy(g->hs_in_ev[b]);
         if (g->hs_step_ev[b]) cudaEventDestroy(g->hs_step_ev[b]);
+        if (g->hs_out_ev[b]) cudaEventDestroy(g->hs_out_ev[b]);
     }
+    if (g->hs_done) cudaEventDestroy(g->hs_done);
     for (int b = 0; b < kStepBands; ++b) {
         if (g->band_s[b]) cudaStreamDestroy(g->band_s[b]);
         for (int k = 0; k < 2; ++k)
@@ -536,6 +550,7 @@ gals_status gals_set_state(gals_grid *g, const float *const *fields, int nfields
 {
     NvtxRange nvtx_range("gals_set_state");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     if (!fields) return fail(g, GALS_ERR_ARG, "fields is NULL");
     const int core = 1 + g->dim;
     if (nfields != core && nfields != g->nplanes)
@@ -580,6 +595,7 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
 {
     NvtxRange nvtx_range("gals_step");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(g, GALS_ERR_ARG, "dt must be finite and > 0");
     if (nsteps < 0) return fail(g, GALS_ERR_ARG, "nsteps must be >= 0");
@@ -749,6 +765,7 @@ static gals_status check_device_error(gals_grid *g)
 gals_status gals_synchronize(gals_grid *g)
 {
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "synchronize");
     return check_device_error(g);
@@ -769,6 +786,7 @@ gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int
 {
     NvtxRange nvtx_range("gals_read_state");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (!fields || nfields < 1 || nfields > g->nplanes)
         return fail(g, GALS_ERR_ARG, "nfields must be in 1..%d", g->nplanes);
@@ -794,10 +812,11 @@ gals_status gals_read_state(gals_grid *g, float *const *fields, int nfields, int
     return check_device_error(g);
 }
 
-gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, double t0,
-                           const float *const *in, float *const *out)
+// gals_step_host and gals_step_host_async: queue the band pipeline; the synchronous form
+// then drains every stream.
+static gals_status step_host_impl(gals_grid *g, const gals_velocity *v, double dt, double t0,
+                                  const float *const *in, float *const *out, bool async)
 {
-    NvtxRange nvtx_range("gals_step_host");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
     if (!in || !out) return fail(g, GALS_ERR_ARG, "in / out is NULL");
     for (int p = 0; p < g->nplanes; ++p)
@@ -818,9 +837,11 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
         e = cudaStreamCreateWithFlags(&g->hs_in, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->hs_out, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->hs_enter, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->hs_done, cudaEventDisableTiming);
         for (int b = 0; b < kHostBands && e == cudaSuccess; ++b) {
             e = cudaEventCreateWithFlags(&g->hs_in_ev[b], cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->hs_step_ev[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->hs_out_ev[b], cudaEventDisableTiming);
         }
         if (e != cudaSuccess) return cuda_fail(g, e, "copy streams / events");
     }
@@ -850,16 +871,19 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
     float *bin = g->buf[cur], *bout = g->buf[cur ^ 1];
     g->t = t0;
     // work already queued on the grid stream (a step reading or writing the buffers)
-    // comes first
+    // comes first; the copy-in of a band also waits for the copy-out of the same band of
+    // the previous host step, which may still be running (it reads the buffer this step
+    // fills, and its host rows may be this step's input)
     if ((e = cudaEventRecord(g->hs_enter, g->stream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(g->hs_in, g->hs_enter, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(g->hs_out, g->hs_enter, 0)) != cudaSuccess)
         return cuda_fail(g, e, "step_host order");
-    if ((e = cudaMemcpyAsync(g->t_dev, &g->t, sizeof(double), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
+    if ((e = launch_set_time(g->t_dev, t0, g->stream)) != cudaSuccess ||
         (e = launch_coef_table(g->coef, vp, g->t_dev, dt, 1, g->stream)) != cudaSuccess)
         return cuda_fail(g, e, "step_host coefficients");
     auto copy_in = [&](int b) {
         const size_t r0 = (size_t)b * R * rows_per, nr = (size_t)(std::min(nax, (b + 1) * R) - b * R) * rows_per;
+        e = cudaStreamWaitEvent(g->hs_in, g->hs_out_ev[b], 0);
         for (int p = 0; p < g->nplanes && e == cudaSuccess; ++p)
             e = cudaMemcpy2DAsync(bin + p * G.plane + r0 * G.pitch, dpitch, in[p] + r0 * g->n[0], row, row,
                                   nr, cudaMemcpyHostToDevice, g->hs_in);
@@ -877,6 +901,7 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
         for (int p = 0; p < g->nplanes && e == cudaSuccess; ++p)
             e = cudaMemcpy2DAsync(out[p] + r0 * g->n[0], row, bout + p * G.plane + r0 * G.pitch, dpitch, row,
                                   nr, cudaMemcpyDeviceToHost, g->hs_out);
+        if (e == cudaSuccess) e = cudaEventRecord(g->hs_out_ev[b], g->hs_out);
     };
     // enqueue in pipeline order, so that the first bands are stepped and copied out while
     // the host is still queueing the copies of later ones
@@ -886,7 +911,19 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
         if (e == cudaSuccess) step_out(b);
     }
     if (e == cudaSuccess) e = launch_advance_time(g->t_dev, 1, dt, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->hs_done, g->hs_out);
+    if (async && e == cudaSuccess) {
+        // the copies run on; other calls on the grid wait for them (join_host_steps)
+        g->hs_pending = true;
+        g->cur ^= 1;
+        g->t = t0 + dt;
+        g->steps = 1;
+        g->cross_explicit = false;
+        g->has_state = true;
+        return GALS_OK;
+    }
     // every stream is drained before returning, also after a failed launch
+    g->hs_pending = false;
     cudaError_t s1 = cudaStreamSynchronize(g->hs_in), s2 = cudaStreamSynchronize(g->hs_out);
     cudaError_t s3 = cudaStreamSynchronize(g->stream);
     if (e == cudaSuccess) e = s1 != cudaSuccess ? s1 : (s2 != cudaSuccess ? s2 : s3);
@@ -902,11 +939,26 @@ gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, doub
     return check_device_error(g);
 }
 
+gals_status gals_step_host(gals_grid *g, const gals_velocity *v, double dt, double t0,
+                           const float *const *in, float *const *out)
+{
+    NvtxRange nvtx_range("gals_step_host");
+    return step_host_impl(g, v, dt, t0, in, out, false);
+}
+
+gals_status gals_step_host_async(gals_grid *g, const gals_velocity *v, double dt, double t0,
+                                 const float *const *in, float *const *out)
+{
+    NvtxRange nvtx_range("gals_step_host_async");
+    return step_host_impl(g, v, dt, t0, in, out, true);
+}
+
 gals_status gals_eval_points(gals_grid *g, const double *points, int64_t npoints, int memspace,
                              float *H, float *normal, float *kappa)
 {
     NvtxRange nvtx_range("gals_eval_points");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (npoints < 0) return fail(g, GALS_ERR_ARG, "npoints must be >= 0");
     if (npoints > 0 && !points) return fail(g, GALS_ERR_ARG, "points is NULL");
@@ -952,6 +1004,7 @@ gals_status gals_eval_points(gals_grid *g, const double *points, int64_t npoints
 gals_status gals_state_planes(gals_grid *g, float **planes, int nplanes, int64_t *row_pitch)
 {
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     if (!planes || nplanes < 1 || nplanes > g->nplanes)
         return fail(g, GALS_ERR_ARG, "nplanes must be in 1..%d", g->nplanes);
     for (int p = 0; p < nplanes; ++p) planes[p] = g->buf[g->cur] + p * g->geom.plane;
@@ -963,6 +1016,7 @@ gals_status gals_diagnostics(gals_grid *g, const gals_diag_request *req, gals_di
 {
     NvtxRange nvtx_range("gals_diagnostics");
     if (!g) return fail(nullptr, GALS_ERR_ARG, "grid is NULL");
+    if (cudaError_t je = join_host_steps(g); je != cudaSuccess) return cuda_fail(g, je, "join host steps");
     if (!req || !out) return fail(g, GALS_ERR_ARG, "request/out is NULL");
     if (!g->has_state) return fail(g, GALS_ERR_STATE, "no state loaded");
     if (req->q < 0 || req->q > 16) return fail(g, GALS_ERR_ARG, "q must be in 0..16");

@@ -74,6 +74,8 @@ cudaError_t launch_coef_table(StageCoef *table, const VelParams &vp, const doubl
                               double dt, int nsteps, cudaStream_t s);
 // t_dev[0] += nsteps * dt
 cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream_t s);
+// the device clock set to t, in stream order (no host staging, the caller does not block)
+cudaError_t launch_set_time(double *t_dev, double t, cudaStream_t s);
 // Velocity kinds supported per dimension.
 bool vel_supported(int dim, int kind);
 

@@ -17,6 +17,11 @@ __global__ void k_advance_time(double *t, int nsteps, double dt)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) t[0] = t[0] + (double)nsteps * dt;
 }
+
+__global__ void k_set_time(double *t, double value)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) t[0] = value;
+}
 }  // namespace
 
 namespace {
@@ -63,6 +68,12 @@ cudaError_t launch_coef_table(StageCoef *table, const VelParams &vp, const doubl
 cudaError_t launch_advance_time(double *t_dev, int nsteps, double dt, cudaStream_t s)
 {
     k_advance_time<<<1, 32, 0, s>>>(t_dev, nsteps, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_time(double *t_dev, double t, cudaStream_t s)
+{
+    k_set_time<<<1, 32, 0, s>>>(t_dev, t);
     return cudaGetLastError();
 }
 

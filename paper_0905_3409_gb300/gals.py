@@ -32,7 +32,7 @@ MAX_WAVES = 1024
 # every symbol include/gals.h declares
 EXPORTS = [
     "gals_create_grid", "gals_destroy_grid", "gals_set_state", "gals_step", "gals_read_state",
-    "gals_diagnostics", "gals_synchronize", "gals_step_host", "gals_eval_points", "gals_time", "gals_state_planes", "gals_last_error",
+    "gals_diagnostics", "gals_synchronize", "gals_step_host", "gals_step_host_async", "gals_eval_points", "gals_time", "gals_state_planes", "gals_last_error",
     "gals_version",
     "gals_create_batch", "gals_destroy_batch", "gals_batch_set_state", "gals_batch_step",
     "gals_batch_read_state", "gals_batch_synchronize", "gals_batch_autotune",
@@ -123,6 +123,7 @@ def lib() -> ctypes.CDLL:
         L.gals_synchronize.argtypes = [vp]
         L.gals_step_host.argtypes = [vp, ctypes.POINTER(VelocityDesc), ctypes.c_double,
                                      ctypes.c_double, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.gals_step_host_async.argtypes = L.gals_step_host.argtypes
         L.gals_eval_points.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp]
         L.gals_time.argtypes = [vp]
         L.gals_time.restype = ctypes.c_double
@@ -256,6 +257,7 @@ class Grid:
         self.n = tuple(int(v) for v in n)
         self.nplanes = _nplanes(dim)
         self.shape = (self.nplanes,) + tuple(reversed(self.n))
+        self._pending_host = []  # host arrays of asynchronous host steps, until synchronize()
 
     # -- lifecycle
     def close(self):
@@ -338,6 +340,7 @@ class Grid:
 
     def synchronize(self):
         _check(lib().gals_synchronize(self._h), self._h)
+        self._pending_host = []
 
     def eval_points(self, points):
         """Value, unit normal and curvature of the interpolant at points (npts x dim).
@@ -365,11 +368,18 @@ class Grid:
                                       N.ctypes.data, K.ctypes.data), self._h)
         return H, N, K
 
-    def step_host(self, vel: Velocity, dt: float, t0: float, state, out=None):
+    def step_host(self, vel: Velocity, dt: float, t0: float, state, out=None, wait=True):
         """One step from the host state ``state`` (all planes, at time t0) to ``out`` (a new
         host array if None), with the copies overlapped with the step in bands; the grid
-        keeps the new state.  Page-locked (pinned) arrays let the copies overlap."""
-        st = np.ascontiguousarray(state, dtype=np.float32)
+        keeps the new state.  Page-locked (pinned) arrays let the copies overlap.  With
+        ``wait=False`` (gals_step_host_async) the call returns once the work is queued:
+        ``state`` must be a C-contiguous float32 array, and neither it may be changed nor
+        ``out`` read before synchronize(); the grid keeps both arrays alive until then."""
+        if wait:
+            st = np.ascontiguousarray(state, dtype=np.float32)
+        else:
+            st = state
+            assert isinstance(st, np.ndarray) and st.dtype == np.float32 and st.flags.c_contiguous
         assert st.shape == self.shape, (st.shape, self.shape)
         if out is None:
             out = np.empty(self.shape, dtype=np.float32)
@@ -378,8 +388,10 @@ class Grid:
         pin = (ctypes.c_void_p * nf)(*[st[p].ctypes.data for p in range(nf)])
         pout = (ctypes.c_void_p * nf)(*[out[p].ctypes.data for p in range(nf)])
         d = vel.desc()
-        _check(lib().gals_step_host(self._h, ctypes.byref(d), float(dt), float(t0), pin, pout),
-               self._h)
+        call = lib().gals_step_host if wait else lib().gals_step_host_async
+        _check(call(self._h, ctypes.byref(d), float(dt), float(t0), pin, pout), self._h)
+        if not wait:
+            self._pending_host.append((st, out))
         return out
 
     @property

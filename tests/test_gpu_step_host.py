@@ -106,3 +106,53 @@ def test_step_host_refuses_what_it_does_not_serve(G):
     with pytest.raises(G.GalsError) as e:
         g.step_host(G.Velocity("deform3d", T=3.0), 0.01, 0.0, st)
     assert e.value.status == G.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n,vel,cells", CASES)
+def test_async_host_loop_equals_synchronous(G, n, vel, cells):
+    """gals_step_host_async as a host-side time loop (each call's output array is the next
+    call's input, the calls queued back to back, one wait at the end) gives the states of
+    the same loop of synchronous calls bit for bit, and so does a chain into a separate
+    output array followed by a device step and a read (the other calls wait for the
+    pending copies)."""
+    dim = len(n)
+    st = _state(G, n, dim)
+    h = 1.0 / (max(n) - 1)
+    dt, t0 = cells * h, 0.1
+    v = G.Velocity(**vel)
+    nsteps = 4
+    # synchronous reference loop
+    a = G.Grid(n)
+    ref = _pinned(st.shape)
+    ref[:] = st
+    for k in range(nsteps):
+        a.step_host(v, dt, t0 + k * dt, ref, ref)
+    # the same loop queued: one array is each call's input and output
+    b = G.Grid(n)
+    buf = _pinned(st.shape)
+    buf[:] = st
+    for k in range(nsteps):
+        b.step_host(v, dt, t0 + k * dt, buf, buf, wait=False)
+    b.synchronize()
+    assert np.array_equal(buf, ref)
+    assert np.array_equal(b.read_state(), a.read_state())
+    assert b.time == pytest.approx(t0 + nsteps * dt, abs=1e-12)
+    # queued calls from a fixed input into another array, then other calls on the grid
+    c = G.Grid(n)
+    pin_in, pin_out = _pinned(st.shape), _pinned(st.shape)
+    pin_in[:] = st
+    c.step_host(v, dt, t0, pin_in, pin_out, wait=False)
+    c.step_host(v, dt, t0, pin_in, pin_out, wait=False)
+    c.step(v, dt, 1)                        # waits for the pending copies
+    after = c.read_state()
+    d = G.Grid(n)
+    d.set_state(st, t0=t0)
+    d.step(v, dt, 2)
+    assert np.array_equal(after, d.read_state())
+    c.synchronize()
+    one = G.Grid(n)
+    one.set_state(st, t0=t0)
+    one.step(v, dt, 1)
+    assert np.array_equal(pin_out, one.read_state())
+    for g in (a, b, c, d, one):
+        g.close()
