@@ -608,7 +608,7 @@ gals_status gals_step(gals_grid *g, const gals_velocity *v, double dt, int nstep
     float sur_key[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     cudaError_t e;
     if (v->kind == GALS_VEL_WAVES2D && nsteps > 0) {
-        // the modes in device memory, and room for the call's amplitude table
+        // the modes in device memory, and room for the amplitude table of a run of steps
         bool changed = false;
         if ((e = g->waves.upload(v, g->stream, &changed)) != cudaSuccess) return cuda_fail(g, e, "wave table");
         const int64_t need = (int64_t)std::min(nsteps, kGraphSteps) * 3 * v->nmodes;

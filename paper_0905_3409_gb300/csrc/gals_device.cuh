@@ -147,23 +147,29 @@ __device__ inline void stage_coef_one(const VelParams &vp, double t, double dt, 
     sc.pad = 0.f;
     sc.wamp = nullptr;
     if (vp.kind != VK_FOURIER2D) return;
-    for (int s = 0; s < 3; ++s) {
-        const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
+    // each mode once, added to its (k, l) entry: every entry sums its modes in index order
+    double acc[3][16];
+    for (int s = 0; s < 3; ++s)
+        for (int kl = 0; kl < 16; ++kl) acc[s][kl] = 0.0;
+    for (int m = 0; m < vp.nmodes; ++m) {
+        const int code = vp.mode_kl[m], k = code & 0xff, l = code >> 8;
+        if (k < 1 || k > 4 || l < 1 || l > 4) continue;
+        const int kl = (k - 1) * 4 + (l - 1);
+        const double a = (double)vp.mode_a[m], n = vp.mode_n[m], chi = vp.mode_chi[m];
+        for (int s = 0; s < 3; ++s) {
+            const double ts = s == 0 ? t + dt : (s == 1 ? t : t + 0.5 * dt);
+            double ph = 2.0 * (n * ts + chi);  // in units of pi
+            ph = ph - 2.0 * floor(0.5 * ph);
+            acc[s][kl] += a * cospi(ph);
+        }
+    }
+    for (int s = 0; s < 3; ++s)
         for (int kl = 0; kl < 16; ++kl) {
-            const int k = kl / 4 + 1, l = kl % 4 + 1;
-            double acc = 0.0;
-            for (int m = 0; m < vp.nmodes; ++m) {
-                if (vp.mode_kl[m] != (k | (l << 8))) continue;
-                double ph = 2.0 * (vp.mode_n[m] * ts + vp.mode_chi[m]);  // in units of pi
-                ph = ph - 2.0 * floor(0.5 * ph);
-                acc += (double)vp.mode_a[m] * cospi(ph);
-            }
-            const float a = (float)acc, lp = (float)l * kPi;
+            const float a = (float)acc[s][kl], lp = (float)(kl % 4 + 1) * kPi;
             sc.A[s][kl] = a;
             sc.Al[s][kl] = a * lp;
             sc.All[s][kl] = a * lp * lp;
         }
-    }
 }
 
 // ---------------------------------------------------------------- velocity fields
