@@ -39,6 +39,8 @@ def expected_bands(n1, reach_rows):
 def _vel(G, kind):
     if kind == "vortex2d":
         return G.Velocity("vortex2d", T=8.0)
+    if kind == "waves2d":
+        return G.Velocity("waves2d", modes=inputs.wave_modes(32, seed=41))
     if kind == "rotation":
         return G.Velocity("rotation", omega=2 * math.pi)
     if kind == "fourier2d":
@@ -54,6 +56,7 @@ CASES = [
     ((190, 450), "vortex2d", 0.8, "compact", "central"),
     ((140, 170), "heun", 0.8, "full", "central"),
     ((201, 150), "vortex2d", 0.8, "full", "cell"),
+    ((260, 140), "waves2d", 0.8, "full", "central"),
 ]
 
 
@@ -70,7 +73,8 @@ def test_banded_graph_equals_single_steps(G, n, kind, cfl, layout, cross):
     a.step(vel, dt, nsteps)  # one captured graph of row bands
     for _ in range(nsteps):
         b.step(vel, dt, 1)   # one eager launch per step, whole grid
-    assert b.last_step_launches() == 3  # coefficients, step, clock
+    # (plane waves: amplitudes,) coefficients, step, clock
+    assert b.last_step_launches() == (4 if kind == "waves2d" else 3)
     ra, rb = a.read_state(), b.read_state()
     assert np.array_equal(ra, rb, equal_nan=True)
     assert np.isfinite(ra).all()
@@ -133,3 +137,21 @@ def test_bench_configuration_bands_equal_single_steps(G):
     assert np.array_equal(ra, rb)
     a.close()
     b.close()
+
+
+def test_banded_graph_explicit_cross_compact(G):
+    """COMPACT layout with the mixed derivatives given explicitly (zero, as configuration 1
+    sets them): only the first step of the call reads the given planes, later ones rebuild
+    them; a banded multi-step call equals single steps bit for bit."""
+    n = (230, 170)
+    st = inputs.circle_sdf(n).astype(np.float32)
+    st[3] = 0.0
+    vel = G.Velocity("vortex2d", T=8.0)
+    dt = 0.8 / (max(n) - 1)
+    a, b = G.Grid(n, layout="compact"), G.Grid(n, layout="compact")
+    for g in (a, b):
+        g.set_state(st, recon=False)
+    a.step(vel, dt, 5)
+    for _ in range(5):
+        b.step(vel, dt, 1)
+    assert np.array_equal(a.read_state(), b.read_state())
